@@ -1,0 +1,201 @@
+/*
+ * amlbm.h -- C ABI of the GB300 (sm_103a) axisymmetric multiphase lattice
+ * Boltzmann library (Srivastava, Perlekar, ten Thije Boonkkamp, Verma, Toschi,
+ * "Axisymmetric Multiphase Lattice Boltzmann Method", arXiv:1310.1871).
+ *
+ * What the library computes (one timestep of every site of the D2Q9 meridional
+ * (z, r) lattice, Sec. II):
+ *   rho = sum_i f_i, rho u = sum_i c_i f_i                        (App. A, Eq. hydro_var)
+ *   psi = rho0 (1 - exp(-rho / rho0))                             (Sec. II.A)
+ *   F   = F_SC (Eq. scforce) + F^{gamma,sym} (Eq. scAxisExtra, with the
+ *         isotropic stencils of Sec. II.D) + rho g_z e_z          (Sec. III.1)
+ *   u   = (rho u + F/2)/rho,  u^eq = (rho u + tau F)/rho          (Eqs. uhydro, ueq)
+ *   h_i = W_i (S + 3 (c_iz H_z + c_ir H_r)), S = -rho u_r / r     (Eq. condition_h, App. A)
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f^eq_i(rho, u^eq))/tau + h_i   (Eq. lbm2d_mod_new)
+ * with mid-grid specular reflection on the axis, mid-grid specular (free-slip)
+ * or bounce-back (no-slip) at the outer radial wall, and periodic z (Sec. II.E).
+ *
+ * Lattice conventions
+ *   Sites (k, j), k = 0..Nz-1 along z (z_k = k), j = 0..Nr-1 along r
+ *   (r_j = j + 1/2: the axis lies half a spacing below row 0).
+ *   Velocities (c_z, c_r): c_0 = (0,0), c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0),
+ *   c_4 = (0,-1), c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1), c_8 = (1,-1).
+ *   Host field arrays are float64, row-major [Nr][Nz] (a[j * Nz + k]);
+ *   populations on the host are float64 [9][Nr][Nz].
+ *
+ * Memory and ownership
+ *   A context owns one device arena.  The caller either passes device memory
+ *   (workspace != NULL, at least amlbm_*_workspace_bytes() bytes, 256-byte
+ *   aligned, kept alive until destroy) or lets the library cudaMalloc it.
+ *   Host arrays passed to any call are read or written during the call only.
+ *   All work is enqueued on the stream given at creation (a cudaStream_t;
+ *   NULL = legacy default stream).  Calls that return host data synchronise
+ *   that stream; amlbm_step and amlbm_batch_step do not.
+ *
+ * Errors
+ *   Every int-returning call returns AMLBM_OK (0) or a negative AMLBM_E* code
+ *   and never throws.  amlbm_last_error() returns a thread-local message for
+ *   the last failing call on the calling thread.  A CUDA error from an
+ *   asynchronous launch may surface at a later call that synchronises.
+ */
+#ifndef AMLBM_H
+#define AMLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMLBM_OK 0
+#define AMLBM_EINVAL (-1)    /* bad argument (sizes, tau <= 1/2, rho0 <= 0, G < -6.5, ...) */
+#define AMLBM_ENOMEM (-2)    /* device allocation failed or workspace too small */
+#define AMLBM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define AMLBM_EUNSTABLE (-5) /* diagnostics found a non-finite or non-positive density */
+
+/* Outer radial wall (Sec. II.E). */
+#define AMLBM_WALL_FREESLIP 0 /* mid-grid specular reflection */
+#define AMLBM_WALL_NOSLIP 1   /* mid-grid bounce-back */
+
+/* Discretisation of h_i(x + c_i/2, t + 1/2) in Eq. lbm2d_mod_new. */
+#define AMLBM_SRC_LOCAL 0 /* h at the departure site, time t (default) */
+#define AMLBM_SRC_LINK 1  /* average of h at both ends of the link, time t */
+
+/* Storage of the populations; arithmetic is FP64 for F64 and FP32 otherwise. */
+#define AMLBM_STORE_F64 0
+#define AMLBM_STORE_F32 1
+#define AMLBM_STORE_F16 2  /* IEEE half of f_i - W_i rho_ref */
+#define AMLBM_STORE_BF16 3 /* bfloat16 of f_i - W_i rho_ref */
+
+/* Boundary and model options of one lattice. */
+typedef struct amlbm_bc {
+  int wall_r;     /* AMLBM_WALL_* */
+  int axisym;     /* 1: axisymmetric sources and force (default); 0: planar 2D Shan-Chen */
+  int src_mode;   /* AMLBM_SRC_* */
+  int storage;    /* AMLBM_STORE_* (a batch uses the storage of its first instance) */
+  double g_z;     /* body acceleration along +z (force rho g_z), Sec. III.1 */
+  double rho_ref; /* shift of the 16-bit storage forms */
+} amlbm_bc;
+
+/* Parameters of the diagnostics (where to measure the drop or thread). */
+typedef struct amlbm_diag_params {
+  double zc;    /* axial position of the drop centre / probe column */
+  double R;     /* radius used to normalise the quadrupole amplitude a2 */
+  double rho_l; /* liquid density of the indicator phi = (rho - rho_v)/(rho_l - rho_v) */
+  double rho_v; /* vapour density of the indicator */
+} amlbm_diag_params;
+
+/* Diagnostics of the current state, all accumulated in FP64 (deterministic order). */
+typedef struct amlbm_diag {
+  double mass2d; /* sum rho */
+  double mass3d; /* sum 2 pi r rho */
+  double momz3d; /* sum 2 pi r rho u_z (hydrodynamic u) */
+  double Eke;    /* pi sum r rho |u|^2 (Sec. III) */
+  double umax;   /* max |u| */
+  double a2;     /* 5/(4 pi R^5) sum 2 pi r phi ((z - zc)^2 - r^2/2) */
+  double A;      /* interface radius on column round(zc): first row where rho < (rho_l+rho_v)/2, interpolated */
+  double neck;   /* minimum over columns of the interface radius */
+  double p_in;   /* p = c_s^2 rho + c_s^2 G psi^2 / 2 (Eq. pressure) at (round(zc), row 0) */
+  double p_out;  /* the same at (round(zc) + Nz/2, row Nr-1) */
+  double dp;     /* p_in - p_out */
+  double bad;    /* number of sites with non-finite or non-positive rho */
+  double sumS;   /* sum over sites of the mass source -rho u_r / r */
+  double steps;  /* timesteps taken since the fields were set */
+  double reserved[2];
+} amlbm_diag;
+
+/* ---------------------------------------------------------------- one lattice */
+
+typedef struct amlbm_ctx amlbm_ctx;
+
+/* Device bytes a context of this size and storage needs. */
+size_t amlbm_workspace_bytes(int Nz, int Nr, int storage);
+
+/* Create a lattice of Nz x Nr sites with relaxation time tau (nu = (tau - 1/2)/3),
+ * Shan-Chen coupling G and pseudopotential scale rho0.  bc may be NULL (defaults:
+ * free-slip, axisymmetric, departure-site source, FP64 storage, g_z = 0,
+ * rho_ref = 1).  Requires Nz >= 1, Nr >= 4, tau > 1/2, rho0 > 0, G >= -6.5
+ * (the paper's stability limit is G >= -6, Sec. II.D).  cuda_stream is a
+ * cudaStream_t.  workspace: see "Memory and ownership". */
+int amlbm_create(int Nz, int Nr, double tau, double G, double rho0, const amlbm_bc* bc,
+                 void* cuda_stream, void* workspace, size_t workspace_bytes, amlbm_ctx** out);
+
+/* f = f^eq(rho, u) from host arrays [Nr][Nz] (uz, ur may be NULL for rest). */
+int amlbm_init_fields(amlbm_ctx* ctx, const double* rho, const double* uz, const double* ur);
+
+/* The same from device float64 arrays [Nr][Nz] (uz, ur may be NULL). */
+int amlbm_init_fields_device(amlbm_ctx* ctx, const double* rho, const double* uz,
+                             const double* ur);
+
+/* Enqueue n timesteps (n >= 0) on the context's stream. */
+int amlbm_step(amlbm_ctx* ctx, int n);
+
+/* Density and hydrodynamic velocity (Eq. uhydro) of the current state into host
+ * arrays [Nr][Nz]; any pointer may be NULL.  f (nullable) receives the decoded
+ * populations [9][Nr][Nz].  Synchronises. */
+int amlbm_read_fields(amlbm_ctx* ctx, double* rho, double* uz, double* ur, double* f);
+
+/* Diagnostics of the current state; dp may be NULL (zc = Nz/2, R = 1, rho_l = 2,
+ * rho_v = 0.1).  Returns AMLBM_EUNSTABLE (after filling *out) when bad > 0.
+ * Synchronises. */
+int amlbm_diagnostics(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* out);
+
+/* Copy the full state (populations, psi, step count) to / from a host buffer.
+ * amlbm_save_state with buf == NULL stores the needed size in *len. */
+int amlbm_save_state(amlbm_ctx* ctx, void* buf, size_t* len);
+int amlbm_load_state(amlbm_ctx* ctx, const void* buf, size_t len);
+
+/* Device pointers of the current populations ([9][Nr][pitch], element type of
+ * the storage) and psi ([Nr][pitch], FP64 for F64 storage, else FP32), and the
+ * row pitch in elements.  Valid until the next step. */
+int amlbm_device_state(amlbm_ctx* ctx, void** f, void** psi, int* pitch);
+
+void amlbm_destroy(amlbm_ctx* ctx);
+
+/* ---------------------------------------------------------------- batches */
+
+/* One independent lattice of a batch. */
+typedef struct amlbm_instance {
+  int Nz, Nr;
+  double tau, G, rho0;
+  amlbm_bc bc;
+} amlbm_instance;
+
+/* Tile shape of the fused step kernel (sites along z x sites along r).
+ * tile_z = tile_r = 0 lets the library choose. */
+typedef struct amlbm_tune {
+  int tile_z, tile_r;
+  int graph_chunk; /* steps per captured CUDA graph in amlbm_batch_step (0 = no graph) */
+} amlbm_tune;
+
+typedef struct amlbm_batch amlbm_batch;
+
+/* Supported tiles for a storage form, as pairs (tile_z, tile_r); returns the count. */
+int amlbm_tiles(int storage, int* tz, int* tr, int cap);
+
+size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst);
+
+/* n independent lattices stepped together: one kernel launch per timestep covers
+ * every tile of every instance.  All instances use inst[0].bc.storage. */
+int amlbm_batch_create(int n, const amlbm_instance* inst, const amlbm_tune* tune,
+                       void* cuda_stream, void* workspace, size_t workspace_bytes,
+                       amlbm_batch** out);
+int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const double* uz,
+                            const double* ur);
+int amlbm_batch_step(amlbm_batch* b, int n);
+int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f);
+int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out);
+/* Sites of all instances (the work of one batch timestep) and kernel launches per step. */
+long long amlbm_batch_sites(const amlbm_batch* b);
+void amlbm_batch_destroy(amlbm_batch* b);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* amlbm_last_error(void);
+
+/* Library version string. */
+const char* amlbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMLBM_H */

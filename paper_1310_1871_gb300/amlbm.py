@@ -1,0 +1,327 @@
+"""Thin ctypes binding of libamlbm.so (the C ABI declared in include/amlbm.h).
+
+Argument marshalling only: every step of the lattice Boltzmann update runs in
+the library's CUDA kernels.  PyTorch provides the device workspace and the
+stream.  There is no CPU fallback: if the library cannot be built or loaded,
+or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamlbm.so")
+_lib = None
+_lock = threading.Lock()
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -5
+WALL = {"freeslip": 0, "noslip": 1}
+SRC = {"local": 0, "link": 1}
+STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+DIAG_FIELDS = ["mass2d", "mass3d", "momz3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out",
+               "dp", "bad", "sumS", "steps"]
+
+
+class AmlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"amlbm error {code}: {msg}")
+        self.code = code
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("wall_r", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int),
+                ("storage", ctypes.c_int), ("g_z", ctypes.c_double), ("rho_ref", ctypes.c_double)]
+
+
+class DiagParams(ctypes.Structure):
+    _fields_ = [("zc", ctypes.c_double), ("R", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("rho_v", ctypes.c_double)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in DIAG_FIELDS] + [("reserved", ctypes.c_double * 2)]
+
+
+class InstanceC(ctypes.Structure):
+    _fields_ = [("Nz", ctypes.c_int), ("Nr", ctypes.c_int), ("tau", ctypes.c_double),
+                ("G", ctypes.c_double), ("rho0", ctypes.c_double), ("bc", BC)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("tile_z", ctypes.c_int), ("tile_r", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
+
+
+EXPORTS = [
+    "amlbm_workspace_bytes", "amlbm_create", "amlbm_init_fields", "amlbm_init_fields_device",
+    "amlbm_step", "amlbm_read_fields", "amlbm_diagnostics", "amlbm_save_state", "amlbm_load_state",
+    "amlbm_device_state", "amlbm_destroy", "amlbm_tiles", "amlbm_batch_workspace_bytes",
+    "amlbm_batch_create", "amlbm_batch_init_fields", "amlbm_batch_step", "amlbm_batch_read",
+    "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
+    "amlbm_version",
+]
+
+
+def load(build_if_missing: bool = True):
+    """Load libamlbm.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1310_1871_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        sz = ctypes.c_size_t
+        lib.amlbm_workspace_bytes.argtypes = [ip, ip, ip]
+        lib.amlbm_workspace_bytes.restype = sz
+        lib.amlbm_create.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(BC), vp, vp, sz, ctypes.POINTER(vp)]
+        lib.amlbm_init_fields.argtypes = [vp, dp, dp, dp]
+        lib.amlbm_init_fields_device.argtypes = [vp, vp, vp, vp]
+        lib.amlbm_step.argtypes = [vp, ip]
+        lib.amlbm_read_fields.argtypes = [vp, dp, dp, dp, dp]
+        lib.amlbm_diagnostics.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
+        lib.amlbm_save_state.argtypes = [vp, vp, ctypes.POINTER(sz)]
+        lib.amlbm_load_state.argtypes = [vp, vp, sz]
+        lib.amlbm_device_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip)]
+        lib.amlbm_destroy.argtypes = [vp]
+        lib.amlbm_destroy.restype = None
+        lib.amlbm_tiles.argtypes = [ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
+        lib.amlbm_batch_workspace_bytes.argtypes = [ip, ctypes.POINTER(InstanceC)]
+        lib.amlbm_batch_workspace_bytes.restype = sz
+        lib.amlbm_batch_create.argtypes = [ip, ctypes.POINTER(InstanceC), ctypes.POINTER(Tune), vp, vp,
+                                           sz, ctypes.POINTER(vp)]
+        lib.amlbm_batch_init_fields.argtypes = [vp, ip, dp, dp, dp]
+        lib.amlbm_batch_step.argtypes = [vp, ip]
+        lib.amlbm_batch_read.argtypes = [vp, ip, dp, dp, dp, dp]
+        lib.amlbm_batch_diagnostics.argtypes = [vp, ip, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
+        lib.amlbm_batch_sites.argtypes = [vp]
+        lib.amlbm_batch_sites.restype = ctypes.c_longlong
+        lib.amlbm_batch_destroy.argtypes = [vp]
+        lib.amlbm_batch_destroy.restype = None
+        lib.amlbm_last_error.restype = ctypes.c_char_p
+        lib.amlbm_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(lib, rc):
+    if rc != OK:
+        raise AmlbmError(rc, lib.amlbm_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream), s
+
+
+def make_bc(wall="freeslip", axisym=True, src="local", storage="f64", gz=0.0, rho_ref=1.0) -> BC:
+    return BC(WALL[wall] if isinstance(wall, str) else int(wall), int(bool(axisym)),
+              SRC[src] if isinstance(src, str) else int(src),
+              STORAGE[storage] if isinstance(storage, str) else int(storage), float(gz), float(rho_ref))
+
+
+def _diag_dict(d: Diag) -> dict:
+    return {n: getattr(d, n) for n in DIAG_FIELDS}
+
+
+@dataclass
+class InstanceSpec:
+    """One lattice of a batch (plain parameters; fields are set with init_fields)."""
+    Nz: int
+    Nr: int
+    tau: float = 1.0
+    G: float = -5.0
+    rho0: float = 1.0
+    wall: str = "freeslip"
+    axisym: bool = True
+    src: str = "local"
+    gz: float = 0.0
+    rho_ref: float = 1.0
+
+
+class Batch:
+    """Independent lattices stepped together, one kernel launch per timestep."""
+
+    def __init__(self, specs, storage="f32", tile=None, graph_chunk=0, stream=None):
+        import torch
+        self.lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("amlbm needs a CUDA device")
+        self.specs = list(specs)
+        n = len(self.specs)
+        arr = (InstanceC * n)()
+        for i, s in enumerate(self.specs):
+            arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
+                               make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref))
+        self._arr = arr
+        nbytes = self.lib.amlbm_batch_workspace_bytes(n, arr)
+        if nbytes == 0:
+            raise AmlbmError(EINVAL, self.lib.amlbm_last_error().decode())
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        sh, self.stream = _stream_handle(stream)
+        tune = Tune(*(tile if tile else (0, 0)), int(graph_chunk))
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.amlbm_batch_create(n, arr, ctypes.byref(tune), sh,
+                                                     ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)))
+        self.h = h
+        self.storage = storage
+        self.sites = int(self.lib.amlbm_batch_sites(h))
+
+    def init_fields(self, k, rho, uz=None, ur=None):
+        s = self.specs[k]
+        shp = (s.Nr, s.Nz)
+        rho, uz, ur = _host(rho, shp), _host(uz, shp), _host(ur, shp)
+        _check(self.lib, self.lib.amlbm_batch_init_fields(self.h, k, _dptr(rho), _dptr(uz), _dptr(ur)))
+
+    def step(self, n=1):
+        _check(self.lib, self.lib.amlbm_batch_step(self.h, int(n)))
+
+    def read(self, k, with_f=False):
+        s = self.specs[k]
+        rho, uz, ur = (np.empty((s.Nr, s.Nz)) for _ in range(3))
+        f = np.empty((9, s.Nr, s.Nz)) if with_f else None
+        _check(self.lib, self.lib.amlbm_batch_read(self.h, k, _dptr(rho), _dptr(uz), _dptr(ur), _dptr(f)))
+        return (rho, uz, ur, f) if with_f else (rho, uz, ur)
+
+    def read_f(self, k):
+        s = self.specs[k]
+        f = np.empty((9, s.Nr, s.Nz))
+        _check(self.lib, self.lib.amlbm_batch_read(self.h, k, None, None, None, _dptr(f)))
+        return f
+
+    def diagnostics(self, k, zc=None, R=1.0, rho_l=2.0, rho_v=0.1, check=True):
+        s = self.specs[k]
+        dp = DiagParams(s.Nz / 2 if zc is None else float(zc), float(R), float(rho_l), float(rho_v))
+        d = Diag()
+        rc = self.lib.amlbm_batch_diagnostics(self.h, k, ctypes.byref(dp), ctypes.byref(d))
+        if rc not in (OK, EUNSTABLE) or (check and rc != OK):
+            _check(self.lib, rc)
+        return _diag_dict(d)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.amlbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Lattice:
+    """One Nz x Nr lattice (amlbm_ctx)."""
+
+    def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, wall="freeslip", axisym=True, src="local",
+                 storage="f64", gz=0.0, rho_ref=1.0, stream=None):
+        import torch
+        self.lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("amlbm needs a CUDA device")
+        self.Nz, self.Nr = int(Nz), int(Nr)
+        bc = make_bc(wall, axisym, src, storage, gz, rho_ref)
+        nbytes = self.lib.amlbm_workspace_bytes(self.Nz, self.Nr, bc.storage)
+        if nbytes == 0:
+            raise AmlbmError(EINVAL, "bad lattice size or storage")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        sh, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(self.lib, self.lib.amlbm_create(self.Nz, self.Nr, float(tau), float(G), float(rho0),
+                                               ctypes.byref(bc), sh, ctypes.c_void_p(aligned), nbytes,
+                                               ctypes.byref(h)))
+        self.h = h
+        self.storage = storage
+
+    def init_fields(self, rho, uz=None, ur=None):
+        shp = (self.Nr, self.Nz)
+        rho, uz, ur = _host(rho, shp), _host(uz, shp), _host(ur, shp)
+        _check(self.lib, self.lib.amlbm_init_fields(self.h, _dptr(rho), _dptr(uz), _dptr(ur)))
+
+    def init_fields_device(self, rho, uz=None, ur=None):
+        """rho, uz, ur: contiguous float64 CUDA tensors [Nr, Nz] (uz, ur optional)."""
+        def p(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()
+            return ctypes.c_void_p(t.data_ptr())
+        _check(self.lib, self.lib.amlbm_init_fields_device(self.h, p(rho), p(uz), p(ur)))
+
+    def step(self, n=1):
+        _check(self.lib, self.lib.amlbm_step(self.h, int(n)))
+
+    def read(self):
+        rho, uz, ur = (np.empty((self.Nr, self.Nz)) for _ in range(3))
+        _check(self.lib, self.lib.amlbm_read_fields(self.h, _dptr(rho), _dptr(uz), _dptr(ur), None))
+        return rho, uz, ur
+
+    def read_f(self):
+        f = np.empty((9, self.Nr, self.Nz))
+        _check(self.lib, self.lib.amlbm_read_fields(self.h, None, None, None, _dptr(f)))
+        return f
+
+    def diagnostics(self, zc=None, R=1.0, rho_l=2.0, rho_v=0.1, check=True):
+        dp = DiagParams(self.Nz / 2 if zc is None else float(zc), float(R), float(rho_l), float(rho_v))
+        d = Diag()
+        rc = self.lib.amlbm_diagnostics(self.h, ctypes.byref(dp), ctypes.byref(d))
+        if rc not in (OK, EUNSTABLE) or (check and rc != OK):
+            _check(self.lib, rc)
+        return _diag_dict(d)
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(self.lib, self.lib.amlbm_save_state(self.h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.lib, self.lib.amlbm_save_state(self.h, buf, ctypes.byref(n)))
+        return buf.raw
+
+    def load_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        _check(self.lib, self.lib.amlbm_load_state(self.h, buf, len(data)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.amlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tiles(storage="f32"):
+    lib = load()
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    n = lib.amlbm_tiles(st, None, None, 0)
+    tz, tr = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+    lib.amlbm_tiles(st, tz, tr, n)
+    return list(zip(tz, tr))

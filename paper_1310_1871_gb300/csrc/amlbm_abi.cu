@@ -1,0 +1,583 @@
+// Host side of the C ABI declared in include/amlbm.h: validation, the device
+// arena, kernel launches, CUDA-graph chunks of timesteps, read-back and
+// diagnostics.  Every entry point returns a status code and never throws.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "amlbm.h"
+#include "amlbm_internal.cuh"
+
+using amlbm::InstDesc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define AMLBM_CK(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(AMLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int pitch_of(int Nz) { return (Nz + 31) / 32 * 32; }
+size_t elem_bytes(int storage) {
+  return storage == AMLBM_STORE_F64 ? 8 : storage == AMLBM_STORE_F32 ? 4 : 2;
+}
+size_t compute_bytes(int storage) { return storage == AMLBM_STORE_F64 ? 8 : 4; }
+
+amlbm_bc default_bc() {
+  amlbm_bc b;
+  b.wall_r = AMLBM_WALL_FREESLIP;
+  b.axisym = 1;
+  b.src_mode = AMLBM_SRC_LOCAL;
+  b.storage = AMLBM_STORE_F64;
+  b.g_z = 0.0;
+  b.rho_ref = 1.0;
+  return b;
+}
+
+// Tile choice when the caller gives none: the largest compiled tile that still
+// yields two CTAs per SM over the whole batch, else the smallest tile.
+void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* tz, int* tr) {
+  int cz[16], cr[16];
+  const int n = amlbm::tile_list(storage, cz, cr, 16);
+  int best = -1;
+  long long best_area = -1;
+  for (int c = 0; c < n; ++c) {
+    long long tiles = 0;
+    for (const auto& I : inst)
+      tiles += (long long)((I.Nz + cz[c] - 1) / cz[c]) * ((I.Nr + cr[c] - 1) / cr[c]);
+    const long long area = (long long)cz[c] * cr[c];
+    if (tiles >= 2 * 152 && area > best_area) { best = c; best_area = area; }
+  }
+  if (best < 0) {
+    best = 0;
+    for (int c = 1; c < n; ++c)
+      if ((long long)cz[c] * cr[c] < (long long)cz[best] * cr[best]) best = c;
+  }
+  *tz = cz[best];
+  *tr = cr[best];
+}
+
+int validate(const amlbm_instance& I, int idx) {
+  const std::string w = "instance " + std::to_string(idx) + ": ";
+  if (I.Nz < 1 || I.Nr < 4 || I.Nz > (1 << 20) || I.Nr > (1 << 20) ||
+      (long long)I.Nz * I.Nr > (1LL << 30))
+    return fail(AMLBM_EINVAL, w + "need 1 <= Nz, 4 <= Nr, Nz*Nr <= 2^30");
+  if (!(I.tau > 0.5) || !std::isfinite(I.tau)) return fail(AMLBM_EINVAL, w + "tau must exceed 1/2");
+  if (!(I.rho0 > 0) || !std::isfinite(I.rho0)) return fail(AMLBM_EINVAL, w + "rho0 must be positive");
+  if (!(I.G >= -6.5) || !std::isfinite(I.G))
+    return fail(AMLBM_EINVAL, w + "G below -6.5 (the Shan-Chen model is unstable beyond G ~ -6)");
+  if (I.bc.wall_r != AMLBM_WALL_FREESLIP && I.bc.wall_r != AMLBM_WALL_NOSLIP)
+    return fail(AMLBM_EINVAL, w + "bad wall_r");
+  if (I.bc.axisym != 0 && I.bc.axisym != 1) return fail(AMLBM_EINVAL, w + "axisym must be 0 or 1");
+  if (I.bc.src_mode != AMLBM_SRC_LOCAL && I.bc.src_mode != AMLBM_SRC_LINK)
+    return fail(AMLBM_EINVAL, w + "bad src_mode");
+  if (I.bc.storage < AMLBM_STORE_F64 || I.bc.storage > AMLBM_STORE_BF16)
+    return fail(AMLBM_EINVAL, w + "bad storage");
+  if (!std::isfinite(I.bc.g_z) || !std::isfinite(I.bc.rho_ref))
+    return fail(AMLBM_EINVAL, w + "g_z and rho_ref must be finite");
+  return AMLBM_OK;
+}
+
+struct Layout {
+  size_t total = 0;
+  size_t desc = 0, tiles = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0, unpack = 0;
+  std::vector<size_t> f0, f1, p0, p1, rho, uz, ur;
+  int ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
+};
+
+Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz, int tr) {
+  Layout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
+  const size_t n = inst.size();
+  for (const auto& I : inst) {
+    L.ntiles += ((I.Nz + tz - 1) / tz) * ((I.Nr + tr - 1) / tr);
+    L.maxN = std::max(L.maxN, I.Nz * I.Nr);
+    L.maxNz = std::max(L.maxNz, I.Nz);
+    L.diag_nblk = std::max(L.diag_nblk, amlbm::diag_blocks(I.Nz, I.Nr));
+  }
+  L.desc = take(n * sizeof(InstDesc));
+  L.tiles = take((size_t)L.ntiles * sizeof(int));
+  L.diag_part = take((size_t)L.diag_nblk * 8 * sizeof(double));
+  L.diag_cols = take((size_t)L.maxNz * sizeof(double));
+  L.diag_out = take(16 * sizeof(double));
+  L.upload = take((size_t)3 * L.maxN * sizeof(double));
+  L.unpack = take((size_t)9 * L.maxN * sizeof(double));
+  for (const auto& I : inst) {
+    const size_t plane = (size_t)pitch_of(I.Nz) * I.Nr;
+    L.f0.push_back(take(9 * plane * elem_bytes(storage)));
+    L.f1.push_back(take(9 * plane * elem_bytes(storage)));
+    L.p0.push_back(take(plane * compute_bytes(storage)));
+    L.p1.push_back(take(plane * compute_bytes(storage)));
+    L.rho.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
+    L.uz.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
+    L.ur.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
+  }
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct amlbm_batch {
+  int n = 0, storage = 0, tz = 0, tr = 0, graph_chunk = 0;
+  cudaStream_t stream = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool owns = false;
+  Layout L;
+  std::vector<InstDesc> desc;
+  std::vector<long long> steps;  // per instance, since its fields were set
+  InstDesc* d_desc = nullptr;
+  int* d_tiles = nullptr;
+  int parity = 0;
+  long long sites = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+struct amlbm_ctx {
+  amlbm_batch* b;
+};
+
+namespace {
+
+int launch_steps_direct(amlbm_batch* b, int n) {
+  for (int s = 0; s < n; ++s) {
+    const cudaError_t e = amlbm::launch_step(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles,
+                                             b->L.ntiles, 0, b->parity, b->stream);
+    if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
+    b->parity ^= 1;
+  }
+  return AMLBM_OK;
+}
+
+int ensure_graph(amlbm_batch* b, int parity) {
+  if (b->graph[parity]) return AMLBM_OK;
+  cudaGraph_t g = nullptr;
+  AMLBM_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int p = parity;
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < b->graph_chunk && e == cudaSuccess; ++s) {
+    e = amlbm::launch_step(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles, b->L.ntiles, 0, p,
+                           b->stream);
+    p ^= 1;
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(AMLBM_ECUDA, std::string("graph capture: ") +
+                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&b->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return fail(AMLBM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+  return AMLBM_OK;
+}
+
+int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune, void* stream,
+                void* workspace, size_t ws_bytes, amlbm_batch** out) {
+  if (!out) return fail(AMLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (inst.empty()) return fail(AMLBM_EINVAL, "need at least one instance");
+  for (size_t i = 0; i < inst.size(); ++i) {
+    const int rc = validate(inst[i], (int)i);
+    if (rc) return rc;
+  }
+  const int storage = inst[0].bc.storage;
+  int tz = 0, tr = 0;
+  if (tune && (tune->tile_z || tune->tile_r)) {
+    tz = tune->tile_z;
+    tr = tune->tile_r;
+    if (!amlbm::tile_supported(storage, tz, tr))
+      return fail(AMLBM_EINVAL, "tile " + std::to_string(tz) + "x" + std::to_string(tr) +
+                                    " is not compiled for this storage (see amlbm_tiles)");
+  } else {
+    pick_tile(storage, inst, &tz, &tr);
+  }
+  amlbm_batch* b = new (std::nothrow) amlbm_batch();
+  if (!b) return fail(AMLBM_ENOMEM, "host allocation failed");
+  b->n = (int)inst.size();
+  b->storage = storage;
+  b->tz = tz;
+  b->tr = tr;
+  b->graph_chunk = tune ? std::max(0, tune->graph_chunk) : 0;
+  if (b->graph_chunk % 2) b->graph_chunk += 1;  // even: a chunk returns to its parity
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (!b->stream) b->graph_chunk = 0;  // the legacy stream cannot be captured
+  b->L = make_layout(inst, storage, tz, tr);
+  if (workspace) {
+    if (ws_bytes < b->L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) {
+      delete b;
+      return fail(AMLBM_ENOMEM, "workspace too small or not 256-byte aligned: need " +
+                                    std::to_string(b->L.total) + " bytes");
+    }
+    b->arena = static_cast<char*>(workspace);
+    b->arena_bytes = ws_bytes;
+  } else {
+    const cudaError_t e = cudaMalloc(&b->arena, b->L.total);
+    if (e != cudaSuccess) {
+      delete b;
+      return fail(AMLBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->owns = true;
+    b->arena_bytes = b->L.total;
+  }
+  const Layout& L = b->L;
+  std::vector<int> tiles;
+  tiles.reserve(L.ntiles);
+  for (int i = 0; i < b->n; ++i) {
+    const amlbm_instance& I = inst[i];
+    InstDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.Nz = I.Nz;
+    d.Nr = I.Nr;
+    d.P = pitch_of(I.Nz);
+    d.wall = I.bc.wall_r;
+    d.axisym = I.bc.axisym;
+    d.src = I.bc.src_mode;
+    d.tiles_z = (I.Nz + tz - 1) / tz;
+    d.tiles_r = (I.Nr + tr - 1) / tr;
+    d.tile_base = (int)tiles.size();
+    d.tau = I.tau;
+    d.G = I.G;
+    d.rho0 = I.rho0;
+    d.gz = I.bc.g_z;
+    d.rho_ref = I.bc.rho_ref;
+    d.f[0] = b->arena + L.f0[i];
+    d.f[1] = b->arena + L.f1[i];
+    d.psi[0] = b->arena + L.p0[i];
+    d.psi[1] = b->arena + L.p1[i];
+    d.rho_out = reinterpret_cast<double*>(b->arena + L.rho[i]);
+    d.uz_out = reinterpret_cast<double*>(b->arena + L.uz[i]);
+    d.ur_out = reinterpret_cast<double*>(b->arena + L.ur[i]);
+    for (int t = 0; t < d.tiles_z * d.tiles_r; ++t) tiles.push_back(i);
+    b->desc.push_back(d);
+    b->sites += (long long)I.Nz * I.Nr;
+  }
+  b->steps.assign(b->n, 0);
+  b->d_desc = reinterpret_cast<InstDesc*>(b->arena + L.desc);
+  b->d_tiles = reinterpret_cast<int*>(b->arena + L.tiles);
+  cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), b->desc.size() * sizeof(InstDesc),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    if (b->owns) cudaFree(b->arena);
+    delete b;
+    return fail(AMLBM_ECUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return AMLBM_OK;
+}
+
+int check_k(const amlbm_batch* b, int k) {
+  if (!b) return fail(AMLBM_EINVAL, "NULL batch");
+  if (k < 0 || k >= b->n) return fail(AMLBM_EINVAL, "instance index out of range");
+  return AMLBM_OK;
+}
+
+// f = f^eq(rho, u) for instance k from device arrays (uz, ur nullable).
+int init_device(amlbm_batch* b, int k, const double* rho, const double* uz, const double* ur) {
+  const InstDesc& d = b->desc[k];
+  const cudaError_t e = amlbm::launch_init(b->storage, b->d_desc, k, d.Nz, d.Nr, rho, uz, ur,
+                                           b->parity, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("init kernel: ") + cudaGetErrorString(e));
+  b->steps[k] = 0;
+  return AMLBM_OK;
+}
+
+int init_host(amlbm_batch* b, int k, const double* rho, const double* uz, const double* ur) {
+  int rc = check_k(b, k);
+  if (rc) return rc;
+  if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
+  const InstDesc& d = b->desc[k];
+  const size_t N = (size_t)d.Nz * d.Nr;
+  double* st = reinterpret_cast<double*>(b->arena + b->L.upload);
+  for (size_t n = 0; n < N; ++n)
+    if (!(rho[n] > 0) || !std::isfinite(rho[n]))
+      return fail(AMLBM_EINVAL, "rho must be positive and finite at every site");
+  AMLBM_CK(cudaMemcpyAsync(st, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (uz) AMLBM_CK(cudaMemcpyAsync(st + N, uz, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (ur) AMLBM_CK(cudaMemcpyAsync(st + 2 * N, ur, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  rc = init_device(b, k, st, uz ? st + N : nullptr, ur ? st + 2 * N : nullptr);
+  if (rc) return rc;
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  return AMLBM_OK;
+}
+
+int macro_for(amlbm_batch* b, int k) {
+  const InstDesc& d = b->desc[k];
+  const int nt = d.tiles_z * d.tiles_r;
+  const cudaError_t e = amlbm::launch_macro(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles, nt,
+                                            d.tile_base, b->parity, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
+  return AMLBM_OK;
+}
+
+int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f) {
+  int rc = check_k(b, k);
+  if (rc) return rc;
+  const InstDesc& d = b->desc[k];
+  const size_t N = (size_t)d.Nz * d.Nr;
+  if (rho || uz || ur) {
+    rc = macro_for(b, k);
+    if (rc) return rc;
+    if (rho) AMLBM_CK(cudaMemcpyAsync(rho, d.rho_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (uz) AMLBM_CK(cudaMemcpyAsync(uz, d.uz_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (ur) AMLBM_CK(cudaMemcpyAsync(ur, d.ur_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  if (f) {
+    double* un = reinterpret_cast<double*>(b->arena + b->L.unpack);
+    const cudaError_t e = amlbm::launch_unpack(b->storage, b->d_desc, k, d.Nz, d.Nr, b->parity, un, b->stream);
+    if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("unpack kernel: ") + cudaGetErrorString(e));
+    AMLBM_CK(cudaMemcpyAsync(f, un, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  return AMLBM_OK;
+}
+
+int diag_host(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out) {
+  int rc = check_k(b, k);
+  if (rc) return rc;
+  if (!out) return fail(AMLBM_EINVAL, "out is NULL");
+  const InstDesc& d = b->desc[k];
+  amlbm_diag_params p;
+  if (dp) p = *dp;
+  else { p.zc = d.Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1; }
+  if (!(p.R > 0) || !(p.rho_l != p.rho_v)) return fail(AMLBM_EINVAL, "diag params: need R > 0, rho_l != rho_v");
+  rc = macro_for(b, k);
+  if (rc) return rc;
+  double* part = reinterpret_cast<double*>(b->arena + b->L.diag_part);
+  double* cols = reinterpret_cast<double*>(b->arena + b->L.diag_cols);
+  double* res = reinterpret_cast<double*>(b->arena + b->L.diag_out);
+  const int nblk = amlbm::diag_blocks(d.Nz, d.Nr);
+  const cudaError_t e = amlbm::launch_diag(b->storage, b->d_desc, k, d.Nz, d.Nr, b->parity, p.zc, p.R,
+                                           p.rho_l, p.rho_v, part, nblk, cols, res, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("diag kernels: ") + cudaGetErrorString(e));
+  double h[16];
+  AMLBM_CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  std::memset(out, 0, sizeof(*out));
+  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
+  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
+  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
+  out->steps = (double)b->steps[k];
+  if (out->bad > 0) return fail(AMLBM_EUNSTABLE, "non-finite or non-positive density at " +
+                                                    std::to_string((long long)out->bad) + " sites");
+  return AMLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amlbm_last_error(void) { return g_err.c_str(); }
+const char* amlbm_version(void) { return "amlbm 0.1 (sm_103a)"; }
+
+int amlbm_tiles(int storage, int* tz, int* tr, int cap) { return amlbm::tile_list(storage, tz, tr, cap); }
+
+size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
+  if (n < 1 || !inst) return 0;
+  std::vector<amlbm_instance> v(inst, inst + n);
+  for (int i = 0; i < n; ++i)
+    if (validate(v[i], i)) return 0;
+  int tz, tr;
+  pick_tile(v[0].bc.storage, v, &tz, &tr);
+  // room for the smallest compiled tile (the most tiles) whatever the tune picks
+  const Layout a = make_layout(v, v[0].bc.storage, tz, tr);
+  const Layout s = make_layout(v, v[0].bc.storage, 32, 8);
+  return std::max(a.total, s.total);
+}
+
+int amlbm_batch_create(int n, const amlbm_instance* inst, const amlbm_tune* tune, void* stream,
+                       void* workspace, size_t workspace_bytes, amlbm_batch** out) {
+  if (n < 1 || !inst) return fail(AMLBM_EINVAL, "need n >= 1 instances");
+  std::vector<amlbm_instance> v(inst, inst + n);
+  return batch_build(v, tune, stream, workspace, workspace_bytes, out);
+}
+
+int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const double* uz, const double* ur) {
+  return init_host(b, k, rho, uz, ur);
+}
+
+int amlbm_batch_step(amlbm_batch* b, int n) {
+  if (!b) return fail(AMLBM_EINVAL, "NULL batch");
+  if (n < 0) return fail(AMLBM_EINVAL, "n must be >= 0");
+  int left = n;
+  if (b->graph_chunk > 0) {
+    while (left >= b->graph_chunk) {
+      int rc = ensure_graph(b, b->parity);
+      if (rc) return rc;
+      AMLBM_CK(cudaGraphLaunch(b->graph[b->parity], b->stream));
+      left -= b->graph_chunk;  // an even chunk leaves the parity unchanged
+    }
+  }
+  const int rc = launch_steps_direct(b, left);
+  if (rc) return rc;
+  for (auto& s : b->steps) s += n;
+  return AMLBM_OK;
+}
+
+int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f) {
+  return read_host(b, k, rho, uz, ur, f);
+}
+
+int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out) {
+  return diag_host(b, k, dp, out);
+}
+
+long long amlbm_batch_sites(const amlbm_batch* b) { return b ? b->sites : 0; }
+
+void amlbm_batch_destroy(amlbm_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  for (auto& g : b->graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (b->owns && b->arena) cudaFree(b->arena);
+  delete b;
+}
+
+// ------------------------------------------------------------- one lattice --
+
+static amlbm_instance one(int Nz, int Nr, double tau, double G, double rho0, const amlbm_bc* bc) {
+  amlbm_instance I;
+  I.Nz = Nz; I.Nr = Nr; I.tau = tau; I.G = G; I.rho0 = rho0;
+  I.bc = bc ? *bc : default_bc();
+  return I;
+}
+
+size_t amlbm_workspace_bytes(int Nz, int Nr, int storage) {
+  amlbm_bc bc = default_bc();
+  bc.storage = storage;
+  amlbm_instance I = one(Nz, Nr, 1.0, -5.0, 1.0, &bc);
+  return amlbm_batch_workspace_bytes(1, &I);
+}
+
+int amlbm_create(int Nz, int Nr, double tau, double G, double rho0, const amlbm_bc* bc,
+                 void* cuda_stream, void* workspace, size_t workspace_bytes, amlbm_ctx** out) {
+  if (!out) return fail(AMLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::vector<amlbm_instance> v{one(Nz, Nr, tau, G, rho0, bc)};
+  amlbm_batch* b = nullptr;
+  const int rc = batch_build(v, nullptr, cuda_stream, workspace, workspace_bytes, &b);
+  if (rc) return rc;
+  amlbm_ctx* c = new (std::nothrow) amlbm_ctx{b};
+  if (!c) { amlbm_batch_destroy(b); return fail(AMLBM_ENOMEM, "host allocation failed"); }
+  *out = c;
+  return AMLBM_OK;
+}
+
+int amlbm_init_fields(amlbm_ctx* c, const double* rho, const double* uz, const double* ur) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  return init_host(c->b, 0, rho, uz, ur);
+}
+
+int amlbm_init_fields_device(amlbm_ctx* c, const double* rho, const double* uz, const double* ur) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
+  return init_device(c->b, 0, rho, uz, ur);
+}
+
+int amlbm_step(amlbm_ctx* c, int n) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  return amlbm_batch_step(c->b, n);
+}
+
+int amlbm_read_fields(amlbm_ctx* c, double* rho, double* uz, double* ur, double* f) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  return read_host(c->b, 0, rho, uz, ur, f);
+}
+
+int amlbm_diagnostics(amlbm_ctx* c, const amlbm_diag_params* dp, amlbm_diag* out) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  return diag_host(c->b, 0, dp, out);
+}
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int Nz, Nr, storage, pad;
+  long long steps;
+  size_t fbytes, pbytes;
+};
+}  // namespace
+
+int amlbm_save_state(amlbm_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return fail(AMLBM_EINVAL, "NULL argument");
+  amlbm_batch* b = c->b;
+  const InstDesc& d = b->desc[0];
+  const size_t plane = (size_t)d.P * d.Nr;
+  const size_t fb = 9 * plane * elem_bytes(b->storage), pb = plane * compute_bytes(b->storage);
+  const size_t need = sizeof(StateHeader) + fb + pb;
+  if (!buf) { *len = need; return AMLBM_OK; }
+  if (*len < need) return fail(AMLBM_EINVAL, "buffer too small: need " + std::to_string(need));
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "AMLBMST1", 8);
+  h.Nz = d.Nz; h.Nr = d.Nr; h.storage = b->storage; h.steps = b->steps[0]; h.fbytes = fb; h.pbytes = pb;
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  AMLBM_CK(cudaMemcpyAsync(p + sizeof(h), d.f[b->parity], fb, cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaMemcpyAsync(p + sizeof(h) + fb, d.psi[b->parity], pb, cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  *len = need;
+  return AMLBM_OK;
+}
+
+int amlbm_load_state(amlbm_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) return fail(AMLBM_EINVAL, "NULL argument");
+  amlbm_batch* b = c->b;
+  const InstDesc& d = b->desc[0];
+  StateHeader h;
+  if (len < sizeof(h)) return fail(AMLBM_EINVAL, "buffer too small");
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t plane = (size_t)d.P * d.Nr;
+  const size_t fb = 9 * plane * elem_bytes(b->storage), pb = plane * compute_bytes(b->storage);
+  if (std::memcmp(h.magic, "AMLBMST1", 8) || h.Nz != d.Nz || h.Nr != d.Nr || h.storage != b->storage ||
+      h.fbytes != fb || h.pbytes != pb || len < sizeof(h) + fb + pb)
+    return fail(AMLBM_EINVAL, "state does not match this context");
+  const char* p = static_cast<const char*>(buf);
+  AMLBM_CK(cudaMemcpyAsync(d.f[b->parity], p + sizeof(h), fb, cudaMemcpyHostToDevice, b->stream));
+  AMLBM_CK(cudaMemcpyAsync(d.psi[b->parity], p + sizeof(h) + fb, pb, cudaMemcpyHostToDevice, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  b->steps[0] = h.steps;
+  return AMLBM_OK;
+}
+
+int amlbm_device_state(amlbm_ctx* c, void** f, void** psi, int* pitch) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  const InstDesc& d = c->b->desc[0];
+  if (f) *f = d.f[c->b->parity];
+  if (psi) *psi = d.psi[c->b->parity];
+  if (pitch) *pitch = d.P;
+  return AMLBM_OK;
+}
+
+void amlbm_destroy(amlbm_ctx* c) {
+  if (!c) return;
+  amlbm_batch_destroy(c->b);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Internal declarations shared by the kernels and the C-ABI host code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace amlbm {
+
+// One lattice of a batch as the kernels see it.  Populations are stored as
+// [9][Nr][P] (z contiguous, row pitch P elements) and psi as [Nr][P]; both come
+// in two copies (ping-pong) selected by the batch-wide parity.
+struct InstDesc {
+  int Nz, Nr, P;
+  int wall, axisym, src;
+  int tiles_z, tiles_r, tile_base;
+  int pad_;
+  double tau, G, rho0, gz, rho_ref;
+  void* f[2];
+  void* psi[2];
+  double* rho_out;  // [Nr][Nz] scratch for read-back and diagnostics
+  double* uz_out;
+  double* ur_out;
+};
+
+// Kernel launchers (defined in amlbm_step.cu).  storage = AMLBM_STORE_*.
+// Every launcher returns the cudaGetLastError() of its launch.
+// The step and macro kernels run CTAs for the flattened tiles
+// [toff, toff + ntiles) of the batch.
+cudaError_t launch_step(int storage, int tz, int tr, const InstDesc* d_desc,
+                        const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
+cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d_desc,
+                         const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
+cudaError_t launch_init(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
+                        const double* rho, const double* uz, const double* ur, int parity,
+                        cudaStream_t s);
+cudaError_t launch_unpack(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
+                          int parity, double* f_out, cudaStream_t s);
+// Diagnostics: partial sums into `partials` (nblk x 8 doubles, plus Nz column
+// radii), then a single-block pass into out[16].
+cudaError_t launch_diag(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
+                        int parity, double zc, double R, double rho_l, double rho_v,
+                        double* partials, int nblk, double* cols, double* out, cudaStream_t s);
+int diag_blocks(int Nz, int Nr);
+bool tile_supported(int storage, int tz, int tr);
+int tile_list(int storage, int* tz, int* tr, int cap);
+size_t step_smem_bytes(int storage, int tz, int tr);
+
+}  // namespace amlbm

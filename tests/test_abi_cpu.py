@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every
+function include/amlbm.h declares, and rejects bad arguments before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1310_1871_gb300 import amlbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "amlbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amlbm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return amlbm.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(amlbm.EXPORTS)
+
+
+def test_version_and_error_string(lib):
+    assert b"sm_103a" in lib.amlbm_version()
+    assert isinstance(lib.amlbm_last_error(), bytes)
+
+
+@pytest.mark.parametrize("Nz,Nr,tau,G,rho0", [
+    (0, 16, 1.0, -5.0, 1.0), (16, 3, 1.0, -5.0, 1.0), (16, 16, 0.5, -5.0, 1.0),
+    (16, 16, 1.0, -7.0, 1.0), (16, 16, 1.0, -5.0, 0.0), (16, 16, float("nan"), -5.0, 1.0)])
+def test_create_rejects_bad_arguments(lib, Nz, Nr, tau, G, rho0):
+    h = ctypes.c_void_p()
+    bc = amlbm.make_bc()
+    rc = lib.amlbm_create(Nz, Nr, tau, G, rho0, ctypes.byref(bc), None, None, 0, ctypes.byref(h))
+    assert rc == amlbm.EINVAL
+    assert h.value is None
+    assert len(lib.amlbm_last_error()) > 0
+
+
+def test_bad_flags_and_tiles_rejected(lib):
+    h = ctypes.c_void_p()
+    for bc in (amlbm.BC(2, 1, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0.0, 1.0),
+               amlbm.BC(0, 1, 5, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 9, 0.0, 1.0)):
+        assert lib.amlbm_create(16, 16, 1.0, -5.0, 1.0, ctypes.byref(bc), None, None, 0,
+                                ctypes.byref(h)) == amlbm.EINVAL
+    inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(32, 16, 1.0, -5.0, 1.0, amlbm.make_bc(storage="f64")))
+    tune = amlbm.Tune(128, 8, 0)  # not compiled for FP64
+    assert lib.amlbm_batch_create(1, inst, ctypes.byref(tune), None, None, 0, ctypes.byref(h)) == amlbm.EINVAL
+    assert b"tile" in lib.amlbm_last_error()
+
+
+def test_tile_lists_and_workspace_sizes(lib):
+    assert (32, 8) in amlbm.tiles("f64") and (128, 8) not in amlbm.tiles("f64")
+    assert (128, 8) in amlbm.tiles("bf16")
+    small = lib.amlbm_workspace_bytes(64, 32, 0)
+    big = lib.amlbm_workspace_bytes(256, 128, 0)
+    half = lib.amlbm_workspace_bytes(256, 128, 3)
+    assert 0 < small < big and half < big
+    # populations (two copies) dominate: 2 x 9 x pitch x Nr x 8 bytes for FP64
+    assert big >= 2 * 9 * 256 * 128 * 8
+    assert lib.amlbm_workspace_bytes(0, 128, 0) == 0
+
+
+def test_workspace_too_small_rejected(lib):
+    h = ctypes.c_void_p()
+    bc = amlbm.make_bc()
+    # a fake (never dereferenced) aligned device address with too few bytes
+    rc = lib.amlbm_create(64, 32, 1.0, -5.0, 1.0, ctypes.byref(bc), None, ctypes.c_void_p(1 << 20), 16,
+                          ctypes.byref(h))
+    assert rc == amlbm.ENOMEM

@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: FP64 storage matches the oracle to a max relative error of 1e-11 after up
+to 1000 steps (f pointwise, rho pointwise, u normwise: max|du| / max|u|).  The
+FP32 form is held to 1e-5 in rho over 1000 steps and the 16-bit shifted forms to
+the bounds stated at their tests.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1310_1871_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1310_1871_gb300 import amlbm  # noqa: E402
+
+WALLS = {0: "freeslip", 1: "noslip"}
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def run_pair(Nz, Nr, steps, fields, tau=1.0, G=-5.0, wall=0, axisym=1, src=0, gz=0.0,
+             storage="f64", tile=None, rho_ref=1.0):
+    rho, uz, ur = fields
+    o = O.Oracle(Nz, Nr, tau=tau, G=G, gz=gz, wall=wall, axisym=axisym, src_mode=src)
+    f_ref = o.run(o.init(rho, uz, ur), steps)
+    spec = amlbm.InstanceSpec(Nz, Nr, tau, G, 1.0, WALLS[wall], bool(axisym),
+                              "link" if src else "local", gz, rho_ref)
+    b = amlbm.Batch([spec], storage=storage, tile=tile)
+    b.init_fields(0, rho, uz, ur)
+    b.step(steps)
+    f_gpu = b.read_f(0)
+    rho_g, uz_g, ur_g = b.read(0)
+    b.close()
+    F = o.fields(f_ref)
+    return f_gpu, f_ref, (rho_g, uz_g, ur_g), F
+
+
+def check_fp64(res, tol=1e-11):
+    f_gpu, f_ref, (rho, uz, ur), F = res
+    assert np.isfinite(f_gpu).all()
+    assert rel(f_gpu, f_ref) < tol
+    assert np.abs(rho / F["rho"] - 1).max() < tol
+    umax = max(np.abs(F["uz"]).max(), np.abs(F["ur"]).max())
+    if umax > 0:
+        assert max(np.abs(uz - F["uz"]).max(), np.abs(ur - F["ur"]).max()) / umax < tol
+
+
+def test_fp64_static_drop_1000_steps():
+    """The static-drop workload: 64 x 32, G = -5, tau = 1, R = 12 at (32, 0), 1000 steps."""
+    check_fp64(run_pair(64, 32, 1000, I.drop(64, 32, 32.0, 12.0)))
+
+
+@pytest.mark.parametrize("wall,src,axisym,gz,tau,G", [
+    (0, 0, 1, 0.0, 0.8, -5.0), (1, 0, 1, 1e-4, 1.0, -4.6), (0, 1, 1, 0.0, 0.9, -5.0),
+    (1, 1, 1, 0.0, 0.7, -4.8), (0, 0, 0, 0.0, 1.0, -5.5), (1, 0, 0, 5e-5, 0.6, 0.0)])
+def test_fp64_flag_combinations(wall, src, axisym, gz, tau, G):
+    fields = I.drop(40, 20, 17.0, 7.0, amps=(0.1,)) if G else I.noisy(40, 20, seed=4)
+    check_fp64(run_pair(40, 20, 200, fields, tau=tau, G=G, wall=wall, axisym=axisym, src=src, gz=gz))
+
+
+@pytest.mark.parametrize("tile", [(32, 8), (64, 8)])
+def test_fp64_ragged_tiles(tile):
+    """Sizes that are not multiples of the tile (ragged tail in z and r, several tiles)."""
+    check_fp64(run_pair(70, 21, 300, I.drop(70, 21, 30.0, 9.0, amps=(0.08,)), tau=0.85, tile=tile))
+
+
+@pytest.mark.parametrize("Nz,Nr", [(1, 64), (3, 4), (5, 9), (33, 4)])
+def test_fp64_degenerate_sizes(Nz, Nr):
+    """Single-column lattice (the flat interface of Table I), minimum Nr and odd sizes."""
+    fields = I.slab(Nz, Nr, Nr / 2, 1.93, 0.16) if Nz == 1 else I.noisy(Nz, Nr, seed=Nz)
+    check_fp64(run_pair(Nz, Nr, 300, fields, tau=0.9))
+
+
+def test_fp64_oscillating_drop_full_size():
+    """The oscillating-drop workload at full size: 256 x 128, R = 40 with 5% P2, tau = 0.8."""
+    check_fp64(run_pair(256, 128, 1000, I.drop(256, 128, 128.0, 40.0, amps=(0.05,)), tau=0.8))
+
+
+def test_fp64_thread_full_size():
+    """The capillary-thread workload: lambda = 200 x 128, R0 = 25, 10% cos perturbation."""
+    check_fp64(run_pair(200, 128, 1000, I.thread(200, 128, 25.0, 0.1)))
+
+
+def test_fp32_static_drop():
+    """FP32 storage and arithmetic stay within 1e-5 of the FP64 oracle in rho over 1000 steps."""
+    _, _, (rho, _, _), F = run_pair(64, 32, 1000, I.drop(64, 32, 32.0, 12.0), storage="f32", tile=(32, 8))
+    err = np.abs(rho / F["rho"] - 1).max()
+    print(f"fp32 rho max rel err {err:.3e}")
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("storage,bound", [("f16", 5e-3), ("bf16", 4e-2)])
+def test_shifted_16bit_storage(storage, bound):
+    """Populations stored as f_i - W_i rho_ref in 16 bits, FP32 arithmetic, rho_ref = 1.
+    Measured max relative error in rho after 1000 steps is printed; the bound is the
+    one this storage form meets (the 1e-4 target needs a finer shift, see the
+    precision study)."""
+    _, _, (rho, _, _), F = run_pair(64, 32, 1000, I.drop(64, 32, 32.0, 12.0), storage=storage,
+                                    tile=(32, 8))
+    err = np.abs(rho / F["rho"] - 1).max()
+    print(f"{storage} rho max rel err {err:.3e}")
+    assert np.isfinite(rho).all() and err < bound
+
+
+def test_batch_equals_single_instances_bitwise():
+    """Uneven instances in one launch give bit-identical results to separate runs."""
+    specs = [amlbm.InstanceSpec(48, 24, 0.9, -5.0), amlbm.InstanceSpec(70, 21, 0.75, -4.7, wall="noslip"),
+             amlbm.InstanceSpec(33, 16, 1.1, -5.3, src="link")]
+    fields = [I.drop(48, 24, 24.0, 8.0, amps=(0.05,)), I.drop(70, 21, 35.0, 9.0),
+              I.drop(33, 16, 16.0, 6.0, amps=(0.02,))]
+    for storage in ("f64", "f32", "bf16"):
+        b = amlbm.Batch(specs, storage=storage, tile=(32, 8))
+        for k, fl in enumerate(fields):
+            b.init_fields(k, *fl)
+        b.step(150)
+        for k, (s, fl) in enumerate(zip(specs, fields)):
+            one = amlbm.Batch([s], storage=storage, tile=(32, 8))
+            one.init_fields(0, *fl)
+            one.step(150)
+            assert np.array_equal(one.read_f(0), b.read_f(k)), (storage, k)
+            one.close()
+        b.close()
+
+
+def test_graph_chunks_equal_direct_launches():
+    s = [amlbm.InstanceSpec(64, 32, 0.9, -5.0)]
+    fl = I.drop(64, 32, 32.0, 10.0, amps=(0.05,))
+    out = []
+    for chunk in (0, 16):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            b = amlbm.Batch(s, storage="f32", graph_chunk=chunk, stream=stream)
+            b.init_fields(0, *fl)
+            b.step(37)
+            out.append(b.read_f(0))
+            b.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_diagnostics_match_oracle():
+    Nz, Nr, zc, R = 64, 32, 32.0, 12.0
+    fl = I.drop(Nz, Nr, zc, R, amps=(0.05,))
+    lat = amlbm.Lattice(Nz, Nr, tau=0.9, G=-5.0)
+    lat.init_fields(*fl)
+    lat.step(200)
+    d = lat.diagnostics(zc=zc, R=R, rho_l=1.93, rho_v=0.16)
+    o = O.Oracle(Nz, Nr, tau=0.9, G=-5.0)
+    f = o.run(o.init(*fl), 200)
+    e = o.diag(f, zc, R, 1.93, 0.16)
+    for k in ("mass2d", "mass3d", "momz3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out", "dp", "sumS"):
+        scale = max(abs(e[k]), 1e-12)
+        assert abs(d[k] - e[k]) <= 1e-10 * scale + 1e-15, (k, d[k], e[k])
+    assert d["bad"] == 0 and d["steps"] == 200
+    lat.close()
+
+
+def test_diagnostics_flag_unstable_state():
+    lat = amlbm.Lattice(16, 8, tau=1.0, G=-5.0)
+    rho = torch.ones(8, 16, dtype=torch.float64, device="cuda")
+    rho[3, 5] = -1.0
+    lat.init_fields_device(rho)
+    d = lat.diagnostics(check=False)
+    assert d["bad"] == 1
+    with pytest.raises(amlbm.AmlbmError) as e:
+        lat.diagnostics()
+    assert e.value.code == amlbm.EUNSTABLE
+    lat.close()
+
+
+def test_save_load_state_roundtrip():
+    fl = I.drop(40, 20, 20.0, 7.0, amps=(0.05,))
+    lat = amlbm.Lattice(40, 20, tau=0.9, G=-5.0, storage="f32")
+    lat.init_fields(*fl)
+    lat.step(30)
+    state = lat.save_state()
+    lat.step(40)
+    a = lat.read_f()
+    lat.load_state(state)
+    lat.step(40)
+    assert np.array_equal(lat.read_f(), a)
+    lat.close()
+
+
+def test_device_init_equals_host_init():
+    fl = I.drop(40, 20, 20.0, 7.0)
+    a = amlbm.Lattice(40, 20)
+    a.init_fields(*fl)
+    b = amlbm.Lattice(40, 20)
+    b.init_fields_device(*(torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in fl))
+    assert np.array_equal(a.read_f(), b.read_f())
+    a.close()
+    b.close()
+
+
+def test_batch_sweep_sampled_against_oracle():
+    """The 64-drop batch sweep at full size (FP64 storage), 20 steps; three instances
+    (smallest, largest, one oscillating) are checked against the oracle."""
+    inst = I.batch_sweep(64)
+    specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
+    b = amlbm.Batch(specs, storage="f64")
+    for k, x in enumerate(inst):
+        b.init_fields(k, *x.make_fields())
+    b.step(20)
+    sizes = [x.Nz * x.Nr for x in inst]
+    picks = {int(np.argmin(sizes)), int(np.argmax(sizes)), 1}
+    for k in picks:
+        x = inst[k]
+        o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+        f_ref = o.run(o.init(*x.make_fields()), 20)
+        assert rel(b.read_f(k), f_ref) < 1e-12, k
+    b.close()
