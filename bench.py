@@ -1,0 +1,327 @@
+"""Throughput of the axisymmetric Shan-Chen LBM step on GB300 (MLUPS and HBM roofline).
+
+Workload: the batched sweep of 64 independent drops (R ~ U[10, 60], grid 4R x 2R,
+G ~ U[-5.5, -4.6], tau ~ U[0.6, 1.2], l = 2 amplitude ~ U[0, 0.08] on half of
+them, seeds 1234 + k), populations stored as bfloat16 shifted by W_i rho_ref with
+FP32 arithmetic, all instances in one kernel launch per timestep.
+
+One bench step = one timestep of every site of every instance.  The state
+(~28 MB) fits in L2, so L2 is flushed (a 256 MB write) before every timed step
+and each step is timed alone with CUDA events on the launching stream: the
+figure is the HBM-fed rate, a lower bound on a run that stays L2-resident.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own 64-instance batch (seeds offset by
+64 x rank): independent problems, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1310_1871_gb300 import inputs as I  # noqa: E402
+
+METRIC = "MLUPS & % of HBM roofline, mixed-precision/batched vs plain FP64 at same error"
+UNIT = "MLUPS"
+STORAGE = "bf16"
+BYTES_PER_LU = {"f64": 18 * 8 + 2 * 8, "f32": 18 * 4 + 2 * 4, "f16": 18 * 2 + 2 * 4, "bf16": 18 * 2 + 2 * 4}
+WORKLOAD = ("batched sweep: 64 axisymmetric drops, R~U[10,60], grid 4R x 2R, G~U[-5.5,-4.6], "
+            "tau~U[0.6,1.2], a2~U[0,0.08] on odd instances, seeds 1234+k")
+
+
+def config(sites, storage=STORAGE, tile=None):
+    return {"workload": WORKLOAD, "instances": 64, "sites_per_step": int(sites),
+            "storage": f"{storage} shifted by W_i*rho_ref" if storage in ("f16", "bf16") else storage,
+            "arithmetic": "f64" if storage == "f64" else "f32",
+            "tile": list(tile) if tile else None,
+            "l2": "flushed before every timed step (256 MB write); state 28 MB < L2",
+            "launch": "one kernel per timestep for all 64 instances"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed loop runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_batch(storage, rank, tile=None, graph_chunk=0, stream=None):
+    from paper_1310_1871_gb300 import amlbm
+    inst = I.batch_sweep(64, seed0=1234 + 64 * rank)
+    specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
+    b = amlbm.Batch(specs, storage=storage, tile=tile, graph_chunk=graph_chunk, stream=stream)
+    for k, x in enumerate(inst):
+        b.init_fields(k, *x.make_fields())
+    return b, inst
+
+
+def time_steps(torch, b, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms) of `steps` timesteps, L2 flushed before each."""
+    for _ in range(warmup):
+        flush.add_(1)
+        b.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s in range(steps):
+        flush.add_(1)  # 256 MB read-modify-write on the same stream evicts the state from L2
+        ev[s][0].record(stream)
+        b.step(1)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(c) for a, c in ev]
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        b, inst = build_batch(STORAGE, rank, stream=stream)
+        sites = b.sites
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            times = time_steps(torch, b, args.steps, args.warmup, flush, stream)
+            wall = time.perf_counter() - t0
+        total_ms = float(sum(times))
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.barrier()
+            total_ms = float(t.item())
+        mlups = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+        avg_ms = total_ms / args.steps
+        hbm, kind = peaks()
+        achieved = BYTES_PER_LU[STORAGE] * sites / (avg_ms * 1e-3) / 1e9
+
+        # end to end through the public C ABI: host fields in pinned memory are
+        # uploaded every step, one timestep runs, and every instance's diagnostics
+        # (FP64 reductions) are read back to the host
+        e2e_steps = max(3, min(args.steps, 20))
+        pinned = []
+        for x in inst:
+            fl = x.make_fields()
+            pinned.append([torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in fl])
+        h2d = sum(a.nbytes for fl in pinned for a in fl)
+        d2h = 64 * 16 * 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for k, fl in enumerate(pinned):
+                b.init_fields(k, *fl)
+            b.step(1)
+            for k, x in enumerate(inst):
+                b.diagnostics(k, zc=x.zc, R=x.R, rho_l=x.rho_l, rho_v=x.rho_v, check=False)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_val = world * sites * e2e_steps / e2e_s / 1e6
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_val = world * sites * e2e_steps / float(t.item()) / 1e6
+        b.close()
+
+        # the same workload in the other storage forms (plain FP64 is the
+        # parity form; FP32 the unshifted single-precision form)
+        compare = {}
+        if rank == 0 and not args.no_compare:
+            for st in ("f64", "f32"):
+                bb, _ = build_batch(st, rank, stream=stream)
+                tt = time_steps(torch, bb, min(args.steps, 200), 3, flush, stream)
+                compare[st] = round(bb.sites * len(tt) / (sum(tt) * 1e-3) / 1e6, 1)
+                bb.close()
+            compare[STORAGE] = round(mlups / world, 1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(seconds=args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(mlups, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config(sites),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": None,
+                         "peak_kind": kind, "bytes_per_lu": BYTES_PER_LU[STORAGE],
+                         "kernel": "step_kernel<__nv_bfloat16>"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h),
+                    "path": "amlbm_batch_init_fields x64 (pinned host) + amlbm_batch_step(1) + "
+                            "amlbm_batch_diagnostics x64"},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "compare_mlups": compare or None,
+            "wall_s_timed_loop": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle, single-threaded, stepping instances of the same workload in
+    turn (one instance-timestep per step) until about `seconds` of work is done."""
+    import oracle as O
+    inst = I.batch_sweep(64)
+    states = {}
+    done_sites = 0
+    elapsed = 0.0
+    k = 0
+    n_steps = 0
+    while elapsed < seconds:
+        x = inst[k % 64]
+        if k % 64 not in states:
+            o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+            states[k % 64] = (o, o.init(*x.make_fields()))
+        o, f = states[k % 64]
+        t1 = time.perf_counter()
+        f = o.run(f, 1)
+        done_t = time.perf_counter() - t1
+        states[k % 64] = (o, f)
+        done_sites += x.Nz * x.Nr
+        n_steps += 1
+        k += 1
+        elapsed += done_t
+    return {"value": round(done_sites / elapsed / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} instance-timesteps of the 64-drop sweep ({done_sites} site updates, "
+                      f"{elapsed:.1f} s), FP64, one thread"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step advances one instance of the sweep
+    (in turn) by one timestep on the host; MLUPS over the timed steps."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    inst = I.batch_sweep(64)
+    states = []
+    for x in inst:
+        o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+        states.append([o, o.init(*x.make_fields())])
+    for s in range(args.warmup):
+        o, f = states[s % 64]
+        states[s % 64][1] = o.run(f, 1)
+    sites = 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        o, f = states[(args.warmup + s) % 64]
+        states[(args.warmup + s) % 64][1] = o.run(f, 1)
+        sites += inst[(args.warmup + s) % 64].Nz * inst[(args.warmup + s) % 64].Nr
+    el = time.perf_counter() - t0
+    val = sites / el / 1e6
+    line = {
+        "metric": METRIC, "value": round(val, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / max(args.steps, 1) * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference", "config": config(sum(x.Nz * x.Nr for x in inst), "f64"),
+        "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one instance-timestep of the 64-drop sweep per step, instances in "
+                                   f"turn ({sites} site updates in {el:.1f} s), FP64 oracle, one thread"},
+        "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="amlbm", choices=["amlbm", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64/FP32 comparison runs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

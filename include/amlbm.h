@@ -64,8 +64,15 @@ extern "C" {
 /* Storage of the populations; arithmetic is FP64 for F64 and FP32 otherwise. */
 #define AMLBM_STORE_F64 0
 #define AMLBM_STORE_F32 1
-#define AMLBM_STORE_F16 2  /* IEEE half of f_i - W_i rho_ref */
-#define AMLBM_STORE_BF16 3 /* bfloat16 of f_i - W_i rho_ref */
+#define AMLBM_STORE_F16 2  /* IEEE half of f_i - W_i s (s: see AMLBM_SHIFT_*) */
+#define AMLBM_STORE_BF16 3 /* bfloat16 of f_i - W_i s */
+
+/* What the FP32 and 16-bit forms store: f_i - W_i s.  FP64 storage is never shifted. */
+#define AMLBM_SHIFT_DEFAULT 0 /* NONE for FP32, LOCAL for FP16 / BF16 */
+#define AMLBM_SHIFT_NONE 1    /* s = 0 */
+#define AMLBM_SHIFT_GLOBAL 2  /* s = rho_ref, one constant per lattice */
+#define AMLBM_SHIFT_LOCAL 3   /* s = -rho0 ln(1 - psi/rho0) of the site's stored psi: the
+                                 site's own density recovered from psi, no extra bytes */
 
 /* Boundary and model options of one lattice. */
 typedef struct amlbm_bc {
@@ -73,8 +80,10 @@ typedef struct amlbm_bc {
   int axisym;     /* 1: axisymmetric sources and force (default); 0: planar 2D Shan-Chen */
   int src_mode;   /* AMLBM_SRC_* */
   int storage;    /* AMLBM_STORE_* (a batch uses the storage of its first instance) */
+  int shift;      /* AMLBM_SHIFT_* */
+  int reserved;   /* must be 0 */
   double g_z;     /* body acceleration along +z (force rho g_z), Sec. III.1 */
-  double rho_ref; /* shift of the 16-bit storage forms */
+  double rho_ref; /* constant of AMLBM_SHIFT_GLOBAL */
 } amlbm_bc;
 
 /* Parameters of the diagnostics (where to measure the drop or thread). */
@@ -113,8 +122,8 @@ size_t amlbm_workspace_bytes(int Nz, int Nr, int storage);
 
 /* Create a lattice of Nz x Nr sites with relaxation time tau (nu = (tau - 1/2)/3),
  * Shan-Chen coupling G and pseudopotential scale rho0.  bc may be NULL (defaults:
- * free-slip, axisymmetric, departure-site source, FP64 storage, g_z = 0,
- * rho_ref = 1).  Requires Nz >= 1, Nr >= 4, tau > 1/2, rho0 > 0, G >= -6.5
+ * free-slip, axisymmetric, departure-site source, FP64 storage, default
+ * shift, g_z = 0, rho_ref = 1).  Requires Nz >= 1, Nr >= 4, tau > 1/2, rho0 > 0, G >= -6.5
  * (the paper's stability limit is G >= -6, Sec. II.D).  cuda_stream is a
  * cudaStream_t.  workspace: see "Memory and ownership". */
 int amlbm_create(int Nz, int Nr, double tau, double G, double rho0, const amlbm_bc* bc,

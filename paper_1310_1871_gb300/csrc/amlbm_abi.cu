@@ -47,32 +47,40 @@ amlbm_bc default_bc() {
   b.axisym = 1;
   b.src_mode = AMLBM_SRC_LOCAL;
   b.storage = AMLBM_STORE_F64;
+  b.shift = AMLBM_SHIFT_DEFAULT;
+  b.reserved = 0;
   b.g_z = 0.0;
   b.rho_ref = 1.0;
   return b;
 }
 
-// Tile choice when the caller gives none: the largest compiled tile that still
-// yields two CTAs per SM over the whole batch, else the smallest tile.
+// Tile choice when the caller gives none: the first shape of a preference
+// list (fastest first on the 64-drop sweep) that still gives every SM two
+// CTAs over the whole batch, else the smallest tile.
 void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* tz, int* tr) {
-  int cz[16], cr[16];
-  const int n = amlbm::tile_list(storage, cz, cr, 16);
-  int best = -1;
-  long long best_area = -1;
+  static const int pref64[][2] = {{58, 8}, {26, 8}};
+  static const int pref32[][2] = {{26, 16}, {58, 8}, {32, 16}, {32, 8}};
+  const bool f64 = storage == AMLBM_STORE_F64;
+  const int n = f64 ? 2 : 4;
   for (int c = 0; c < n; ++c) {
+    const int z = f64 ? pref64[c][0] : pref32[c][0], r = f64 ? pref64[c][1] : pref32[c][1];
     long long tiles = 0;
-    for (const auto& I : inst)
-      tiles += (long long)((I.Nz + cz[c] - 1) / cz[c]) * ((I.Nr + cr[c] - 1) / cr[c]);
-    const long long area = (long long)cz[c] * cr[c];
-    if (tiles >= 2 * 152 && area > best_area) { best = c; best_area = area; }
+    for (const auto& I : inst) tiles += (long long)((I.Nz + z - 1) / z) * ((I.Nr + r - 1) / r);
+    if (tiles >= 2 * 152) { *tz = z; *tr = r; return; }
   }
-  if (best < 0) {
-    best = 0;
-    for (int c = 1; c < n; ++c)
-      if ((long long)cz[c] * cr[c] < (long long)cz[best] * cr[best]) best = c;
+  *tz = 32;
+  *tr = 8;
+}
+
+// Shift code the kernels use: 0 none, 1 global rho_ref, 2 local (from psi).
+int resolve_shift(const amlbm_bc& bc) {
+  if (bc.storage == AMLBM_STORE_F64) return 0;
+  switch (bc.shift) {
+    case AMLBM_SHIFT_NONE: return 0;
+    case AMLBM_SHIFT_GLOBAL: return 1;
+    case AMLBM_SHIFT_LOCAL: return 2;
+    default: return bc.storage == AMLBM_STORE_F32 ? 0 : 2;
   }
-  *tz = cz[best];
-  *tr = cr[best];
 }
 
 int validate(const amlbm_instance& I, int idx) {
@@ -91,6 +99,10 @@ int validate(const amlbm_instance& I, int idx) {
     return fail(AMLBM_EINVAL, w + "bad src_mode");
   if (I.bc.storage < AMLBM_STORE_F64 || I.bc.storage > AMLBM_STORE_BF16)
     return fail(AMLBM_EINVAL, w + "bad storage");
+  if (I.bc.shift < AMLBM_SHIFT_DEFAULT || I.bc.shift > AMLBM_SHIFT_LOCAL)
+    return fail(AMLBM_EINVAL, w + "bad shift");
+  if (I.bc.storage == AMLBM_STORE_F64 && I.bc.shift > AMLBM_SHIFT_NONE)
+    return fail(AMLBM_EINVAL, w + "FP64 storage is not shifted");
   if (!std::isfinite(I.bc.g_z) || !std::isfinite(I.bc.rho_ref))
     return fail(AMLBM_EINVAL, w + "g_z and rho_ref must be finite");
   return AMLBM_OK;
@@ -253,6 +265,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.wall = I.bc.wall_r;
     d.axisym = I.bc.axisym;
     d.src = I.bc.src_mode;
+    d.shift = resolve_shift(I.bc);
     d.tiles_z = (I.Nz + tz - 1) / tz;
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
@@ -401,12 +414,13 @@ size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
   std::vector<amlbm_instance> v(inst, inst + n);
   for (int i = 0; i < n; ++i)
     if (validate(v[i], i)) return 0;
-  int tz, tr;
-  pick_tile(v[0].bc.storage, v, &tz, &tr);
-  // room for the smallest compiled tile (the most tiles) whatever the tune picks
-  const Layout a = make_layout(v, v[0].bc.storage, tz, tr);
-  const Layout s = make_layout(v, v[0].bc.storage, 32, 8);
-  return std::max(a.total, s.total);
+  // room for whichever compiled tile the tune picks (the tile list grows with
+  // the number of tiles)
+  int tz[32], tr[32];
+  const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, tz, tr, 32));
+  size_t need = 0;
+  for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);
+  return need;
 }
 
 int amlbm_batch_create(int n, const amlbm_instance* inst, const amlbm_tune* tune, void* stream,

@@ -13,7 +13,7 @@ struct InstDesc {
   int Nz, Nr, P;
   int wall, axisym, src;
   int tiles_z, tiles_r, tile_base;
-  int pad_;
+  int shift;  // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
   double tau, G, rho0, gz, rho_ref;
   void* f[2];
   void* psi[2];

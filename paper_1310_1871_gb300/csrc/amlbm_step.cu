@@ -42,41 +42,55 @@ __host__ __device__ constexpr int opp_(int i) {
        : i == 5 ? 7 : i == 7 ? 5 : i == 6 ? 8 : 6;
 }
 
-// Storage codecs.  The 16-bit forms hold f_i - W_i rho_ref.
+// Storage codecs: plain conversion between the stored element and the
+// arithmetic type.  The shift W_i s of the FP32 / 16-bit forms is applied by
+// the callers (decode: f = q + W_i s; encode: q = f - W_i s).
 template <class S> struct Store;
 template <> struct Store<double> {
   using C = double;
-  static __device__ __forceinline__ C load(const double* p, C) { return *p; }
-  static __device__ __forceinline__ void store(double* p, C v, C) { *p = v; }
-  static __device__ __forceinline__ C round(C v, C) { return v; }
+  static __device__ __forceinline__ C to(double v) { return v; }
+  static __device__ __forceinline__ double from(C v) { return v; }
 };
 template <> struct Store<float> {
   using C = float;
-  static __device__ __forceinline__ C load(const float* p, C) { return *p; }
-  static __device__ __forceinline__ void store(float* p, C v, C) { *p = v; }
-  static __device__ __forceinline__ C round(C v, C) { return v; }
+  static __device__ __forceinline__ C to(float v) { return v; }
+  static __device__ __forceinline__ float from(C v) { return v; }
 };
 template <> struct Store<__half> {
   using C = float;
-  static __device__ __forceinline__ C load(const __half* p, C s) { return __half2float(*p) + s; }
-  static __device__ __forceinline__ void store(__half* p, C v, C s) { *p = __float2half_rn(v - s); }
-  static __device__ __forceinline__ C round(C v, C s) { return __half2float(__float2half_rn(v - s)) + s; }
+  static __device__ __forceinline__ C to(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half from(C v) { return __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
   using C = float;
-  static __device__ __forceinline__ C load(const __nv_bfloat16* p, C s) {
-    return __bfloat162float(*p) + s;
-  }
-  static __device__ __forceinline__ void store(__nv_bfloat16* p, C v, C s) {
-    *p = __float2bfloat16_rn(v - s);
-  }
-  static __device__ __forceinline__ C round(C v, C s) {
-    return __bfloat162float(__float2bfloat16_rn(v - s)) + s;
-  }
+  static __device__ __forceinline__ C to(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 from(C v) { return __float2bfloat16_rn(v); }
 };
 
+// exp / log / reciprocal of the arithmetic type.  The FP32 forms use the SFU
+// approximations (relative error ~1e-7, far below the storage rounding).
 __device__ __forceinline__ double exp_c(double x) { return exp(x); }
-__device__ __forceinline__ float exp_c(float x) { return expf(x); }
+__device__ __forceinline__ float exp_c(float x) { return __expf(x); }
+__device__ __forceinline__ double rcp_c(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_c(float x) { return __frcp_rn(x); }
+
+// Shift s of a site from its stored psi: 0 (none), rho_ref (global), or the
+// density recovered from psi, -rho0 ln(1 - psi/rho0) (local).  Writer and
+// reader evaluate it from the same stored psi with the same non-contracted
+// operations, so both see the same s bit for bit.
+__device__ __forceinline__ double shift_base(int mode, double psi, double inv_rho0, double rho0,
+                                             double rref) {
+  (void)psi; (void)inv_rho0; (void)rho0;
+  return mode == 1 ? rref : 0.0;  // FP64 storage is never shifted locally
+}
+__device__ __forceinline__ float shift_base(int mode, float psi, float inv_rho0, float rho0,
+                                            float rref) {
+  if (mode == 2) {
+    const float q = __fsub_rn(1.0f, __fmul_rn(psi, inv_rho0));
+    return __fmul_rn(-rho0, __logf(q));
+  }
+  return mode == 1 ? rref : 0.0f;
+}
 
 __device__ __forceinline__ int wrapz(int k, int Nz) {
   k %= Nz;
@@ -90,27 +104,33 @@ __device__ __forceinline__ int reflect_row(int j, int Nr) {
   return j < 0 ? 0 : (j >= Nr ? Nr - 1 : j);
 }
 
-// Isotropic 4th-order first derivative, Sec. II.D Eq. forthorder_firstderivativex:
-// (1/36) sum_i c_i,AX (8 phi(x + c_i) - phi(x + 2 c_i)); AX = 1 along r, 0 along z.
-// p points at x in a row-major tile whose rows (r) are `stride` apart.
-template <int AX, class C>
-__device__ __forceinline__ C iso(const C* p, int stride) {
-  C s = C(0);
-#pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    const int c = AX ? cr_(i) : cz_(i);
-    if (c != 0) {
-      const C a = p[cr_(i) * stride + cz_(i)];
-      const C b = p[2 * cr_(i) * stride + 2 * cz_(i)];
-      s += c > 0 ? (C(8) * a - b) : -(C(8) * a - b);
-    }
-  }
-  return s * C(1.0 / 36.0);
+// Isotropic 4th-order first derivatives, Sec. II.D Eq. forthorder_firstderivativex:
+//   d_a phi(x) = (1/36) sum_i c_ia (8 phi(x + c_i) - phi(x + 2 c_i)).
+// p points at x in a row-major tile whose rows (r) are `st` apart.  The terms
+// are added in z-mirror pairs (c_1, c_3), (c_5, c_6), (c_8, c_7) so that a
+// field mirrored in z gives an exactly mirrored derivative: without this, the
+// rounding of the FP32 forms carries a net axial bias every step and a drop
+// drifts along the axis.
+template <class C>
+__device__ __forceinline__ C link8(const C* p, int dz, int dr, int st) {
+  return C(8) * p[dr * st + dz] - p[2 * dr * st + 2 * dz];
+}
+template <class C>
+__device__ __forceinline__ C iso_r(const C* p, int st) {
+  const C a = link8(p, 0, 1, st) - link8(p, 0, -1, st);
+  const C b = (link8(p, 1, 1, st) + link8(p, -1, 1, st)) - (link8(p, 1, -1, st) + link8(p, -1, -1, st));
+  return (a + b) * C(1.0 / 36.0);
+}
+template <class C>
+__device__ __forceinline__ C iso_z(const C* p, int st) {
+  const C a = link8(p, 1, 0, st) - link8(p, -1, 0, st);
+  const C b = (link8(p, 1, 1, st) - link8(p, -1, 1, st)) + (link8(p, 1, -1, st) - link8(p, -1, -1, st));
+  return (a + b) * C(1.0 / 36.0);
 }
 // 1D 4th-order central difference with element step `step` (Sec. II.D).
 template <class C>
 __device__ __forceinline__ C d1(const C* p, int step) {
-  return (-p[2 * step] + C(8) * p[step] - C(8) * p[-step] + p[-2 * step]) * C(1.0 / 12.0);
+  return (C(8) * (p[step] - p[-step]) - (p[2 * step] - p[-2 * step])) * C(1.0 / 12.0);
 }
 
 template <class C>
@@ -119,16 +139,10 @@ __device__ __forceinline__ C feq(int i, C rho, C vz, C vr) {
   const C vv = vz * vz + vr * vr;
   return C(w_(i)) * rho * (C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * vv);
 }
-
-// BGK collision of population i loaded from p, towards f^eq(rho, u^eq) (Eq. lbm2d).
-template <class S>
-__device__ __forceinline__ typename Store<S>::C collide(int i, const S* p, typename Store<S>::C rho,
-                                                        typename Store<S>::C vz, typename Store<S>::C vr,
-                                                        typename Store<S>::C omega,
-                                                        typename Store<S>::C rref) {
-  using C = typename Store<S>::C;
-  const C f = Store<S>::load(p, C(w_(i)) * rref);
-  return f + (feq(i, rho, vz, vr) - f) * omega;
+// rho = sum_i f_i, added in z-mirror pairs.
+template <class C>
+__device__ __forceinline__ C moment0(const C* f) {
+  return (f[0] + (f[2] + f[4])) + ((f[1] + f[3]) + ((f[5] + f[6]) + (f[7] + f[8])));
 }
 // h_i = W_i (S + (c_iz H_z + c_ir H_r) / c_s^2), Eq. condition_h.
 template <class C>
@@ -136,8 +150,44 @@ __device__ __forceinline__ C source(int i, C S_, C Hz, C Hr) {
   return C(w_(i)) * (S_ + C(3) * (C(cz_(i)) * Hz + C(cr_(i)) * Hr));
 }
 
-// Tile geometry: halos of psi (7), d_r psi (5), 1D d_r psi (z 5, r 3),
-// macroscopic fields (3) and sources (1).
+// The nine equilibria with f^eq_0 = rho - sum_{i>0} f^eq_i: the same value as
+// W_0 rho (1 - 1.5 u^2) in exact arithmetic, but the collision then conserves
+// mass to rounding.  With the directly evaluated f^eq_0 the FP32-rounded
+// weights do not sum to 1 and the FP32 forms gain mass every step (a 1.5e-5
+// drift over 1000 steps of the static drop, and a 1e-4 density error at the
+// interface).
+template <class C>
+__device__ __forceinline__ void equilibrium(C rho, C vz, C vr, C* fe) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) fe[i] = feq(i, rho, vz, vr);
+  fe[0] = rho - ((fe[2] + fe[4]) + ((fe[1] + fe[3]) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
+}
+// The nine sources with h_0 = S - sum_{i>0} h_i, so that sum_i h_i = S to
+// rounding (the App. A zeroth moment) in every precision.
+template <class C>
+__device__ __forceinline__ void sources(C S_, C Hz, C Hr, C* h) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) h[i] = source(i, S_, Hz, Hr);
+  h[0] = S_ - ((h[2] + h[4]) + ((h[1] + h[3]) + ((h[5] + h[6]) + (h[7] + h[8]))));
+}
+
+// 256 threads per CTA.  Every 2D region of a tile is walked as warp tasks: a
+// task is a 32-wide segment of one row, so each warp reads and writes one
+// contiguous run of a row and branches that depend on the row never diverge.
+constexpr int NT = 256, NWARP = NT / 32;
+
+template <int ROWS, int W, class F>
+__device__ __forceinline__ void for_tile(F&& body) {
+  constexpr int SEGS = (W + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  for (int t = threadIdx.x >> 5; t < ROWS * SEGS; t += NWARP) {
+    const int lr = t / SEGS, lc = (t - lr * SEGS) * 32 + lane;
+    if (lc < W) body(lr, lc);
+  }
+}
+
+// Tile geometry.  Halos: psi 7, isotropic d_r psi 5, 1D d_r psi (z 5, r 3),
+// rho and u 3, collided populations and sources 1.
 template <class C, int BZ, int BR>
 struct Geo {
   static constexpr int HP = 7, HD = 5, HF = 3;
@@ -147,107 +197,154 @@ struct Geo {
   static constexpr int FZ = BZ + 2 * HF, FR = BR + 2 * HF;
   static constexpr int SZ = BZ + 2, SR = BR + 2;
   static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER, nF = FZ * FR, nS = SZ * SR;
-  // S, H_z, H_r reuse the psi / derivative region, which is dead by then.
-  static_assert(nP + nD + nE >= 3 * nS, "source tiles must fit in the stencil region");
-  static constexpr size_t bytes = sizeof(C) * (size_t)(nP + nD + nE + 5 * nF);
+  // region A holds psi and its derivatives, later the sources S, H_z, H_r
+  static constexpr int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
+  static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
+  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(nA + 3 * nF + 9 * nS);
 };
 
-constexpr int NT = 256;
+struct Tile {
+  int inst, k0, j0;
+};
 
-// Stages 0-2: psi tile, derivative tiles, and rho, u, u^eq on the tile plus 3.
-template <class S, int BZ, int BR>
-__device__ void macro_tile(const InstDesc& D, int k0, int j0, const S* __restrict__ fin,
-                           const typename Store<S>::C* __restrict__ psin,
-                           typename Store<S>::C* sm) {
+__device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_inst, int toff, int BZ,
+                                        int BR) {
+  Tile t;
+  const int b = blockIdx.x + toff;
+  t.inst = tile_inst[b];
+  const int tb = descs[t.inst].tile_base, tz = descs[t.inst].tiles_z;
+  const int l = b - tb;
+  t.k0 = (l % tz) * BZ;
+  t.j0 = (l / tz) * BR;
+  return t;
+}
+
+// The fused update of one tile (READBACK: only rho and u of the tile, for
+// read-back and diagnostics).
+template <class S, int BZ, int BR, bool READBACK>
+__global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ descs,
+                                                 const int* __restrict__ tile_inst, int toff,
+                                                 int parity) {
   using C = typename Store<S>::C;
   using G = Geo<C, BZ, BR>;
-  const int Nz = D.Nz, Nr = D.Nr, P = D.P;
-  const size_t plane = (size_t)P * Nr;
-  C* sPsi = sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* colmap = reinterpret_cast<int*>(smem_raw);
+  int* rowmap = colmap + G::PZ;
+  C* base = reinterpret_cast<C*>(smem_raw + G::int_bytes);
+  C* sPsi = base;
   C* sDr = sPsi + G::nP;
   C* sD1 = sDr + G::nD;
-  C* sRho = sD1 + G::nE;
+  C* sS = base;  // after stage 2
+  C* sHz = sS + G::nS;
+  C* sHr = sHz + G::nS;
+  C* sRho = base + G::nA;
   C* sUz = sRho + G::nF;
   C* sUr = sUz + G::nF;
-  C* sVz = sUr + G::nF;
-  C* sVr = sVz + G::nF;
-  const int tid = threadIdx.x;
+  C* sFs = sUr + G::nF;
 
-  for (int idx = tid; idx < G::nP; idx += NT) {
-    const int lr = idx / G::PZ, lc = idx - lr * G::PZ;
-    const int j = reflect_row(j0 - G::HP + lr, Nr);
-    const int k = wrapz(k0 - G::HP + lc, Nz);
-    sPsi[idx] = psin[(size_t)j * P + k];
-  }
-  __syncthreads();
+  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const InstDesc& D = descs[T.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  const size_t plane = (size_t)P * Nr;
+  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
+  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
   const bool ax = D.axisym != 0;
+  const int shift = D.shift;
+  const C tau = C(D.tau), omega = C(1) / tau, Gc = C(D.G), gz = C(D.gz), rho0 = C(D.rho0),
+          rref = C(D.rho_ref), gfac = -(Gc / C(2)) * C(1.0 / 9.0), inv_rho0 = rcp_c(rho0);
+
+  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
+  for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
+  __syncthreads();
+
+  // Stage 0: psi with ghost cells (periodic z, even mirror in r).
+  for_tile<G::PR, G::PZ>([&](int lr, int lc) {
+    sPsi[lr * G::PZ + lc] = psin[(size_t)rowmap[lr] * P + colmap[lc]];
+  });
+  __syncthreads();
+
+  // Stage 1: isotropic d_r psi (tile + 5) and 1D d_r psi (z: tile + 5, r: tile + 3).
   if (ax) {
-    for (int idx = tid; idx < G::nD; idx += NT) {
-      const int lr = idx / G::DZ, lc = idx - lr * G::DZ;
-      sDr[idx] = iso<1>(sPsi + (lr + G::HP - G::HD) * G::PZ + (lc + G::HP - G::HD), G::PZ);
-    }
-    for (int idx = tid; idx < G::nE; idx += NT) {
-      const int lr = idx / G::EZ, lc = idx - lr * G::EZ;
-      sD1[idx] = d1(sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HD), G::PZ);
-    }
+    for_tile<G::DR, G::DZ>([&](int lr, int lc) {
+      sDr[lr * G::DZ + lc] = iso_r(sPsi + (lr + G::HP - G::HD) * G::PZ + (lc + G::HP - G::HD), G::PZ);
+    });
+    for_tile<G::ER, G::EZ>([&](int lr, int lc) {
+      sD1[lr * G::EZ + lc] = d1(sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HD), G::PZ);
+    });
     __syncthreads();
   }
 
-  const C tau = C(D.tau), Gc = C(D.G), gz = C(D.gz), rref = C(D.rho_ref);
-  for (int idx = tid; idx < G::nF; idx += NT) {
-    const int lr = idx / G::FZ, lc = idx - lr * G::FZ;
+  // Stage 2 (tile + 3): moments, Shan-Chen force (Eq. scforce), axisymmetric
+  // force (Eq. scAxisExtra, c_s^4 = 1/9), body force, u (Eq. uhydro); on the
+  // tile + 1 also u^eq (Eq. ueq) and the BGK collision of all nine populations,
+  // kept in shared memory for the streaming stage.
+  for_tile<G::FR, G::FZ>([&](int lr, int lc) {
     const int j = j0 - G::HF + lr;
-    if (j < 0 || j >= Nr) continue;
-    const int k = wrapz(k0 - G::HF + lc, Nz);
-    const S* fp = fin + (size_t)j * P + k;
-    C rho = C(0), jz = C(0), jr = C(0);
+    if (j < 0 || j >= Nr) return;
+    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+    const bool srow = lr >= 2 && lr < G::FR - 2;
+    {
+      const C* p = sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HF);
+      const C psi = p[0];
+      const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
+      const S* fp = fin + (size_t)j * P + colmap[lc + G::HP - G::HF];
+      C f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const C fi = Store<S>::load(fp + i * plane, C(w_(i)) * rref);
-      rho += fi;
-      if (cz_(i) > 0) jz += fi;
-      if (cz_(i) < 0) jz -= fi;
-      if (cr_(i) > 0) jr += fi;
-      if (cr_(i) < 0) jr -= fi;
-    }
-    const C* p = sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HF);
-    const C psi = p[0];
-    // Shan-Chen force, Eq. scforce: -G psi sum_i W_i psi(x + c_i) c_i.
-    C sz = C(0), sr = C(0);
+      for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fp[i * plane]) + C(w_(i)) * sb;
+      // moments and the Shan-Chen neighbour sums in z-mirror pairs (see iso_r)
+      const C rho = moment0(f);
+      const C jz = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+      const C jr = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
+      const int Z = G::PZ;
+      const C sz = C(1.0 / 9.0) * (p[1] - p[-1]) +
+                   C(1.0 / 36.0) * ((p[Z + 1] - p[Z - 1]) + (p[-Z + 1] - p[-Z - 1]));
+      const C sr = C(1.0 / 9.0) * (p[Z] - p[-Z]) +
+                   C(1.0 / 36.0) * ((p[Z + 1] - p[-Z + 1]) + (p[Z - 1] - p[-Z - 1]));
+      C Fz = -Gc * psi * sz, Fr = -Gc * psi * sr;
+      if (ax) {
+        const C* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
+        const C Drr = iso_r(dr, G::DZ);
+        const C Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
+        const C g = gfac * psi * inv_r;
+        Fz += g * Dzr;
+        Fr += g * (Drr - dr[0] * inv_r);
+      }
+      Fz += rho * gz;
+      const C inv_rho = rcp_c(rho);
+      const int fi = lr * G::FZ + lc;
+      sRho[fi] = rho;
+      sUz[fi] = (jz + C(0.5) * Fz) * inv_rho;
+      sUr[fi] = (jr + C(0.5) * Fr) * inv_rho;
+      if (!READBACK && srow && lc >= 2 && lc < G::FZ - 2) {
+        const C vz = (jz + tau * Fz) * inv_rho, vr = (jr + tau * Fr) * inv_rho;
+        C fe[9];
+        equilibrium(rho, vz, vr, fe);
+        C* out = sFs + (lr - 2) * G::SZ + (lc - 2);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-      const C q = C(w_(i)) * p[cr_(i) * G::PZ + cz_(i)];
-      if (cz_(i) > 0) sz += q;
-      if (cz_(i) < 0) sz -= q;
-      if (cr_(i) > 0) sr += q;
-      if (cr_(i) < 0) sr -= q;
+        for (int i = 0; i < 9; ++i) out[i * G::nS] = f[i] + (fe[i] - f[i]) * omega;
+      }
     }
-    C Fz = -Gc * psi * sz, Fr = -Gc * psi * sr;
-    if (ax) {
-      // Eq. scAxisExtra with c_s^4 = 1/9: d_rr psi = iso d_r of iso d_r psi,
-      // d_zr psi = 1D d_z of 1D d_r psi.
-      const C r = C(j) + C(0.5);
-      const C* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
-      const C Dr = dr[0];
-      const C Drr = iso<1>(dr, G::DZ);
-      const C Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
-      const C g = -(Gc / C(2)) * C(1.0 / 9.0) * psi;
-      Fz += g * Dzr / r;
-      Fr += g * (Drr / r - Dr / (r * r));
-    }
-    Fz += rho * gz;
-    sRho[idx] = rho;
-    sUz[idx] = (jz + Fz / C(2)) / rho;
-    sUr[idx] = (jr + Fr / C(2)) / rho;
-    sVz[idx] = (jz + tau * Fz) / rho;
-    sVr[idx] = (jr + tau * Fr) / rho;
-  }
+  });
   __syncthreads();
-  if (ax) {
-    // Ghost rows of u (depth 2): u_z even and u_r odd about the axis; about the
-    // outer wall u_r odd and u_z even (free-slip) or odd (no-slip).
-    for (int idx = tid; idx < G::nF; idx += NT) {
-      const int lr = idx / G::FZ, lc = idx - lr * G::FZ;
+
+  if (READBACK) {
+    for_tile<BR, BZ>([&](int lr, int lc) {
+      const int j = j0 + lr, k = k0 + lc;
+      if (j >= Nr || k >= Nz) return;
+      const int fi = (lr + G::HF) * G::FZ + (lc + G::HF);
+      const size_t o = (size_t)j * Nz + k;
+      D.rho_out[o] = double(sRho[fi]);
+      D.uz_out[o] = double(sUz[fi]);
+      D.ur_out[o] = double(sUr[fi]);
+    });
+    return;
+  }
+
+  // Ghost rows of u (depth 2) on tiles that touch the axis or the wall: u_z even
+  // and u_r odd about the axis; about the outer wall u_r odd and u_z even
+  // (free-slip) or odd (no-slip).
+  if (ax && (j0 < G::HF || j0 + BR + G::HF > Nr)) {
+    for_tile<G::FR, G::FZ>([&](int lr, int lc) {
       const int j = j0 - G::HF + lr;
       int m;
       C sgz;
@@ -258,160 +355,95 @@ __device__ void macro_tile(const InstDesc& D, int k0, int j0, const S* __restric
         m = 2 * Nr - 1 - j;
         sgz = D.wall == AMLBM_WALL_NOSLIP ? C(-1) : C(1);
       } else {
-        continue;
+        return;
       }
       const int src = (m - (j0 - G::HF)) * G::FZ + lc;
-      sUz[idx] = sgz * sUz[src];
-      sUr[idx] = -sUr[src];
-    }
+      sUz[lr * G::FZ + lc] = sgz * sUz[src];
+      sUr[lr * G::FZ + lc] = -sUr[src];
+    });
     __syncthreads();
   }
-}
 
-template <class S, int BZ, int BR>
-__global__ void __launch_bounds__(NT) step_kernel(const InstDesc* __restrict__ descs,
-                                                  const int* __restrict__ tile_inst, int toff,
-                                                  int parity) {
-  using C = typename Store<S>::C;
-  using G = Geo<C, BZ, BR>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int b = blockIdx.x + toff;
-  const int inst = tile_inst[b];
-  const InstDesc& D = descs[inst];
-  const int t = b - D.tile_base;
-  const int tzi = t % D.tiles_z, tri = t / D.tiles_z;
-  const int k0 = tzi * BZ, j0 = tri * BR;
-  const int Nz = D.Nz, Nr = D.Nr, P = D.P;
-  const size_t plane = (size_t)P * Nr;
-  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
-  S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
-  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
-  C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
-
-  macro_tile<S, BZ, BR>(D, k0, j0, fin, psin, sm);
-
-  C* sRho = sm + G::nP + G::nD + G::nE;
-  C* sUz = sRho + G::nF;
-  C* sUr = sUz + G::nF;
-  C* sVz = sUr + G::nF;
-  C* sVr = sVz + G::nF;
-  C* sS = sm;
-  C* sHz = sS + G::nS;
-  C* sHr = sHz + G::nS;
-  const bool ax = D.axisym != 0;
-  const C tau = C(D.tau), omega = C(1) / tau, rho0 = C(D.rho0), rref = C(D.rho_ref);
-  const int tid = threadIdx.x;
-
-  // Stage 3: velocity gradients and axisymmetric sources on the tile plus 1
-  // (App. A: S = -rho u_r / r, H_z, H_r of Eqs. corr_z_ns_eqn, corr_r_ns_eqn,
-  // mu = rho c_s^2 (tau - 1/2)).
-  for (int idx = tid; idx < G::nS; idx += NT) {
-    const int lr = idx / G::SZ, lc = idx - lr * G::SZ;
+  // Stage 3 (tile + 1): velocity gradients and the sources of App. A,
+  // S = -rho u_r / r, H_z, H_r with mu = rho c_s^2 (tau - 1/2), added to the
+  // collided populations (the whole h_i, or half of it for the link average).
+  const bool link = D.src == AMLBM_SRC_LINK;
+  for_tile<G::SR, G::SZ>([&](int lr, int lc) {
     const int j = j0 - 1 + lr;
-    C S_ = C(0), Hz = C(0), Hr = C(0);
-    if (ax && j >= 0 && j < Nr) {
-      const int fi = (lr + 2) * G::FZ + (lc + 2);
-      const C druz = iso<1>(sUz + fi, G::FZ);
-      const C dzur = iso<0>(sUr + fi, G::FZ);
-      const C drur = iso<1>(sUr + fi, G::FZ);
-      const C rho = sRho[fi], uz = sUz[fi], ur = sUr[fi];
-      const C r = C(j) + C(0.5);
-      const C mu = rho * (tau - C(0.5)) / C(3);
-      S_ = -rho * ur / r;
-      Hz = (mu * (druz + dzur) - rho * ur * uz) / r;
-      Hr = (C(2) * mu * (drur - ur / r) - rho * ur * ur) / r;
+    if (j < 0 || j >= Nr) return;
+    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+    {
+      const int si = lr * G::SZ + lc;
+      C S_ = C(0), Hz = C(0), Hr = C(0);
+      if (ax) {
+        const int fi = (lr + 2) * G::FZ + (lc + 2);
+        const C druz = iso_r(sUz + fi, G::FZ);
+        const C dzur = iso_z(sUr + fi, G::FZ);
+        const C drur = iso_r(sUr + fi, G::FZ);
+        const C rho = sRho[fi], uz = sUz[fi], ur = sUr[fi];
+        const C mu = rho * (tau - C(0.5)) * C(1.0 / 3.0);
+        S_ = -rho * ur * inv_r;
+        Hz = (mu * (druz + dzur) - rho * ur * uz) * inv_r;
+        Hr = (C(2) * mu * (drur - ur * inv_r) - rho * ur * ur) * inv_r;
+        const C hw = link ? C(0.5) : C(1);
+        C h[9];
+        sources(S_, Hz, Hr, h);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] += hw * h[i];
+      }
+      sS[si] = S_;
+      sHz[si] = Hz;
+      sHr[si] = Hr;
     }
-    sS[idx] = S_;
-    sHz[idx] = Hz;
-    sHr[idx] = Hr;
-  }
+  });
   __syncthreads();
 
-  // Stage 4: pull streaming of the collided populations with the boundary maps.
-  // Rows away from the axis and the wall take every population from x - c_i in
-  // the same direction (compile-time indices); rows 0 and Nr-1 apply the
-  // reflection maps.  A warp covers one row, so the two paths never diverge.
-  const bool link = D.src == AMLBM_SRC_LINK;
+  // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
+  // population comes from x - c_i in the same direction; rows 0 and Nr-1 apply
+  // the reflection maps (a warp covers one row, so the paths never diverge).
+  // Then psi of the new state and the shifted store.
+  S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
+  C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
-  for (int idx = tid; idx < BZ * BR; idx += NT) {
-    const int lr = idx / BZ, lc = idx - lr * BZ;
+  for_tile<BR, BZ>([&](int lr, int lc) {
     const int j = j0 + lr, k = k0 + lc;
-    if (j >= Nr || k >= Nz) continue;
+    if (j >= Nr || k >= Nz) return;
     const bool edge = (j == 0) || (j == Nr - 1);
-    const int di = (lr + 1) * G::SZ + (lc + 1);
-    C rho_new = C(0);
+    {
+      C fn[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      int sl = lr - cr_(i), sc = lc - cz_(i), sj = j - cr_(i), sk = k - cz_(i), ii = i;
-      if (edge) {
-        if (cr_(i) > 0 && j == 0) {  // arrives through the axis: specular reflection
-          sl = lr; sj = 0; ii = mirror_(i);
-        } else if (cr_(i) < 0 && j == Nr - 1) {  // arrives through the outer wall
-          sl = lr; sj = Nr - 1;
-          if (noslip) { sc = lc; sk = k; ii = opp_(i); }
-          else { ii = mirror_(i); }
-        }
-      }
-      if (sk < 0) sk += Nz; else if (sk >= Nz) sk -= Nz;
-      const int fi = (sl + G::HF) * G::FZ + (sc + G::HF);
-      const int si = (sl + 1) * G::SZ + (sc + 1);
-      const S* src = fin + (size_t)sj * P + sk;
-      C post, hsrc;
-      if (!edge) {
-        post = collide<S>(i, src + i * plane, sRho[fi], sVz[fi], sVr[fi], omega, rref);
-        hsrc = source<C>(i, sS[si], sHz[si], sHr[si]);
-      } else {
-        post = C(0); hsrc = C(0);
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-          if (q == ii) {
-            post = collide<S>(q, src + q * plane, sRho[fi], sVz[fi], sVr[fi], omega, rref);
-            hsrc = source<C>(q, sS[si], sHz[si], sHr[si]);
+      for (int i = 0; i < 9; ++i) {
+        int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
+        if (edge) {
+          if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
+            sl = lr + 1; ii = mirror_(i);
+          } else if (cr_(i) < 0 && j == Nr - 1) {  // through the outer wall
+            sl = lr + 1;
+            if (noslip) { sc = lc + 1; ii = opp_(i); }
+            else { ii = mirror_(i); }
           }
+        }
+        fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
       }
-      const C fnew = link ? post + C(0.5) * (hsrc + source<C>(i, sS[di], sHz[di], sHr[di]))
-                          : post + hsrc;
-      const C sh = C(w_(i)) * rref;
-      Store<S>::store(fout + i * plane + (size_t)j * P + k, fnew, sh);
-      rho_new += Store<S>::round(fnew, sh);
+      if (link) {
+        const int di = (lr + 1) * G::SZ + (lc + 1);
+        C h[9];
+        sources(sS[di], sHz[di], sHr[di], h);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fn[i] += C(0.5) * h[i];
+      }
+      const C rho = moment0(fn);
+      const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
+      const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
+      S* o = fout + (size_t)j * P + k;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+      psout[(size_t)j * P + k] = psi;
     }
-    psout[(size_t)j * P + k] = rho0 * (C(1) - exp_c(-rho_new / rho0));
-  }
+  });
 }
 
-// Density and hydrodynamic velocity of the current state (read-back and diagnostics).
-template <class S, int BZ, int BR>
-__global__ void __launch_bounds__(NT) macro_kernel(const InstDesc* __restrict__ descs,
-                                                   const int* __restrict__ tile_inst, int toff,
-                                                   int parity) {
-  using C = typename Store<S>::C;
-  using G = Geo<C, BZ, BR>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int b = blockIdx.x + toff;
-  const int inst = tile_inst[b];
-  const InstDesc& D = descs[inst];
-  const int t = b - D.tile_base;
-  const int k0 = (t % D.tiles_z) * BZ, j0 = (t / D.tiles_z) * BR;
-  macro_tile<S, BZ, BR>(D, k0, j0, static_cast<const S*>(D.f[parity]),
-                        static_cast<const C*>(D.psi[parity]), sm);
-  C* sRho = sm + G::nP + G::nD + G::nE;
-  C* sUz = sRho + G::nF;
-  C* sUr = sUz + G::nF;
-  for (int idx = threadIdx.x; idx < BZ * BR; idx += NT) {
-    const int lr = idx / BZ, lc = idx - lr * BZ;
-    const int j = j0 + lr, k = k0 + lc;
-    if (j >= D.Nr || k >= D.Nz) continue;
-    const int fi = (lr + G::HF) * G::FZ + (lc + G::HF);
-    const size_t o = (size_t)j * D.Nz + k;
-    D.rho_out[o] = double(sRho[fi]);
-    D.uz_out[o] = double(sUz[fi]);
-    D.ur_out[o] = double(sUr[fi]);
-  }
-}
-
-// f = f^eq(rho, u) (no force shift) and psi of the stored state.
+// f = f^eq(rho, u) (no force shift) and psi of the new state.
 template <class S>
 __global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const double* rho_in,
                             const double* uz_in, const double* ur_in, int parity) {
@@ -422,19 +454,18 @@ __global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const 
   const int j = n / D.Nz, k = n - j * D.Nz;
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   S* f = static_cast<S*>(D.f[parity]);
-  C* psi = static_cast<C*>(D.psi[parity]);
-  const C rho = C(rho_in[n]);
+  C* psi_out = static_cast<C*>(D.psi[parity]);
+  const C rho_i = C(rho_in[n]);
   const C uz = uz_in ? C(uz_in[n]) : C(0), ur = ur_in ? C(ur_in[n]) : C(0);
-  const C rref = C(D.rho_ref), rho0 = C(D.rho0);
-  C rs = C(0);
+  const C rho0 = C(D.rho0), rref = C(D.rho_ref);
+  C fe[9];
+  equilibrium(rho_i, uz, ur, fe);
+  const C rho = moment0(fe);
+  const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
+  const C sb = shift_base(D.shift, psi, rcp_c(rho0), rho0, rref);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const C v = feq(i, rho, uz, ur);
-    const C sh = C(w_(i)) * rref;
-    Store<S>::store(f + i * plane + o, v, sh);
-    rs += Store<S>::round(v, sh);
-  }
-  psi[o] = rho0 * (C(1) - exp_c(-rs / rho0));
+  for (int i = 0; i < 9; ++i) f[i * plane + o] = Store<S>::from(fe[i] - C(w_(i)) * sb);
+  psi_out[o] = psi;
 }
 
 template <class S>
@@ -448,9 +479,10 @@ __global__ void unpack_kernel(const InstDesc* __restrict__ descs, int inst, int 
   const int j = n / D.Nz, k = n - j * D.Nz;
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   const S* f = static_cast<const S*>(D.f[parity]);
+  const C psi = static_cast<const C*>(D.psi[parity])[o];
+  const C sb = shift_base(D.shift, psi, rcp_c(C(D.rho0)), C(D.rho0), C(D.rho_ref));
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    out[(size_t)i * N + n] = double(Store<S>::load(f + i * plane + o, C(w_(i)) * C(D.rho_ref)));
+  for (int i = 0; i < 9; ++i) out[(size_t)i * N + n] = double(Store<S>::to(f[i * plane + o]) + C(w_(i)) * sb);
 }
 
 // ----------------------------------------------------------- diagnostics --
@@ -566,52 +598,50 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_kernel(const InstDesc* __r
   }
 }
 
-template <class S, int BZ, int BR>
-cudaError_t launch_step_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
-                          cudaStream_t s) {
+template <class S, int BZ, int BR, bool RB>
+cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
+                     cudaStream_t s) {
   using C = typename Store<S>::C;
   constexpr size_t smem = Geo<C, BZ, BR>::bytes;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(step_kernel<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(macro_kernel<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, RB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     attr = true;
   }
-  step_kernel<S, BZ, BR><<<ntiles, NT, smem, s>>>(d, ti, toff, parity);
-  return cudaGetLastError();
-}
-template <class S, int BZ, int BR>
-cudaError_t launch_macro_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
-                           cudaStream_t s) {
-  using C = typename Store<S>::C;
-  constexpr size_t smem = Geo<C, BZ, BR>::bytes;
-  cudaFuncSetAttribute(macro_kernel<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  macro_kernel<S, BZ, BR><<<ntiles, NT, smem, s>>>(d, ti, toff, parity);
+  lbm_kernel<S, BZ, BR, RB><<<ntiles, NT, smem, s>>>(d, ti, toff, parity);
   return cudaGetLastError();
 }
 
 // Tile shapes compiled for each storage form.
 struct TileEntry { int storage, tz, tr; };
+#define AMLBM_TILES_16(ST) \
+  {ST, 32, 8}, {ST, 64, 8}, {ST, 58, 8}, {ST, 58, 16}, {ST, 26, 16}, {ST, 32, 16}, {ST, 122, 8}
 constexpr TileEntry kTiles[] = {
-    {AMLBM_STORE_F64, 32, 8},  {AMLBM_STORE_F64, 64, 8},
-    {AMLBM_STORE_F32, 32, 8},  {AMLBM_STORE_F32, 64, 8},  {AMLBM_STORE_F32, 128, 8},  {AMLBM_STORE_F32, 64, 16},
-    {AMLBM_STORE_F16, 32, 8},  {AMLBM_STORE_F16, 64, 8},  {AMLBM_STORE_F16, 128, 8},  {AMLBM_STORE_F16, 64, 16},
-    {AMLBM_STORE_BF16, 32, 8}, {AMLBM_STORE_BF16, 64, 8}, {AMLBM_STORE_BF16, 128, 8}, {AMLBM_STORE_BF16, 64, 16},
+    {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 64, 8}, {AMLBM_STORE_F64, 58, 8}, {AMLBM_STORE_F64, 26, 8},
+    AMLBM_TILES_16(AMLBM_STORE_F32), AMLBM_TILES_16(AMLBM_STORE_F16), AMLBM_TILES_16(AMLBM_STORE_BF16),
 };
+#undef AMLBM_TILES_16
 
 template <class S>
 cudaError_t dispatch(bool macro, int tz, int tr, const InstDesc* d, const int* ti, int nt, int toff,
                      int par, cudaStream_t s) {
   if (nt <= 0) return cudaSuccess;
-#define AMLBM_TILE(TZ, TR)                                                       \
-  if (tz == TZ && tr == TR)                                                      \
-    return macro ? launch_macro_t<S, TZ, TR>(d, ti, nt, toff, par, s)            \
-                 : launch_step_t<S, TZ, TR>(d, ti, nt, toff, par, s);
+#define AMLBM_TILE(TZ, TR)                                                \
+  if (tz == TZ && tr == TR)                                               \
+    return macro ? launch_t<S, TZ, TR, true>(d, ti, nt, toff, par, s)     \
+                 : launch_t<S, TZ, TR, false>(d, ti, nt, toff, par, s);
   AMLBM_TILE(32, 8)
   AMLBM_TILE(64, 8)
-  if constexpr (!std::is_same<S, double>::value) {
-    AMLBM_TILE(128, 8)
-    AMLBM_TILE(64, 16)
+  AMLBM_TILE(58, 8)
+  if constexpr (std::is_same<S, double>::value) {
+    AMLBM_TILE(26, 8)
+  } else {
+    AMLBM_TILE(58, 16)
+    AMLBM_TILE(26, 16)
+    AMLBM_TILE(32, 16)
+    AMLBM_TILE(122, 8)
   }
 #undef AMLBM_TILE
   return cudaErrorInvalidValue;
@@ -649,8 +679,10 @@ int tile_list(int storage, int* tz, int* tr, int cap) {
 size_t step_smem_bytes(int storage, int tz, int tr) {
   const size_t c = storage == AMLBM_STORE_F64 ? 8 : 4;
   const int nP = (tz + 14) * (tr + 14), nD = (tz + 10) * (tr + 10), nE = (tz + 10) * (tr + 6);
-  const int nF = (tz + 6) * (tr + 6);
-  return c * (size_t)(nP + nD + nE + 5 * nF);
+  const int nF = (tz + 6) * (tr + 6), nS = (tz + 2) * (tr + 2);
+  const int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
+  const size_t ib = ((size_t)(tz + 14 + tr + 14) * 4 + 15) / 16 * 16;
+  return ib + c * (size_t)(nA + 3 * nF + 9 * nS);
 }
 
 cudaError_t launch_step(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,

@@ -49,8 +49,9 @@ def test_create_rejects_bad_arguments(lib, Nz, Nr, tau, G, rho0):
 
 def test_bad_flags_and_tiles_rejected(lib):
     h = ctypes.c_void_p()
-    for bc in (amlbm.BC(2, 1, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0.0, 1.0),
-               amlbm.BC(0, 1, 5, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 9, 0.0, 1.0)):
+    for bc in (amlbm.BC(2, 1, 0, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0, 0, 0.0, 1.0),
+               amlbm.BC(0, 1, 5, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 9, 0, 0, 0.0, 1.0),
+               amlbm.BC(0, 1, 0, 2, 7, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 0, 3, 0, 0.0, 1.0)):
         assert lib.amlbm_create(16, 16, 1.0, -5.0, 1.0, ctypes.byref(bc), None, None, 0,
                                 ctypes.byref(h)) == amlbm.EINVAL
     inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(32, 16, 1.0, -5.0, 1.0, amlbm.make_bc(storage="f64")))
@@ -61,7 +62,7 @@ def test_bad_flags_and_tiles_rejected(lib):
 
 def test_tile_lists_and_workspace_sizes(lib):
     assert (32, 8) in amlbm.tiles("f64") and (128, 8) not in amlbm.tiles("f64")
-    assert (128, 8) in amlbm.tiles("bf16")
+    assert (122, 8) in amlbm.tiles("bf16") and (26, 16) in amlbm.tiles("f32")
     small = lib.amlbm_workspace_bytes(64, 32, 0)
     big = lib.amlbm_workspace_bytes(256, 128, 0)
     half = lib.amlbm_workspace_bytes(256, 128, 3)
