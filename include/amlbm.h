@@ -161,6 +161,26 @@ int amlbm_device_state(amlbm_ctx* ctx, void** f, void** psi, int* pitch);
 
 void amlbm_destroy(amlbm_ctx* ctx);
 
+/* amlbm_diagnostics without any device allocation (the paper has no
+ * counterpart: this is a library facility).  For callers that must not
+ * allocate device memory when they ask for diagnostics, e.g. a monitoring hook
+ * inside an application whose caching allocator owns the device memory (a raw
+ * cudaMalloc may then fail, and cudaMalloc / cudaFree synchronise the whole
+ * device).  Same arguments, result and errors as amlbm_diagnostics; the
+ * context is the input and *out the output.  The reduction scratch is a fixed
+ * array of the library's own device memory (131,200 bytes, reserved on every
+ * device that loads the library and held until the process exits), so:
+ *   - lattices with Nz > AMLBM_NOALLOC_MAX_NZ are rejected with AMLBM_EINVAL;
+ *   - the first call on a device looks up the array's address on that device
+ *     (cudaGetSymbolAddress); make that first call, with the context's device
+ *     current, before any stream capture;
+ *   - every call shares the array: each call writes every entry it reads, so
+ *     nothing needs clearing, but calls that overlap on the GPU (several host
+ *     threads or streams of one device) race and must be serialised.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define AMLBM_NOALLOC_MAX_NZ 8192
+int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* out);
+
 /* ---------------------------------------------------------------- batches */
 
 /* One independent lattice of a batch. */

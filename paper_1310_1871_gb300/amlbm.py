@@ -64,7 +64,7 @@ EXPORTS = [
     "amlbm_device_state", "amlbm_destroy", "amlbm_tiles", "amlbm_batch_workspace_bytes",
     "amlbm_batch_create", "amlbm_batch_init_fields", "amlbm_batch_step", "amlbm_batch_read",
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
-    "amlbm_version",
+    "amlbm_version", "amlbm_diagnostics_noalloc",
 ]
 
 
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         lib.amlbm_batch_destroy.restype = None
         lib.amlbm_last_error.restype = ctypes.c_char_p
         lib.amlbm_version.restype = ctypes.c_char_p
+        lib.amlbm_diagnostics_noalloc.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
         _lib = lib
         return lib
 

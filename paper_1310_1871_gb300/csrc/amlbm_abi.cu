@@ -595,3 +595,28 @@ void amlbm_destroy(amlbm_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------- helpers for other entry points --
+namespace amlbm {
+
+int ctx_info(amlbm_ctx* c, CtxInfo* out) {
+  if (!c || !c->b || !out) return fail(AMLBM_EINVAL, "NULL context");
+  const amlbm_batch* b = c->b;
+  out->d_desc = b->d_desc;
+  out->Nz = b->desc[0].Nz;
+  out->Nr = b->desc[0].Nr;
+  out->storage = b->storage;
+  out->parity = b->parity;
+  out->steps = b->steps[0];
+  out->stream = b->stream;
+  return AMLBM_OK;
+}
+
+int ctx_readback(amlbm_ctx* c) {
+  if (!c || !c->b) return fail(AMLBM_EINVAL, "NULL context");
+  return macro_for(c->b, 0);
+}
+
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+}  // namespace amlbm

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace amlbm {
 
 // One lattice of a batch as the kernels see it.  Populations are stored as
@@ -44,5 +46,23 @@ int diag_blocks(int Nz, int Nr);
 bool tile_supported(int storage, int tz, int tr);
 int tile_list(int storage, int* tz, int* tr, int cap);
 size_t step_smem_bytes(int storage, int tz, int tr);
+
+// Access to a lattice context for entry points defined outside the ABI file
+// (amlbm_abi.cu implements these).
+struct CtxInfo {
+  const InstDesc* d_desc;  // device descriptor array (one instance)
+  int Nz, Nr, storage, parity;
+  long long steps;
+  cudaStream_t stream;
+};
+}  // namespace amlbm
+struct amlbm_ctx;
+namespace amlbm {
+int ctx_info(amlbm_ctx* ctx, CtxInfo* out);
+// Enqueue the read-back kernel (rho and u of the current state into the
+// context's own buffers).
+int ctx_readback(amlbm_ctx* ctx);
+// Record a message for amlbm_last_error() and return code.
+int set_error(int code, const std::string& msg);
 
 }  // namespace amlbm
