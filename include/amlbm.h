@@ -181,6 +181,50 @@ void amlbm_destroy(amlbm_ctx* ctx);
 #define AMLBM_NOALLOC_MAX_NZ 8192
 int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* out);
 
+/* ---------------------------------------------------------- differentiation */
+
+/* Objectives of the differentiable runs (both linear in rho inside J). */
+#define AMLBM_OBJ_A2SQ 0 /* J = a2(T)^2, a2 = 5/(4 pi R^5) sum 2 pi r phi ((z - zc)^2 - r^2/2) */
+#define AMLBM_OBJ_NECK 1 /* J = sqrt(2 sum_j r_j phi(kstar, j)): the radius of column kstar */
+
+/* A differentiable run: the initial density is a shape-perturbed drop
+ *   rho = rho_v + (rho_l - rho_v)/2 (1 - tanh((d - R_s)/w)),
+ *   R_s(theta) = R (1 + sum_m amps[m] P_{l0+m}(cos theta)),
+ * d and theta measured from (zc, 0); f = f^eq(rho, 0); T timesteps; then J.
+ * phi = (rho - rho_v)/(rho_l - rho_v). */
+typedef struct amlbm_adjoint_problem {
+  int T;           /* timesteps (>= 1) */
+  int ckpt_every;  /* steps between stored states (>= 1); memory ~ (T/ckpt + ckpt) states */
+  int objective;   /* AMLBM_OBJ_* */
+  int l0;          /* Legendre degree of amps[0] */
+  int n_amps;      /* 0..32 */
+  int kstar;       /* column of AMLBM_OBJ_NECK */
+  double zc, R, w, rho_l, rho_v;
+  double obj_R;    /* R of the a2 normalisation */
+  const double* amps; /* host array of n_amps amplitudes */
+} amlbm_adjoint_problem;
+
+/* Device bytes amlbm_adjoint needs for this context and problem (0 if invalid). */
+size_t amlbm_adjoint_workspace_bytes(amlbm_ctx* ctx, const amlbm_adjoint_problem* p);
+
+/* Hand-written discrete adjoint of the run above (SURVEY-named form (3); the paper
+ * differentiates nothing): J and dJ/dG, dJ/dtau, dJ/d(amps) (n_amps values).
+ * The forward run stores the state every ckpt_every steps; the backward sweep
+ * recomputes each segment and applies the transposed step (inverse streaming,
+ * adjoint collision and sources, transposed gradient and force stencils with the
+ * mirror ghosts folded back) from the last step to the first.  Parameter
+ * gradients accumulate in FP64.  Needs FP64 or FP32 storage without shift and the
+ * departure-site source (AMLBM_SRC_LOCAL).  Overwrites the context's state.
+ * workspace: device memory of amlbm_adjoint_workspace_bytes() bytes, or NULL
+ * (then the library allocates and frees it).  Synchronises. */
+int amlbm_adjoint(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* workspace,
+                  size_t workspace_bytes, double* J, double* dJ_dG, double* dJ_dtau,
+                  double* dJ_damps);
+
+/* J of the same run without the adjoint (for finite differences).  Overwrites the
+ * context's state.  Synchronises. */
+int amlbm_objective(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, double* J);
+
 /* ---------------------------------------------------------------- batches */
 
 /* One independent lattice of a batch. */

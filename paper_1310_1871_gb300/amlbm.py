@@ -54,6 +54,17 @@ class InstanceC(ctypes.Structure):
                 ("G", ctypes.c_double), ("rho0", ctypes.c_double), ("bc", BC)]
 
 
+class AdjointProblem(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("objective", ctypes.c_int),
+                ("l0", ctypes.c_int), ("n_amps", ctypes.c_int), ("kstar", ctypes.c_int),
+                ("zc", ctypes.c_double), ("R", ctypes.c_double), ("w", ctypes.c_double),
+                ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double), ("obj_R", ctypes.c_double),
+                ("amps", ctypes.POINTER(ctypes.c_double))]
+
+
+OBJECTIVE = {"a2sq": 0, "neck": 1}
+
+
 class Tune(ctypes.Structure):
     _fields_ = [("tile_z", ctypes.c_int), ("tile_r", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
 
@@ -64,7 +75,8 @@ EXPORTS = [
     "amlbm_device_state", "amlbm_destroy", "amlbm_tiles", "amlbm_batch_workspace_bytes",
     "amlbm_batch_create", "amlbm_batch_init_fields", "amlbm_batch_step", "amlbm_batch_read",
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
-    "amlbm_version", "amlbm_diagnostics_noalloc",
+    "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
+    "amlbm_objective",
 ]
 
 
@@ -112,6 +124,11 @@ def load(build_if_missing: bool = True):
         lib.amlbm_last_error.restype = ctypes.c_char_p
         lib.amlbm_version.restype = ctypes.c_char_p
         lib.amlbm_diagnostics_noalloc.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
+        AP = ctypes.POINTER(AdjointProblem)
+        lib.amlbm_adjoint_workspace_bytes.argtypes = [vp, AP]
+        lib.amlbm_adjoint_workspace_bytes.restype = sz
+        lib.amlbm_adjoint.argtypes = [vp, AP, vp, sz, dp, dp, dp, dp]
+        lib.amlbm_objective.argtypes = [vp, AP, dp]
         _lib = lib
         return lib
 
@@ -301,6 +318,43 @@ class Lattice:
             _check(self.lib, rc)
         return _diag_dict(d)
 
+    @staticmethod
+    def _problem(T, ckpt_every, amps, zc, R, w, rho_l, rho_v, objective, obj_R, kstar, l0):
+        amps = np.ascontiguousarray(np.asarray(amps, dtype=np.float64).reshape(-1))
+        prob = AdjointProblem(int(T), int(ckpt_every), OBJECTIVE[objective] if isinstance(objective, str)
+                              else int(objective), int(l0), int(amps.size), int(kstar), float(zc), float(R),
+                              float(w), float(rho_l), float(rho_v), float(R if obj_R is None else obj_R),
+                              _dptr(amps) if amps.size else None)
+        return prob, amps
+
+    def adjoint(self, T, amps, zc, R, w=2.0, rho_l=1.93, rho_v=0.16, objective="a2sq", obj_R=None,
+                kstar=0, l0=2, ckpt_every=None):
+        """J and dJ/d(G, tau, amps) of: shape-perturbed drop -> f^eq -> T steps -> J, by the
+        hand-written discrete adjoint (state checkpoints every ckpt_every steps, default
+        ~sqrt(T)).  Overwrites the lattice state."""
+        import torch
+        ck = int(ckpt_every) if ckpt_every else max(1, int(round(np.sqrt(T))))
+        prob, keep = self._problem(T, ck, amps, zc, R, w, rho_l, rho_v, objective, obj_R, kstar, l0)
+        nbytes = self.lib.amlbm_adjoint_workspace_bytes(self.h, ctypes.byref(prob))
+        if nbytes == 0:
+            raise AmlbmError(EINVAL, self.lib.amlbm_last_error().decode())
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (ws.data_ptr() + 255) // 256 * 256
+        J, dG, dT = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        dA = np.zeros(max(1, keep.size))
+        _check(self.lib, self.lib.amlbm_adjoint(self.h, ctypes.byref(prob), ctypes.c_void_p(aligned), nbytes,
+                                                ctypes.byref(J), ctypes.byref(dG), ctypes.byref(dT), _dptr(dA)))
+        del ws
+        return J.value, dG.value, dT.value, dA[:keep.size].copy()
+
+    def objective(self, T, amps, zc, R, w=2.0, rho_l=1.93, rho_v=0.16, objective="a2sq", obj_R=None,
+                  kstar=0, l0=2):
+        """J of the same run (no adjoint).  Overwrites the lattice state."""
+        prob, keep = self._problem(T, 1, amps, zc, R, w, rho_l, rho_v, objective, obj_R, kstar, l0)
+        J = ctypes.c_double()
+        _check(self.lib, self.lib.amlbm_objective(self.h, ctypes.byref(prob), ctypes.byref(J)))
+        return J.value
+
     def save_state(self) -> bytes:
         n = ctypes.c_size_t(0)
         _check(self.lib, self.lib.amlbm_save_state(self.h, None, ctypes.byref(n)))
@@ -331,3 +385,64 @@ def tiles(storage="f32"):
     tz, tr = (ctypes.c_int * n)(), (ctypes.c_int * n)()
     lib.amlbm_tiles(st, tz, tr, n)
     return list(zip(tz, tr))
+
+
+@dataclass
+class DropRun:
+    """A differentiable run for DropObjective: lattice, drop, objective."""
+    Nz: int
+    Nr: int
+    T: int
+    zc: float
+    R: float
+    w: float = 2.0
+    rho_l: float = 1.93
+    rho_v: float = 0.16
+    objective: str = "a2sq"
+    obj_R: float = None
+    kstar: int = 0
+    l0: int = 2
+    storage: str = "f64"
+    ckpt_every: int = None
+    wall: str = "freeslip"
+
+
+def _drop_objective_class():
+    import torch
+
+    class DropObjective(torch.autograd.Function):
+        """J(amps, G, tau) of a DropRun; backward returns the discrete-adjoint gradients."""
+
+        @staticmethod
+        def forward(ctx, amps, G, tau, run):
+            lat = Lattice(run.Nz, run.Nr, tau=float(tau), G=float(G), storage=run.storage, wall=run.wall)
+            a = amps.detach().cpu().double().numpy()
+            kw = dict(zc=run.zc, R=run.R, w=run.w, rho_l=run.rho_l, rho_v=run.rho_v,
+                      objective=run.objective, obj_R=run.obj_R, kstar=run.kstar, l0=run.l0)
+            if any(ctx.needs_input_grad[:3]):
+                J, dG, dT, dA = lat.adjoint(run.T, a, ckpt_every=run.ckpt_every, **kw)
+                ctx.save_for_backward(torch.as_tensor(dA, dtype=amps.dtype, device=amps.device),
+                                      torch.tensor(dG, dtype=torch.float64), torch.tensor(dT, dtype=torch.float64))
+            else:
+                J = lat.objective(run.T, a, **kw)
+            lat.close()
+            return torch.tensor(J, dtype=torch.float64, device=amps.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dA, dG, dT = ctx.saved_tensors
+            gJ = gJ.to(torch.float64)
+            return (gJ.to(dA.dtype) * dA, (gJ.cpu() * dG).to(gJ.device), (gJ.cpu() * dT).to(gJ.device), None)
+
+    return DropObjective
+
+
+_DO = None
+
+
+def drop_objective(amps, G, tau, run: DropRun):
+    """torch-differentiable J(amps, G, tau) (see DropRun)."""
+    global _DO
+    if _DO is None:
+        _DO = _drop_objective_class()
+    return _DO.apply(amps, G, tau, run)

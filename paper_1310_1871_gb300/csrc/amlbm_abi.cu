@@ -603,6 +603,7 @@ int ctx_info(amlbm_ctx* c, CtxInfo* out) {
   if (!c || !c->b || !out) return fail(AMLBM_EINVAL, "NULL context");
   const amlbm_batch* b = c->b;
   out->d_desc = b->d_desc;
+  out->host = b->desc[0];
   out->Nz = b->desc[0].Nz;
   out->Nr = b->desc[0].Nr;
   out->storage = b->storage;

@@ -1,0 +1,715 @@
+// Discrete adjoint of the axisymmetric Shan-Chen LBM step (the reverse sweep of
+// the update of Sec. II, transposed operation by operation), the device map from
+// Legendre shape amplitudes to the initial drop, the objectives, and the
+// checkpointed driver behind amlbm_adjoint / amlbm_objective.
+//
+// One adjoint step (lambda^{n+1} -> lambda^n, state f^n) runs as:
+//   inter  : forward intermediates of f^n (lbm_kernel MODE 2)
+//   post   : mu = transpose of the streaming map (a gather), then the adjoint of
+//            the BGK collision and of the sources S, H_z, H_r  -> rho, u, u^eq,
+//            velocity-gradient adjoints, tau part
+//   vel    : transposed gradient stencils with the u ghosts folded back, then the
+//            adjoint of u = (j + F/2)/rho and u^eq = (j + tau F)/rho
+//   force  : adjoint of F_SC (Eq. scforce) and F^gamma (Eq. scAxisExtra) at the
+//            site (local psi factor, d_zr, d_rr, d_r parts), G part
+//   deriv  : transposed 1D d_z (of d_zr) and isotropic d_r (of d_rr)
+//   final  : transposed Shan-Chen neighbour sum, 1D d_r and isotropic d_r on psi,
+//            psi ghosts folded onto their mirrors, d psi/d rho, and
+//            lambda^n_i = (1 - omega) mu_i + rho_bar + c_i . j_bar.
+// All kernels are gathers (no atomics), so the sweep is deterministic.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amlbm.h"
+#include "amlbm_internal.cuh"
+
+namespace amlbm {
+namespace {
+
+__host__ __device__ constexpr int acz(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int acr(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr double aw(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int amirror(int i) {
+  return i == 2 ? 4 : i == 4 ? 2 : i == 5 ? 8 : i == 8 ? 5 : i == 6 ? 7 : i == 7 ? 6 : i;
+}
+__host__ __device__ constexpr int aopp(int i) {
+  return i == 0 ? 0 : i == 1 ? 3 : i == 3 ? 1 : i == 2 ? 4 : i == 4 ? 2
+       : i == 5 ? 7 : i == 7 ? 5 : i == 6 ? 8 : 6;
+}
+
+__device__ __forceinline__ int wz(int k, int Nz) {
+  k %= Nz;
+  return k < 0 ? k + Nz : k;
+}
+
+template <class C>
+struct Adj {
+  int Nz, Nr, P, wall, axisym;
+  size_t plane;
+  C tau, omega, G, rho0, gz;
+  const C* lam_in;
+  C* lam_out;
+  const C* f;      // state f^n, 9 planes
+  const C* inter;  // I_COUNT planes
+  C* mu;           // 9 planes
+  C *rhob, *uzb, *urb, *vzb, *vrb, *g1b, *g2b, *g3b, *jzb, *jrb, *Fzb, *Frb;
+  C *psib, *qz, *qr, *dzrb, *drrb, *drdb, *eb;
+  C* drpb;  // d_r psi adjoint on rows -2 .. Nr+1 (row offset 2)
+  double *accG, *accT;
+};
+
+// value of a [Nr][P] field at (k, j), zero outside the real rows
+template <class C>
+__device__ __forceinline__ C at(const C* a, int k, int j, const Adj<C>& A) {
+  if (j < 0 || j >= A.Nr) return C(0);
+  return a[(size_t)j * A.P + wz(k, A.Nz)];
+}
+// d_r psi adjoint on the padded rows -2 .. Nr+1, zero outside
+template <class C>
+__device__ __forceinline__ C atpad(const C* a, int k, int j, const Adj<C>& A) {
+  if (j < -2 || j > A.Nr + 1) return C(0);
+  return a[(size_t)(j + 2) * A.P + wz(k, A.Nz)];
+}
+
+// Transpose of the isotropic derivative along r (AX = 1) or z (AX = 0) at the
+// (possibly ghost) position (k, j):  sum_i c_i,AX (8 g(y - c_i) - g(y - 2 c_i)) / 36.
+template <int AX, bool PAD, class C>
+__device__ __forceinline__ C iso_t(const C* g, int k, int j, const Adj<C>& A) {
+  C s = C(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int c = AX ? acr(i) : acz(i);
+    if (c == 0) continue;
+    const C a = PAD ? atpad(g, k - acz(i), j - acr(i), A) : at(g, k - acz(i), j - acr(i), A);
+    const C b = PAD ? atpad(g, k - 2 * acz(i), j - 2 * acr(i), A) : at(g, k - 2 * acz(i), j - 2 * acr(i), A);
+    s += C(c) * (C(8) * a - b);
+  }
+  return s * C(1.0 / 36.0);
+}
+
+template <class C>
+__device__ __forceinline__ C feq_std(int i, C rho, C vz, C vr) {
+  const C cv = C(acz(i)) * vz + C(acr(i)) * vr;
+  return C(aw(i)) * rho * (C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * (vz * vz + vr * vr));
+}
+
+// ---- post: inverse streaming, collision and source adjoints (per real site)
+template <class C>
+__global__ void adj_post(Adj<C> A) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.Nz * A.Nr) return;
+  const int j = n / A.Nz, k = n - j * A.Nz;
+  const size_t o = (size_t)j * A.P + k;
+  const bool noslip = A.wall == AMLBM_WALL_NOSLIP;
+  C mu[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    // where population q leaving (k, j) arrives after streaming (Sec. II.E maps)
+    int yk = k + acz(q), yj = j + acr(q), d = q;
+    if (yj < 0) {
+      yj = 0; d = amirror(q);
+    } else if (yj >= A.Nr) {
+      if (noslip) { yk = k; yj = A.Nr - 1; d = aopp(q); }
+      else { yj = A.Nr - 1; d = amirror(q); }
+    }
+    mu[q] = A.lam_in[d * A.plane + (size_t)yj * A.P + wz(yk, A.Nz)];
+    A.mu[q * A.plane + o] = mu[q];
+  }
+  const C* I = A.inter + o;
+  const C rho = I[I_RHO * A.plane], vz = I[I_VZ * A.plane], vr = I[I_VR * A.plane];
+  const C uz = I[I_UZ * A.plane], ur = I[I_UR * A.plane];
+  C rb = C(0), vzb = C(0), vrb = C(0), tb = C(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const C fe = feq_std(q, rho, vz, vr);
+    const C cv = C(acz(q)) * vz + C(acr(q)) * vr;
+    const C m = A.omega * mu[q];
+    rb += m * fe / rho;
+    const C com = m * C(aw(q)) * rho;
+    vzb += com * (C(3) * C(acz(q)) + C(9) * cv * C(acz(q)) - C(3) * vz);
+    vrb += com * (C(3) * C(acr(q)) + C(9) * cv * C(acr(q)) - C(3) * vr);
+    tb += -A.omega * A.omega * mu[q] * (fe - A.f[q * A.plane + o]);
+  }
+  C uzb = C(0), urb = C(0), g1b = C(0), g2b = C(0), g3b = C(0);
+  if (A.axisym) {
+    C Sb = C(0), Hzb = C(0), Hrb = C(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Sb += mu[q] * C(aw(q));
+      Hzb += C(3) * mu[q] * C(aw(q)) * C(acz(q));
+      Hrb += C(3) * mu[q] * C(aw(q)) * C(acr(q));
+    }
+    const C r = C(j) + C(0.5), ir = C(1) / r;
+    const C g1 = I[I_G1 * A.plane], g2 = I[I_G2 * A.plane], g3 = I[I_G3 * A.plane];
+    const C muv = rho * (A.tau - C(0.5)) / C(3);
+    // S = -rho u_r / r
+    rb += -Sb * ur * ir;
+    urb += -Sb * rho * ir;
+    // H_z = (mu (g1 + g2) - rho u_r u_z) / r
+    C mvb = Hzb * (g1 + g2) * ir;
+    g1b = Hzb * muv * ir;
+    g2b = Hzb * muv * ir;
+    rb += -Hzb * ur * uz * ir;
+    urb += -Hzb * rho * uz * ir;
+    uzb += -Hzb * rho * ur * ir;
+    // H_r = (2 mu (g3 - u_r / r) - rho u_r^2) / r
+    mvb += Hrb * C(2) * (g3 - ur * ir) * ir;
+    g3b = Hrb * C(2) * muv * ir;
+    urb += Hrb * (-C(2) * muv * ir - C(2) * rho * ur) * ir;
+    rb += -Hrb * ur * ur * ir;
+    // mu = rho (tau - 1/2) / 3
+    rb += mvb * (A.tau - C(0.5)) / C(3);
+    tb += mvb * rho / C(3);
+  }
+  A.rhob[o] = rb;
+  A.uzb[o] = uzb;
+  A.urb[o] = urb;
+  A.vzb[o] = vzb;
+  A.vrb[o] = vrb;
+  A.g1b[o] = g1b;
+  A.g2b[o] = g2b;
+  A.g3b[o] = g3b;
+  A.accT[o] += double(tb);
+}
+
+// ---- vel: transposed gradient stencils (u ghosts folded), adjoint of u and u^eq
+template <class C>
+__global__ void adj_vel(Adj<C> A) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.Nz * A.Nr) return;
+  const int j = n / A.Nz, k = n - j * A.Nz;
+  const size_t o = (size_t)j * A.P + k;
+  C uzb = A.uzb[o], urb = A.urb[o];
+  if (A.axisym) {
+    const C szw = A.wall == AMLBM_WALL_NOSLIP ? C(-1) : C(1);
+    uzb += iso_t<1, false>(A.g1b, k, j, A);
+    urb += iso_t<0, false>(A.g2b, k, j, A) + iso_t<1, false>(A.g3b, k, j, A);
+    // ghost rows (depth 2) that mirror this row: u_z even / u_r odd at the axis;
+    // at the wall u_r odd and u_z even (free-slip) or odd (no-slip)
+    const int ga = -1 - j;
+    if (ga >= -2) {
+      uzb += iso_t<1, false>(A.g1b, k, ga, A);
+      urb -= iso_t<0, false>(A.g2b, k, ga, A) + iso_t<1, false>(A.g3b, k, ga, A);
+    }
+    const int gw = 2 * A.Nr - 1 - j;
+    if (gw <= A.Nr + 1) {
+      uzb += szw * iso_t<1, false>(A.g1b, k, gw, A);
+      urb -= iso_t<0, false>(A.g2b, k, gw, A) + iso_t<1, false>(A.g3b, k, gw, A);
+    }
+  }
+  const C* I = A.inter + o;
+  const C rho = I[I_RHO * A.plane], ir = C(1) / rho;
+  const C uz = I[I_UZ * A.plane], ur = I[I_UR * A.plane], vz = I[I_VZ * A.plane],
+          vr = I[I_VR * A.plane], Fz = I[I_FZ * A.plane], Fr = I[I_FR * A.plane];
+  const C vzb = A.vzb[o], vrb = A.vrb[o];
+  A.jzb[o] = (uzb + vzb) * ir;
+  A.jrb[o] = (urb + vrb) * ir;
+  const C Fzb = (C(0.5) * uzb + A.tau * vzb) * ir, Frb = (C(0.5) * urb + A.tau * vrb) * ir;
+  A.Fzb[o] = Fzb;
+  A.Frb[o] = Frb;
+  A.rhob[o] += -(uzb * uz + urb * ur + vzb * vz + vrb * vr) * ir + Fzb * A.gz;
+  A.accT[o] += double((vzb * Fz + vrb * Fr) * ir);
+}
+
+// ---- force: local adjoint of F_SC and F^gamma
+template <class C>
+__global__ void adj_force(Adj<C> A) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.Nz * A.Nr) return;
+  const int j = n / A.Nz, k = n - j * A.Nz;
+  const size_t o = (size_t)j * A.P + k;
+  const C* I = A.inter + o;
+  const C psi = I[I_PSI * A.plane], sz = I[I_SZ * A.plane], sr = I[I_SR * A.plane];
+  const C Fzb = A.Fzb[o], Frb = A.Frb[o];
+  // F_SC = -G psi s
+  C pb = -A.G * (Fzb * sz + Frb * sr);
+  double gb = double(-psi * (Fzb * sz + Frb * sr));
+  A.qz[o] = -A.G * psi * Fzb;
+  A.qr[o] = -A.G * psi * Frb;
+  C dzrb = C(0), drrb = C(0), drdb = C(0);
+  if (A.axisym) {
+    const C r = C(j) + C(0.5), ir = C(1) / r;
+    const C Dr = I[I_DR * A.plane], Drr = I[I_DRR * A.plane], Dzr = I[I_DZR * A.plane];
+    const C gf = -A.G / C(18);
+    const C t = Fzb * Dzr * ir + Frb * (Drr * ir - Dr * ir * ir);
+    pb += gf * t;
+    gb += double(-psi * t / C(18));
+    dzrb = gf * psi * Fzb * ir;
+    drrb = gf * psi * Frb * ir;
+    drdb = -gf * psi * Frb * ir * ir;
+  }
+  A.psib[o] = pb;
+  A.dzrb[o] = dzrb;
+  A.drrb[o] = drrb;
+  A.drdb[o] = drdb;
+  A.accG[o] += gb;
+}
+
+// ---- deriv: transposed 1D d_z (into the 1D d_r field) and isotropic d_r (into
+// the padded d_r psi field, rows -2 .. Nr+1)
+template <class C>
+__global__ void adj_deriv(Adj<C> A) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.Nz * (A.Nr + 4)) return;
+  const int jp = n / A.Nz - 2, k = n - (jp + 2) * A.Nz;
+  if (jp >= 0 && jp < A.Nr) {
+    const C* d = A.dzrb + (size_t)jp * A.P;
+    const C e = (C(8) * (d[wz(k - 1, A.Nz)] - d[wz(k + 1, A.Nz)]) -
+                 (d[wz(k - 2, A.Nz)] - d[wz(k + 2, A.Nz)])) * C(1.0 / 12.0);
+    A.eb[(size_t)jp * A.P + k] = e;
+  }
+  C v = iso_t<1, false>(A.drrb, k, jp, A);
+  if (jp >= 0 && jp < A.Nr) v += A.drdb[(size_t)jp * A.P + k];
+  A.drpb[(size_t)(jp + 2) * A.P + k] = v;
+}
+
+// psi adjoint at the (possibly ghost) position (k, y): transposed Shan-Chen
+// neighbour sum, 1D d_r and isotropic d_r.
+template <class C>
+__device__ __forceinline__ C psi_pad_adj(int k, int y, const Adj<C>& A) {
+  C s = C(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const C w = C(aw(i));
+    if (acz(i)) s += w * C(acz(i)) * at(A.qz, k - acz(i), y - acr(i), A);
+    if (acr(i)) s += w * C(acr(i)) * at(A.qr, k - acz(i), y - acr(i), A);
+  }
+  if (A.axisym) {
+    s += (C(8) * (at(A.eb, k, y - 1, A) - at(A.eb, k, y + 1, A)) -
+          (at(A.eb, k, y - 2, A) - at(A.eb, k, y + 2, A))) * C(1.0 / 12.0);
+    s += iso_t<1, true>(A.drpb, k, y, A);
+  }
+  return s;
+}
+
+// ---- final: psi ghosts folded (even mirrors, depth 4), d psi / d rho, lambda^n
+template <class C>
+__global__ void adj_final(Adj<C> A) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= A.Nz * A.Nr) return;
+  const int j = n / A.Nz, k = n - j * A.Nz;
+  const size_t o = (size_t)j * A.P + k;
+  C pb = A.psib[o] + psi_pad_adj(k, j, A);
+  const int ga = -1 - j;
+  if (ga >= -4) pb += psi_pad_adj(k, ga, A);
+  const int gw = 2 * A.Nr - 1 - j;
+  if (gw <= A.Nr + 3) pb += psi_pad_adj(k, gw, A);
+  const C rho = A.inter[I_RHO * A.plane + o];
+  const C rb = A.rhob[o] + pb * exp(-rho / A.rho0);
+  const C jzb = A.jzb[o], jrb = A.jrb[o];
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    A.lam_out[q * A.plane + o] =
+        (C(1) - A.omega) * A.mu[q * A.plane + o] + rb + C(acz(q)) * jzb + C(acr(q)) * jrb;
+}
+
+// ---- the differentiable initial drop and its adjoint
+struct DropMap {
+  int Nz, Nr, l0, namp;
+  double zc, R, w, rho_l, rho_v;
+  double amp[32];
+};
+
+__device__ double legendre_d(int l, double x) {
+  double p0 = 1.0, p1 = x;
+  if (l == 0) return p0;
+  for (int m = 1; m < l; ++m) {
+    const double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+__global__ void drop_kernel(DropMap M, double* rho) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M.Nz * M.Nr) return;
+  const int j = n / M.Nz, k = n - j * M.Nz;
+  const double dz = k - M.zc, r = j + 0.5, d = sqrt(dz * dz + r * r), ct = dz / d;
+  double s = 0.0;
+  for (int m = 0; m < M.namp; ++m) s += M.amp[m] * legendre_d(M.l0 + m, ct);
+  const double Rs = M.R * (1.0 + s);
+  rho[n] = M.rho_v + 0.5 * (M.rho_l - M.rho_v) * (1.0 - tanh((d - Rs) / M.w));
+}
+
+constexpr int RED_NT = 256;
+// per-block sums of sum_x rho_bar(x) d rho(x) / d a_m, rho_bar = sum_i W_i lambda^0_i
+template <class C>
+__global__ void __launch_bounds__(RED_NT) drop_adj_kernel(DropMap M, const C* lam, size_t plane,
+                                                          int P, double* partials) {
+  __shared__ double red[RED_NT];
+  double acc[32];
+  for (int m = 0; m < M.namp; ++m) acc[m] = 0.0;
+  for (int n = blockIdx.x * RED_NT + threadIdx.x; n < M.Nz * M.Nr; n += gridDim.x * RED_NT) {
+    const int j = n / M.Nz, k = n - j * M.Nz;
+    const size_t o = (size_t)j * P + k;
+    double rb = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rb += aw(q) * double(lam[q * plane + o]);
+    const double dz = k - M.zc, r = j + 0.5, d = sqrt(dz * dz + r * r), ct = dz / d;
+    double s = 0.0;
+    for (int m = 0; m < M.namp; ++m) s += M.amp[m] * legendre_d(M.l0 + m, ct);
+    const double X = (d - M.R * (1.0 + s)) / M.w, sh = 1.0 / cosh(X);
+    const double dr_dRs = 0.5 * (M.rho_l - M.rho_v) * sh * sh / M.w;
+    for (int m = 0; m < M.namp; ++m) acc[m] += rb * dr_dRs * M.R * legendre_d(M.l0 + m, ct);
+  }
+  for (int m = 0; m < M.namp; ++m) {
+    red[threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int s = RED_NT / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x * 32 + m] = red[0];
+    __syncthreads();
+  }
+}
+
+// per-block sums of two per-site FP64 arrays ([Nr][P]) -> partials[b * 2 + {0, 1}]
+__global__ void __launch_bounds__(RED_NT) sum2_kernel(const double* a, const double* b, int Nz, int Nr,
+                                                      int P, double* partials) {
+  __shared__ double ra[RED_NT], rb[RED_NT];
+  double sa = 0.0, sb = 0.0;
+  for (int n = blockIdx.x * RED_NT + threadIdx.x; n < Nz * Nr; n += gridDim.x * RED_NT) {
+    const int j = n / Nz, k = n - j * Nz;
+    sa += a[(size_t)j * P + k];
+    sb += b[(size_t)j * P + k];
+  }
+  ra[threadIdx.x] = sa;
+  rb[threadIdx.x] = sb;
+  __syncthreads();
+  for (int s = RED_NT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      ra[threadIdx.x] += ra[threadIdx.x + s];
+      rb[threadIdx.x] += rb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * 2] = ra[0];
+    partials[blockIdx.x * 2 + 1] = rb[0];
+  }
+}
+
+// lambda^T = dJ/df_i(x) = dJ/drho(x) for every i
+template <class C>
+__global__ void seed_kernel(int kind, int Nz, int Nr, int P, size_t plane, double zc, double objR,
+                            double rho_l, double rho_v, int kstar, double a2_or_J, C* lam) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= Nz * Nr) return;
+  const int j = n / Nz, k = n - j * Nz;
+  const double pi = 3.14159265358979323846, r = j + 0.5, dz = k - zc;
+  double s;
+  if (kind == AMLBM_OBJ_A2SQ)
+    s = 2.0 * a2_or_J * 5.0 / (4.0 * pi * pow(objR, 5.0)) * 2.0 * pi * r * (dz * dz - 0.5 * r * r) /
+        (rho_l - rho_v);
+  else
+    s = k == kstar ? r / ((rho_l - rho_v) * a2_or_J) : 0.0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) lam[q * plane + (size_t)j * P + k] = C(s);
+}
+
+// J of the neck objective from the read-back density (one thread)
+__global__ void neck_kernel(const double* rho, int Nz, int Nr, int kstar, double rho_l, double rho_v,
+                            double* J) {
+  double s = 0.0;
+  for (int j = 0; j < Nr; ++j) s += (j + 0.5) * (rho[(size_t)j * Nz + kstar] - rho_v) / (rho_l - rho_v);
+  *J = sqrt(2.0 * s);
+}
+
+}  // namespace
+}  // namespace amlbm
+
+// ------------------------------------------------------------------ driver --
+using amlbm::InstDesc;
+
+namespace {
+
+struct AdjLayout {
+  size_t total = 0;
+  size_t ckpt = 0, seg = 0, lam = 0, inter = 0, mu = 0, arr = 0, drp = 0, acc = 0, rho0 = 0,
+         red = 0, descs = 0, tiles = 0;
+  int nck = 0, nseg = 0, ntiles = 0, nred = 0;
+  size_t state_elems = 0;  // 10 planes (f and psi)
+};
+
+constexpr int kAdjArrays = 19;
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+AdjLayout adj_layout(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem& p) {
+  AdjLayout L;
+  const size_t cb = ci.storage == AMLBM_STORE_F64 ? 8 : 4;
+  const size_t plane = (size_t)ci.host.P * ci.Nr;
+  L.nck = (p.T + p.ckpt_every - 1) / p.ckpt_every;
+  L.nseg = std::min(p.ckpt_every, p.T);
+  L.state_elems = 10 * plane;
+  L.ntiles = ((ci.Nz + 31) / 32) * ((ci.Nr + 7) / 8);
+  L.nred = std::min(1024, (ci.Nz * ci.Nr + 255) / 256);
+  size_t o = 0;
+  auto take = [&](size_t b) { const size_t a = o; o = al(o + b); return a; };
+  L.ckpt = take((size_t)L.nck * L.state_elems * cb);
+  L.seg = take((size_t)L.nseg * L.state_elems * cb);
+  L.lam = take(2 * 9 * plane * cb);
+  L.inter = take((size_t)amlbm::I_COUNT * plane * cb);
+  L.mu = take(9 * plane * cb);
+  L.arr = take((size_t)kAdjArrays * plane * cb);
+  L.drp = take((size_t)(ci.Nr + 4) * ci.host.P * cb);
+  L.acc = take(2 * plane * sizeof(double));
+  L.rho0 = take((size_t)ci.Nz * ci.Nr * sizeof(double));
+  const int nblk = amlbm::diag_blocks(ci.Nz, ci.Nr);
+  L.red = take((size_t)(std::max(L.nred * 34, 8 * nblk + ci.Nz + 16) + 64) * sizeof(double));
+  L.descs = take((size_t)L.nseg * sizeof(InstDesc));
+  L.tiles = take((size_t)L.ntiles * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+int check_problem(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem* p) {
+  using amlbm::set_error;
+  if (!p) return set_error(AMLBM_EINVAL, "NULL problem");
+  if (ci.storage != AMLBM_STORE_F64 && ci.storage != AMLBM_STORE_F32)
+    return set_error(AMLBM_EINVAL, "the adjoint needs FP64 or FP32 storage");
+  if (ci.host.shift != 0) return set_error(AMLBM_EINVAL, "the adjoint needs unshifted storage");
+  if (ci.host.src != AMLBM_SRC_LOCAL)
+    return set_error(AMLBM_EINVAL, "the adjoint implements the departure-site source only");
+  if (p->T < 1 || p->ckpt_every < 1) return set_error(AMLBM_EINVAL, "need T >= 1, ckpt_every >= 1");
+  if (p->n_amps < 0 || p->n_amps > 32 || (p->n_amps > 0 && !p->amps) || p->l0 < 0)
+    return set_error(AMLBM_EINVAL, "need 0 <= n_amps <= 32, amps, l0 >= 0");
+  if (p->objective != AMLBM_OBJ_A2SQ && p->objective != AMLBM_OBJ_NECK)
+    return set_error(AMLBM_EINVAL, "bad objective");
+  if (p->objective == AMLBM_OBJ_NECK && (p->kstar < 0 || p->kstar >= ci.Nz))
+    return set_error(AMLBM_EINVAL, "kstar outside the lattice");
+  if (!(p->w > 0) || !(p->R > 0) || !(p->obj_R > 0) || !(p->rho_l != p->rho_v))
+    return set_error(AMLBM_EINVAL, "need w > 0, R > 0, obj_R > 0, rho_l != rho_v");
+  return AMLBM_OK;
+}
+
+#define ADJ_CK(call)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      rc = amlbm::set_error(AMLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      goto done;                                                                       \
+    }                                                                                  \
+  } while (0)
+
+template <class C>
+int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_bytes, bool adjoint,
+        double* J, double* dG, double* dT, double* dA) {
+  using namespace amlbm;
+  CtxInfo ci;
+  int rc = ctx_info(ctx, &ci);
+  if (rc) return rc;
+  if ((rc = check_problem(ci, p))) return rc;
+  const AdjLayout L = adj_layout(ci, *p);
+  const cudaStream_t s = ci.stream;
+  const int Nz = ci.Nz, Nr = ci.Nr, P = ci.host.P, N = Nz * Nr;
+  const size_t plane = (size_t)P * Nr;
+  const int nb = (N + 255) / 256;
+  char* base = static_cast<char*>(ws);
+  bool owns = false;
+  std::vector<double> red;
+  double Jv = 0.0;
+  if (!base) {
+    const cudaError_t e = cudaMalloc(&base, L.total);
+    if (e != cudaSuccess) return set_error(AMLBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    owns = true;
+  } else if (ws_bytes < L.total || reinterpret_cast<uintptr_t>(ws) % 256) {
+    return set_error(AMLBM_ENOMEM, "adjoint workspace too small or not 256-byte aligned: need " +
+                                       std::to_string(L.total) + " bytes");
+  }
+  {
+    C* ckpt = reinterpret_cast<C*>(base + L.ckpt);
+    C* seg = reinterpret_cast<C*>(base + L.seg);
+    C* lam[2] = {reinterpret_cast<C*>(base + L.lam), reinterpret_cast<C*>(base + L.lam) + 9 * plane};
+    double* rho_init = reinterpret_cast<double*>(base + L.rho0);
+    double* redbuf = reinterpret_cast<double*>(base + L.red);
+    const size_t SB = L.state_elems * sizeof(C), FB = 9 * plane * sizeof(C), PB = plane * sizeof(C);
+    void* fcur;
+    void* pcur;
+    int pitch;
+
+    DropMap M;
+    std::memset(&M, 0, sizeof(M));
+    M.Nz = Nz; M.Nr = Nr; M.l0 = p->l0; M.namp = p->n_amps;
+    M.zc = p->zc; M.R = p->R; M.w = p->w; M.rho_l = p->rho_l; M.rho_v = p->rho_v;
+    for (int m = 0; m < p->n_amps; ++m) M.amp[m] = p->amps[m];
+
+    // forward: initial drop, T steps, states every ckpt_every steps
+    drop_kernel<<<nb, 256, 0, s>>>(M, rho_init);
+    ADJ_CK(cudaGetLastError());
+    ADJ_CK(launch_init(ci.storage, ci.d_desc, 0, Nz, Nr, rho_init, nullptr, nullptr, ci.parity, s));
+    for (int n = 0; n < p->T; ++n) {
+      if (adjoint && n % p->ckpt_every == 0) {
+        amlbm_device_state(ctx, &fcur, &pcur, &pitch);
+        C* dst = ckpt + (size_t)(n / p->ckpt_every) * L.state_elems;
+        ADJ_CK(cudaMemcpyAsync(dst, fcur, FB, cudaMemcpyDeviceToDevice, s));
+        ADJ_CK(cudaMemcpyAsync(dst + 9 * plane, pcur, PB, cudaMemcpyDeviceToDevice, s));
+      }
+      if ((rc = amlbm_step(ctx, 1))) goto done;
+    }
+    // objective of the final state
+    if ((rc = ctx_readback(ctx))) goto done;
+    {
+      double a2 = 0.0;
+      if (p->objective == AMLBM_OBJ_A2SQ) {
+        const int nblk = diag_blocks(Nz, Nr);
+        ADJ_CK(launch_diag(ci.storage, ci.d_desc, 0, Nz, Nr, ci.parity ^ (p->T & 1), p->zc, p->obj_R,
+                           p->rho_l, p->rho_v, redbuf, nblk, redbuf + 8 * nblk, redbuf + 8 * nblk + Nz, s));
+        ADJ_CK(cudaMemcpyAsync(&a2, redbuf + 8 * nblk + Nz + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ADJ_CK(cudaStreamSynchronize(s));
+        Jv = a2 * a2;
+      } else {
+        neck_kernel<<<1, 1, 0, s>>>(ci.host.rho_out, Nz, Nr, p->kstar, p->rho_l, p->rho_v, redbuf);
+        ADJ_CK(cudaGetLastError());
+        ADJ_CK(cudaMemcpyAsync(&Jv, redbuf, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ADJ_CK(cudaStreamSynchronize(s));
+      }
+      if (J) *J = Jv;
+      if (!adjoint) goto done;
+      seed_kernel<C><<<nb, 256, 0, s>>>(p->objective, Nz, Nr, P, plane, p->zc, p->obj_R, p->rho_l,
+                                        p->rho_v, p->kstar, p->objective == AMLBM_OBJ_A2SQ ? a2 : Jv,
+                                        lam[0]);
+      ADJ_CK(cudaGetLastError());
+    }
+    // descriptors of the segment slots for the intermediates kernel (tile 32 x 8)
+    {
+      std::vector<InstDesc> d(L.nseg, ci.host);
+      for (int q = 0; q < L.nseg; ++q) {
+        d[q].tiles_z = (Nz + 31) / 32;
+        d[q].tiles_r = (Nr + 7) / 8;
+        d[q].tile_base = 0;
+        d[q].f[0] = seg + (size_t)q * L.state_elems;
+        d[q].psi[0] = seg + (size_t)q * L.state_elems + 9 * plane;
+      }
+      std::vector<int> tiles(L.ntiles, 0);
+      ADJ_CK(cudaMemcpyAsync(base + L.descs, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+      ADJ_CK(cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      ADJ_CK(cudaMemsetAsync(base + L.acc, 0, 2 * plane * sizeof(double), s));
+      ADJ_CK(cudaStreamSynchronize(s));  // host vectors above go out of scope
+    }
+    {
+      Adj<C> A;
+      A.Nz = Nz; A.Nr = Nr; A.P = P; A.wall = ci.host.wall; A.axisym = ci.host.axisym;
+      A.plane = plane;
+      A.tau = C(ci.host.tau); A.omega = C(1) / A.tau; A.G = C(ci.host.G); A.rho0 = C(ci.host.rho0);
+      A.gz = C(ci.host.gz);
+      A.inter = reinterpret_cast<C*>(base + L.inter);
+      A.mu = reinterpret_cast<C*>(base + L.mu);
+      C* arr = reinterpret_cast<C*>(base + L.arr);
+      C** fields[kAdjArrays] = {&A.rhob, &A.uzb, &A.urb, &A.vzb, &A.vrb, &A.g1b, &A.g2b, &A.g3b, &A.jzb,
+                                &A.jrb, &A.Fzb, &A.Frb, &A.psib, &A.qz, &A.qr, &A.dzrb, &A.drrb, &A.drdb,
+                                &A.eb};
+      for (int q = 0; q < kAdjArrays; ++q) *fields[q] = arr + (size_t)q * plane;
+      A.drpb = reinterpret_cast<C*>(base + L.drp);
+      A.accG = reinterpret_cast<double*>(base + L.acc);
+      A.accT = A.accG + plane;
+      const InstDesc* d_seg = reinterpret_cast<const InstDesc*>(base + L.descs);
+      const int* d_tiles = reinterpret_cast<const int*>(base + L.tiles);
+      const int nbp = (Nz * (Nr + 4) + 255) / 256;
+      int cur = 0;
+      for (int m = L.nck - 1; m >= 0; --m) {
+        const int n0 = m * p->ckpt_every, n1 = std::min(p->T, n0 + p->ckpt_every);
+        // recompute the segment's states from its checkpoint
+        ADJ_CK(cudaMemcpyAsync(seg, ckpt + (size_t)m * L.state_elems, SB, cudaMemcpyDeviceToDevice, s));
+        if (n1 - n0 > 1) {
+          amlbm_device_state(ctx, &fcur, &pcur, &pitch);
+          ADJ_CK(cudaMemcpyAsync(fcur, seg, FB, cudaMemcpyDeviceToDevice, s));
+          ADJ_CK(cudaMemcpyAsync(pcur, seg + 9 * plane, PB, cudaMemcpyDeviceToDevice, s));
+          for (int q = 1; q < n1 - n0; ++q) {
+            if ((rc = amlbm_step(ctx, 1))) goto done;
+            amlbm_device_state(ctx, &fcur, &pcur, &pitch);
+            C* dst = seg + (size_t)q * L.state_elems;
+            ADJ_CK(cudaMemcpyAsync(dst, fcur, FB, cudaMemcpyDeviceToDevice, s));
+            ADJ_CK(cudaMemcpyAsync(dst + 9 * plane, pcur, PB, cudaMemcpyDeviceToDevice, s));
+          }
+        }
+        // transposed steps from the last of the segment to the first
+        for (int n = n1 - 1; n >= n0; --n) {
+          const int q = n - n0;
+          ADJ_CK(launch_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles, const_cast<C*>(A.inter), plane, s));
+          A.f = seg + (size_t)q * L.state_elems;
+          A.lam_in = lam[cur];
+          A.lam_out = lam[cur ^ 1];
+          adj_post<C><<<nb, 256, 0, s>>>(A);
+          adj_vel<C><<<nb, 256, 0, s>>>(A);
+          adj_force<C><<<nb, 256, 0, s>>>(A);
+          adj_deriv<C><<<nbp, 256, 0, s>>>(A);
+          adj_final<C><<<nb, 256, 0, s>>>(A);
+          ADJ_CK(cudaGetLastError());
+          cur ^= 1;
+        }
+      }
+      // parameter gradients (FP64, fixed order)
+      sum2_kernel<<<L.nred, RED_NT, 0, s>>>(A.accG, A.accT, Nz, Nr, P, redbuf);
+      ADJ_CK(cudaGetLastError());
+      if (p->n_amps > 0) {
+        drop_adj_kernel<C><<<L.nred, RED_NT, 0, s>>>(M, lam[cur], plane, P, redbuf + 2 * L.nred);
+        ADJ_CK(cudaGetLastError());
+      }
+      red.resize((size_t)L.nred * 34);
+      ADJ_CK(cudaMemcpyAsync(red.data(), redbuf, red.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      ADJ_CK(cudaStreamSynchronize(s));
+      double g = 0.0, t = 0.0;
+      for (int b = 0; b < L.nred; ++b) { g += red[2 * b]; t += red[2 * b + 1]; }
+      if (dG) *dG = g;
+      if (dT) *dT = t;
+      for (int m = 0; m < p->n_amps; ++m) {
+        double a = 0.0;
+        for (int b = 0; b < L.nred; ++b) a += red[2 * L.nred + (size_t)b * 32 + m];
+        if (dA) dA[m] = a;
+      }
+    }
+  }
+done:
+  if (owns) {
+    cudaStreamSynchronize(s);
+    cudaFree(base);
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t amlbm_adjoint_workspace_bytes(amlbm_ctx* ctx, const amlbm_adjoint_problem* p) {
+  amlbm::CtxInfo ci;
+  if (!ctx || amlbm::ctx_info(ctx, &ci) || check_problem(ci, p)) return 0;
+  return adj_layout(ci, *p).total;
+}
+
+int amlbm_adjoint(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* workspace, size_t bytes,
+                  double* J, double* dJ_dG, double* dJ_dtau, double* dJ_damps) {
+  amlbm::CtxInfo ci;
+  if (!ctx) return amlbm::set_error(AMLBM_EINVAL, "NULL context");
+  const int rc = amlbm::ctx_info(ctx, &ci);
+  if (rc) return rc;
+  if (ci.storage == AMLBM_STORE_F64)
+    return run<double>(ctx, p, workspace, bytes, true, J, dJ_dG, dJ_dtau, dJ_damps);
+  return run<float>(ctx, p, workspace, bytes, true, J, dJ_dG, dJ_dtau, dJ_damps);
+}
+
+int amlbm_objective(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, double* J) {
+  amlbm::CtxInfo ci;
+  if (!ctx) return amlbm::set_error(AMLBM_EINVAL, "NULL context");
+  const int rc = amlbm::ctx_info(ctx, &ci);
+  if (rc) return rc;
+  if (ci.storage == AMLBM_STORE_F64) return run<double>(ctx, p, nullptr, 0, false, J, nullptr, nullptr, nullptr);
+  return run<float>(ctx, p, nullptr, 0, false, J, nullptr, nullptr, nullptr);
+}
+
+}  // extern "C"

@@ -37,6 +37,18 @@ cudaError_t launch_init(int storage, const InstDesc* d_desc, int inst, int Nz, i
                         cudaStream_t s);
 cudaError_t launch_unpack(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
                           int parity, double* f_out, cudaStream_t s);
+// Forward intermediates of one step, per site, [Nr][P] arrays of the compute
+// type, for the adjoint: rho, u, u^eq, total force, psi, the Shan-Chen
+// neighbour sums, d_r psi, d_rr psi, d_zr psi and the velocity gradients
+// d_r u_z, d_z u_r, d_r u_r.
+enum InterField {
+  I_RHO, I_UZ, I_UR, I_VZ, I_VR, I_FZ, I_FR, I_PSI, I_SZ, I_SR, I_DR, I_DRR, I_DZR,
+  I_G1, I_G2, I_G3, I_COUNT
+};
+// Writes the intermediates of the state (f, psi) of instance 0 of d_desc, whose
+// f[0] / psi[0] hold that state, into inter (I_COUNT planes of plane elements).
+cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
+                         int ntiles, void* inter, size_t plane, cudaStream_t s);
 // Diagnostics: partial sums into `partials` (nblk x 8 doubles, plus Nz column
 // radii), then a single-block pass into out[16].
 cudaError_t launch_diag(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
@@ -51,6 +63,7 @@ size_t step_smem_bytes(int storage, int tz, int tr);
 // (amlbm_abi.cu implements these).
 struct CtxInfo {
   const InstDesc* d_desc;  // device descriptor array (one instance)
+  InstDesc host;           // host copy of that descriptor
   int Nz, Nr, storage, parity;
   long long steps;
   cudaStream_t stream;

@@ -219,12 +219,15 @@ __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_i
   return t;
 }
 
-// The fused update of one tile (READBACK: only rho and u of the tile, for
-// read-back and diagnostics).
-template <class S, int BZ, int BR, bool READBACK>
+// The fused update of one tile.  MODE 0: the timestep; MODE 1 (read-back):
+// only rho and u of the tile; MODE 2: the forward intermediates of the tile for
+// the adjoint (into `inter`, I_COUNT planes of `iplane` elements).
+template <class S, int BZ, int BR, int MODE>
 __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ descs,
                                                  const int* __restrict__ tile_inst, int toff,
-                                                 int parity) {
+                                                 int parity, typename Store<S>::C* __restrict__ inter,
+                                                 size_t iplane) {
+  constexpr bool READBACK = MODE == 1;
   using C = typename Store<S>::C;
   using G = Geo<C, BZ, BR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -315,7 +318,31 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
       sRho[fi] = rho;
       sUz[fi] = (jz + C(0.5) * Fz) * inv_rho;
       sUr[fi] = (jr + C(0.5) * Fr) * inv_rho;
-      if (!READBACK && srow && lc >= 2 && lc < G::FZ - 2) {
+      if (MODE == 2 && lr >= G::HF && lr < G::HF + BR && lc >= G::HF && lc < G::HF + BZ &&
+          k0 + lc - G::HF < Nz) {
+        C* o = inter + (size_t)j * P + (k0 + lc - G::HF);
+        o[I_RHO * iplane] = rho;
+        o[I_UZ * iplane] = sUz[fi];
+        o[I_UR * iplane] = sUr[fi];
+        o[I_VZ * iplane] = (jz + tau * Fz) * inv_rho;
+        o[I_VR * iplane] = (jr + tau * Fr) * inv_rho;
+        o[I_FZ * iplane] = Fz;
+        o[I_FR * iplane] = Fr;
+        o[I_PSI * iplane] = psi;
+        o[I_SZ * iplane] = sz;
+        o[I_SR * iplane] = sr;
+        if (ax) {
+          const C* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
+          o[I_DR * iplane] = dr[0];
+          o[I_DRR * iplane] = iso_r(dr, G::DZ);
+          o[I_DZR * iplane] = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
+        } else {
+          o[I_DR * iplane] = C(0);
+          o[I_DRR * iplane] = C(0);
+          o[I_DZR * iplane] = C(0);
+        }
+      }
+      if (MODE == 0 && srow && lc >= 2 && lc < G::FZ - 2) {
         const C vz = (jz + tau * Fz) * inv_rho, vr = (jr + tau * Fr) * inv_rho;
         C fe[9];
         equilibrium(rho, vz, vr, fe);
@@ -380,6 +407,15 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
         const C druz = iso_r(sUz + fi, G::FZ);
         const C dzur = iso_z(sUr + fi, G::FZ);
         const C drur = iso_r(sUr + fi, G::FZ);
+        if (MODE == 2) {
+          if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
+            C* o = inter + (size_t)j * P + (k0 + lc - 1);
+            o[I_G1 * iplane] = druz;
+            o[I_G2 * iplane] = dzur;
+            o[I_G3 * iplane] = drur;
+          }
+          return;
+        }
         const C rho = sRho[fi], uz = sUz[fi], ur = sUr[fi];
         const C mu = rho * (tau - C(0.5)) * C(1.0 / 3.0);
         S_ = -rho * ur * inv_r;
@@ -391,11 +427,21 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
 #pragma unroll
         for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] += hw * h[i];
       }
+      if (MODE == 2) {
+        if (!ax && lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
+          C* o = inter + (size_t)j * P + (k0 + lc - 1);
+          o[I_G1 * iplane] = C(0);
+          o[I_G2 * iplane] = C(0);
+          o[I_G3 * iplane] = C(0);
+        }
+        return;
+      }
       sS[si] = S_;
       sHz[si] = Hz;
       sHr[si] = Hr;
     }
   });
+  if (MODE == 2) return;
   __syncthreads();
 
   // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
@@ -598,19 +644,20 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_kernel(const InstDesc* __r
   }
 }
 
-template <class S, int BZ, int BR, bool RB>
+template <class S, int BZ, int BR, int MODE>
 cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
-                     cudaStream_t s) {
+                     cudaStream_t s, void* inter = nullptr, size_t iplane = 0) {
   using C = typename Store<S>::C;
   constexpr size_t smem = Geo<C, BZ, BR>::bytes;
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, RB>,
+    const cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  lbm_kernel<S, BZ, BR, RB><<<ntiles, NT, smem, s>>>(d, ti, toff, parity);
+  lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
+                                                       iplane);
   return cudaGetLastError();
 }
 
@@ -630,8 +677,8 @@ cudaError_t dispatch(bool macro, int tz, int tr, const InstDesc* d, const int* t
   if (nt <= 0) return cudaSuccess;
 #define AMLBM_TILE(TZ, TR)                                                \
   if (tz == TZ && tr == TR)                                               \
-    return macro ? launch_t<S, TZ, TR, true>(d, ti, nt, toff, par, s)     \
-                 : launch_t<S, TZ, TR, false>(d, ti, nt, toff, par, s);
+    return macro ? launch_t<S, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
+                 : launch_t<S, TZ, TR, 0>(d, ti, nt, toff, par, s);
   AMLBM_TILE(32, 8)
   AMLBM_TILE(64, 8)
   AMLBM_TILE(58, 8)
@@ -692,6 +739,16 @@ cudaError_t launch_step(int storage, int tz, int tr, const InstDesc* d, const in
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                          int toff, int parity, cudaStream_t s) {
   return dispatch_storage(storage, true, tz, tr, d, ti, nt, toff, parity, s);
+}
+
+cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
+                         void* inter, size_t plane, cudaStream_t s) {
+  if (storage == AMLBM_STORE_F64) {
+    if (tz == 32 && tr == 8) return launch_t<double, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
+  } else if (storage == AMLBM_STORE_F32) {
+    if (tz == 32 && tr == 8) return launch_t<float, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_init(int storage, const InstDesc* d, int inst, int Nz, int Nr, const double* rho,
