@@ -234,17 +234,28 @@ typedef struct amlbm_instance {
   amlbm_bc bc;
 } amlbm_instance;
 
-/* Tile shape of the fused step kernel (sites along z x sites along r).
- * tile_z = tile_r = 0 lets the library choose. */
+/* How a timestep is launched.  FUSED: one kernel per tile computes the whole
+ * update, recomputing forces and velocities on a 3-site halo.  SPLIT: a force
+ * kernel writes u and u^eq per site, then a collide-stream kernel reads them with
+ * a halo (less recomputation, 16 or 32 more bytes per site through L2).  Both
+ * give bit-identical states. */
+#define AMLBM_SCHED_AUTO 0
+#define AMLBM_SCHED_FUSED 1
+#define AMLBM_SCHED_SPLIT 2
+
+/* Schedule and tile shape (sites along z x sites along r) of the step kernels;
+ * all zero lets the library choose. */
 typedef struct amlbm_tune {
   int tile_z, tile_r;
   int graph_chunk; /* steps per captured CUDA graph in amlbm_batch_step (0 = no graph) */
+  int schedule;    /* AMLBM_SCHED_* */
 } amlbm_tune;
 
 typedef struct amlbm_batch amlbm_batch;
 
-/* Supported tiles for a storage form, as pairs (tile_z, tile_r); returns the count. */
-int amlbm_tiles(int storage, int* tz, int* tr, int cap);
+/* Tiles compiled for a storage form and schedule, as pairs (tile_z, tile_r);
+ * returns the count (tz, tr may be NULL to query it). */
+int amlbm_tiles(int storage, int schedule, int* tz, int* tr, int cap);
 
 size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst);
 

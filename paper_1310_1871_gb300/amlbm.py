@@ -66,7 +66,11 @@ OBJECTIVE = {"a2sq": 0, "neck": 1}
 
 
 class Tune(ctypes.Structure):
-    _fields_ = [("tile_z", ctypes.c_int), ("tile_r", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
+    _fields_ = [("tile_z", ctypes.c_int), ("tile_r", ctypes.c_int), ("graph_chunk", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
+
+
+SCHEDULE = {"auto": 0, "fused": 1, "split": 2}
 
 
 EXPORTS = [
@@ -108,7 +112,7 @@ def load(build_if_missing: bool = True):
         lib.amlbm_device_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip)]
         lib.amlbm_destroy.argtypes = [vp]
         lib.amlbm_destroy.restype = None
-        lib.amlbm_tiles.argtypes = [ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
+        lib.amlbm_tiles.argtypes = [ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ip]
         lib.amlbm_batch_workspace_bytes.argtypes = [ip, ctypes.POINTER(InstanceC)]
         lib.amlbm_batch_workspace_bytes.restype = sz
         lib.amlbm_batch_create.argtypes = [ip, ctypes.POINTER(InstanceC), ctypes.POINTER(Tune), vp, vp,
@@ -189,7 +193,7 @@ class InstanceSpec:
 class Batch:
     """Independent lattices stepped together, one kernel launch per timestep."""
 
-    def __init__(self, specs, storage="f32", tile=None, graph_chunk=0, stream=None):
+    def __init__(self, specs, storage="f32", tile=None, graph_chunk=0, stream=None, schedule="auto"):
         import torch
         self.lib = load()
         if not torch.cuda.is_available():
@@ -208,7 +212,10 @@ class Batch:
         base = self.workspace.data_ptr()
         aligned = (base + 255) // 256 * 256
         sh, self.stream = _stream_handle(stream)
-        tune = Tune(*(tile if tile else (0, 0)), int(graph_chunk))
+        sched = SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule)
+        if tile and not sched:
+            sched = SCHEDULE["fused"]
+        tune = Tune(*(tile if tile else (0, 0)), int(graph_chunk), sched)
         h = ctypes.c_void_p()
         _check(self.lib, self.lib.amlbm_batch_create(n, arr, ctypes.byref(tune), sh,
                                                      ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)))
@@ -378,12 +385,13 @@ class Lattice:
             pass
 
 
-def tiles(storage="f32"):
+def tiles(storage="f32", schedule="fused"):
     lib = load()
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
-    n = lib.amlbm_tiles(st, None, None, 0)
+    sc = SCHEDULE[schedule] if isinstance(schedule, str) else int(schedule)
+    n = lib.amlbm_tiles(st, sc, None, None, 0)
     tz, tr = (ctypes.c_int * n)(), (ctypes.c_int * n)()
-    lib.amlbm_tiles(st, tz, tr, n)
+    lib.amlbm_tiles(st, sc, tz, tr, n)
     return list(zip(tz, tr))
 
 

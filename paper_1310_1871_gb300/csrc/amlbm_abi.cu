@@ -54,14 +54,15 @@ amlbm_bc default_bc() {
   return b;
 }
 
-// Tile choice when the caller gives none: the first shape of a preference
-// list (fastest first on the 64-drop sweep) that still gives every SM two
-// CTAs over the whole batch, else the smallest tile.
-void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* tz, int* tr) {
-  static const int pref64[][2] = {{58, 8}, {26, 8}};
-  static const int pref32[][2] = {{26, 16}, {58, 8}, {32, 16}, {32, 8}};
+// Schedule and tile when the caller gives none: the split schedule with the
+// first tile of a preference list (fastest first on the 64-drop sweep) that
+// still gives every SM two CTAs over the whole batch, else the smallest tile.
+void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched, int* tz, int* tr) {
+  static const int pref64[][2] = {{32, 16}, {64, 8}, {32, 8}};
+  static const int pref32[][2] = {{64, 8}, {32, 16}, {64, 4}, {32, 8}};
   const bool f64 = storage == AMLBM_STORE_F64;
-  const int n = f64 ? 2 : 4;
+  const int n = f64 ? 3 : 4;
+  *sched = amlbm::SCHED_SPLIT;
   for (int c = 0; c < n; ++c) {
     const int z = f64 ? pref64[c][0] : pref32[c][0], r = f64 ? pref64[c][1] : pref32[c][1];
     long long tiles = 0;
@@ -110,9 +111,10 @@ int validate(const amlbm_instance& I, int idx) {
 
 struct Layout {
   size_t total = 0;
-  size_t desc = 0, tiles = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0, unpack = 0;
-  std::vector<size_t> f0, f1, p0, p1, rho, uz, ur;
-  int ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
+  size_t desc = 0, tiles = 0, rb_tiles = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
+         unpack = 0;
+  std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur;
+  int ntiles = 0, rb_ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
 };
 
 Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz, int tr) {
@@ -122,12 +124,14 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   const size_t n = inst.size();
   for (const auto& I : inst) {
     L.ntiles += ((I.Nz + tz - 1) / tz) * ((I.Nr + tr - 1) / tr);
+    L.rb_ntiles += ((I.Nz + 31) / 32) * ((I.Nr + 7) / 8);
     L.maxN = std::max(L.maxN, I.Nz * I.Nr);
     L.maxNz = std::max(L.maxNz, I.Nz);
     L.diag_nblk = std::max(L.diag_nblk, amlbm::diag_blocks(I.Nz, I.Nr));
   }
   L.desc = take(n * sizeof(InstDesc));
   L.tiles = take((size_t)L.ntiles * sizeof(int));
+  L.rb_tiles = take((size_t)L.rb_ntiles * sizeof(int));
   L.diag_part = take((size_t)L.diag_nblk * 8 * sizeof(double));
   L.diag_cols = take((size_t)L.maxNz * sizeof(double));
   L.diag_out = take(16 * sizeof(double));
@@ -139,6 +143,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
     L.f1.push_back(take(9 * plane * elem_bytes(storage)));
     L.p0.push_back(take(plane * compute_bytes(storage)));
     L.p1.push_back(take(plane * compute_bytes(storage)));
+    L.uv.push_back(take(4 * plane * compute_bytes(storage)));
     L.rho.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
     L.uz.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
     L.ur.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
@@ -150,7 +155,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
 }  // namespace
 
 struct amlbm_batch {
-  int n = 0, storage = 0, tz = 0, tr = 0, graph_chunk = 0;
+  int n = 0, storage = 0, sched = 0, tz = 0, tr = 0, graph_chunk = 0;
   cudaStream_t stream = nullptr;
   char* arena = nullptr;
   size_t arena_bytes = 0;
@@ -160,6 +165,7 @@ struct amlbm_batch {
   std::vector<long long> steps;  // per instance, since its fields were set
   InstDesc* d_desc = nullptr;
   int* d_tiles = nullptr;
+  int* d_rb_tiles = nullptr;
   int parity = 0;
   long long sites = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -173,7 +179,7 @@ namespace {
 
 int launch_steps_direct(amlbm_batch* b, int n) {
   for (int s = 0; s < n; ++s) {
-    const cudaError_t e = amlbm::launch_step(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles,
+    const cudaError_t e = amlbm::launch_step(b->storage, b->sched, b->tz, b->tr, b->d_desc, b->d_tiles,
                                              b->L.ntiles, 0, b->parity, b->stream);
     if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
     b->parity ^= 1;
@@ -188,7 +194,7 @@ int ensure_graph(amlbm_batch* b, int parity) {
   int p = parity;
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < b->graph_chunk && e == cudaSuccess; ++s) {
-    e = amlbm::launch_step(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles, b->L.ntiles, 0, p,
+    e = amlbm::launch_step(b->storage, b->sched, b->tz, b->tr, b->d_desc, b->d_tiles, b->L.ntiles, 0, p,
                            b->stream);
     p ^= 1;
   }
@@ -214,20 +220,29 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     if (rc) return rc;
   }
   const int storage = inst[0].bc.storage;
-  int tz = 0, tr = 0;
-  if (tune && (tune->tile_z || tune->tile_r)) {
+  int tz = 0, tr = 0, sched = 0;
+  if (tune && (tune->tile_z || tune->tile_r || tune->schedule)) {
     tz = tune->tile_z;
     tr = tune->tile_r;
-    if (!amlbm::tile_supported(storage, tz, tr))
+    sched = tune->schedule ? tune->schedule : AMLBM_SCHED_SPLIT;
+    if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT)
+      return fail(AMLBM_EINVAL, "bad schedule");
+    if (!tz && !tr) {
+      int s2;
+      pick_tile(storage, inst, &s2, &tz, &tr);
+      if (!amlbm::tile_supported(storage, sched, tz, tr)) { tz = 32; tr = 8; }
+    }
+    if (!amlbm::tile_supported(storage, sched, tz, tr))
       return fail(AMLBM_EINVAL, "tile " + std::to_string(tz) + "x" + std::to_string(tr) +
-                                    " is not compiled for this storage (see amlbm_tiles)");
+                                    " is not compiled for this storage and schedule (see amlbm_tiles)");
   } else {
-    pick_tile(storage, inst, &tz, &tr);
+    pick_tile(storage, inst, &sched, &tz, &tr);
   }
   amlbm_batch* b = new (std::nothrow) amlbm_batch();
   if (!b) return fail(AMLBM_ENOMEM, "host allocation failed");
   b->n = (int)inst.size();
   b->storage = storage;
+  b->sched = sched;
   b->tz = tz;
   b->tr = tr;
   b->graph_chunk = tune ? std::max(0, tune->graph_chunk) : 0;
@@ -253,8 +268,9 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     b->arena_bytes = b->L.total;
   }
   const Layout& L = b->L;
-  std::vector<int> tiles;
+  std::vector<int> tiles, rb_tiles;
   tiles.reserve(L.ntiles);
+  rb_tiles.reserve(L.rb_ntiles);
   for (int i = 0; i < b->n; ++i) {
     const amlbm_instance& I = inst[i];
     InstDesc d;
@@ -269,6 +285,9 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.tiles_z = (I.Nz + tz - 1) / tz;
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
+    d.rb_tiles_z = (I.Nz + 31) / 32;
+    d.rb_tiles_r = (I.Nr + 7) / 8;
+    d.rb_tile_base = (int)rb_tiles.size();
     d.tau = I.tau;
     d.G = I.G;
     d.rho0 = I.rho0;
@@ -278,21 +297,27 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.f[1] = b->arena + L.f1[i];
     d.psi[0] = b->arena + L.p0[i];
     d.psi[1] = b->arena + L.p1[i];
+    d.uv = b->arena + L.uv[i];
     d.rho_out = reinterpret_cast<double*>(b->arena + L.rho[i]);
     d.uz_out = reinterpret_cast<double*>(b->arena + L.uz[i]);
     d.ur_out = reinterpret_cast<double*>(b->arena + L.ur[i]);
     for (int t = 0; t < d.tiles_z * d.tiles_r; ++t) tiles.push_back(i);
+    for (int t = 0; t < d.rb_tiles_z * d.rb_tiles_r; ++t) rb_tiles.push_back(i);
     b->desc.push_back(d);
     b->sites += (long long)I.Nz * I.Nr;
   }
   b->steps.assign(b->n, 0);
   b->d_desc = reinterpret_cast<InstDesc*>(b->arena + L.desc);
   b->d_tiles = reinterpret_cast<int*>(b->arena + L.tiles);
+  b->d_rb_tiles = reinterpret_cast<int*>(b->arena + L.rb_tiles);
   cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), b->desc.size() * sizeof(InstDesc),
                                   cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice,
                         b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_rb_tiles, rb_tiles.data(), rb_tiles.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     if (b->owns) cudaFree(b->arena);
@@ -340,9 +365,9 @@ int init_host(amlbm_batch* b, int k, const double* rho, const double* uz, const 
 
 int macro_for(amlbm_batch* b, int k) {
   const InstDesc& d = b->desc[k];
-  const int nt = d.tiles_z * d.tiles_r;
-  const cudaError_t e = amlbm::launch_macro(b->storage, b->tz, b->tr, b->d_desc, b->d_tiles, nt,
-                                            d.tile_base, b->parity, b->stream);
+  const int nt = d.rb_tiles_z * d.rb_tiles_r;
+  const cudaError_t e = amlbm::launch_macro(b->storage, 32, 8, b->d_desc, b->d_rb_tiles, nt,
+                                            d.rb_tile_base, b->parity, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
   return AMLBM_OK;
 }
@@ -407,7 +432,9 @@ extern "C" {
 const char* amlbm_last_error(void) { return g_err.c_str(); }
 const char* amlbm_version(void) { return "amlbm 0.1 (sm_103a)"; }
 
-int amlbm_tiles(int storage, int* tz, int* tr, int cap) { return amlbm::tile_list(storage, tz, tr, cap); }
+int amlbm_tiles(int storage, int schedule, int* tz, int* tr, int cap) {
+  return amlbm::tile_list(storage, schedule, tz, tr, cap);
+}
 
 size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
   if (n < 1 || !inst) return 0;
@@ -416,10 +443,12 @@ size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
     if (validate(v[i], i)) return 0;
   // room for whichever compiled tile the tune picks (the tile list grows with
   // the number of tiles)
-  int tz[32], tr[32];
-  const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, tz, tr, 32));
   size_t need = 0;
-  for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);
+  for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_SPLIT; ++sc) {
+    int tz[32], tr[32];
+    const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, sc, tz, tr, 32));
+    for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);
+  }
   return need;
 }
 

@@ -14,11 +14,13 @@ namespace amlbm {
 struct InstDesc {
   int Nz, Nr, P;
   int wall, axisym, src;
-  int tiles_z, tiles_r, tile_base;
+  int tiles_z, tiles_r, tile_base;     // tiling of the step kernels
+  int rb_tiles_z, rb_tiles_r, rb_tile_base;  // 32 x 8 tiling of the read-back kernel
   int shift;  // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
   double tau, G, rho0, gz, rho_ref;
   void* f[2];
   void* psi[2];
+  void* uv;         // split schedule: u_z, u_r, u^eq_z, u^eq_r, 4 planes [Nr][P] of the compute type
   double* rho_out;  // [Nr][Nz] scratch for read-back and diagnostics
   double* uz_out;
   double* ur_out;
@@ -27,8 +29,10 @@ struct InstDesc {
 // Kernel launchers (defined in amlbm_step.cu).  storage = AMLBM_STORE_*.
 // Every launcher returns the cudaGetLastError() of its launch.
 // The step and macro kernels run CTAs for the flattened tiles
-// [toff, toff + ntiles) of the batch.
-cudaError_t launch_step(int storage, int tz, int tr, const InstDesc* d_desc,
+// [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
+// (force kernel, then collide-stream kernel).
+enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
+cudaError_t launch_step(int storage, int schedule, int tz, int tr, const InstDesc* d_desc,
                         const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d_desc,
                          const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
@@ -55,8 +59,8 @@ cudaError_t launch_diag(int storage, const InstDesc* d_desc, int inst, int Nz, i
                         int parity, double zc, double R, double rho_l, double rho_v,
                         double* partials, int nblk, double* cols, double* out, cudaStream_t s);
 int diag_blocks(int Nz, int Nr);
-bool tile_supported(int storage, int tz, int tr);
-int tile_list(int storage, int* tz, int* tr, int cap);
+bool tile_supported(int storage, int schedule, int tz, int tr);
+int tile_list(int storage, int schedule, int* tz, int* tr, int cap);
 size_t step_smem_bytes(int storage, int tz, int tr);
 
 // Access to a lattice context for entry points defined outside the ABI file

@@ -208,11 +208,12 @@ struct Tile {
 };
 
 __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_inst, int toff, int BZ,
-                                        int BR) {
+                                        int BR, bool readback = false) {
   Tile t;
   const int b = blockIdx.x + toff;
   t.inst = tile_inst[b];
-  const int tb = descs[t.inst].tile_base, tz = descs[t.inst].tiles_z;
+  const int tb = readback ? descs[t.inst].rb_tile_base : descs[t.inst].tile_base;
+  const int tz = readback ? descs[t.inst].rb_tiles_z : descs[t.inst].tiles_z;
   const int l = b - tb;
   t.k0 = (l % tz) * BZ;
   t.j0 = (l / tz) * BR;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
   C* sUr = sUz + G::nF;
   C* sFs = sUr + G::nF;
 
-  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR, READBACK);
   const InstDesc& D = descs[T.inst];
   const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
   const size_t plane = (size_t)P * Nr;
@@ -489,6 +490,253 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
   });
 }
 
+
+// ------------------------------------------------------------ split schedule --
+// The same update as lbm_kernel MODE 0 in two kernels, so that the heavy
+// per-site chain runs once per site instead of on a halo of 3:
+//   force_kernel  : psi tile + 4, d_r psi on tile + 2, 1D d_r psi on tile
+//                   (z + 2); per site of the tile the moments, forces, u and u^eq,
+//                   written to four planes;
+//   stream_kernel : u with a halo of 3 (ghost rows mirrored), populations on the
+//                   tile + 1, collision, gradients and sources, gather-stream.
+// The arithmetic is the fused kernel's, operation for operation, so the two
+// schedules give bit-identical states.
+template <class C, int BZ, int BR>
+struct GeoA {
+  static constexpr int HP = 4, HD = 2;
+  static constexpr int PZ = BZ + 2 * HP, PR = BR + 2 * HP;
+  static constexpr int DZ = BZ + 2 * HD, DR = BR + 2 * HD;
+  static constexpr int EZ = BZ + 2 * HD, ER = BR;
+  static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER;
+  static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
+  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(nP + nD + nE);
+};
+
+template <class S, int BZ, int BR>
+__global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ descs,
+                                                   const int* __restrict__ tile_inst, int toff,
+                                                   int parity) {
+  using C = typename Store<S>::C;
+  using G = GeoA<C, BZ, BR>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* colmap = reinterpret_cast<int*>(smem_raw);
+  int* rowmap = colmap + G::PZ;
+  C* sPsi = reinterpret_cast<C*>(smem_raw + G::int_bytes);
+  C* sDr = sPsi + G::nP;
+  C* sD1 = sDr + G::nD;
+  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const InstDesc& D = descs[T.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  const size_t plane = (size_t)P * Nr;
+  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
+  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
+  C* __restrict__ uv = static_cast<C*>(D.uv);
+  const bool ax = D.axisym != 0;
+  const int shift = D.shift;
+  const C tau = C(D.tau), Gc = C(D.G), gz = C(D.gz), rho0 = C(D.rho0), rref = C(D.rho_ref),
+          gfac = -(Gc / C(2)) * C(1.0 / 9.0), inv_rho0 = rcp_c(rho0);
+
+  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
+  for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
+  __syncthreads();
+  for_tile<G::PR, G::PZ>([&](int lr, int lc) {
+    sPsi[lr * G::PZ + lc] = psin[(size_t)rowmap[lr] * P + colmap[lc]];
+  });
+  __syncthreads();
+  if (ax) {
+    for_tile<G::DR, G::DZ>([&](int lr, int lc) {
+      sDr[lr * G::DZ + lc] = iso_r(sPsi + (lr + G::HP - G::HD) * G::PZ + (lc + G::HP - G::HD), G::PZ);
+    });
+    for_tile<G::ER, G::EZ>([&](int lr, int lc) {
+      sD1[lr * G::EZ + lc] = d1(sPsi + (lr + G::HP) * G::PZ + (lc + G::HP - G::HD), G::PZ);
+    });
+    __syncthreads();
+  }
+  for_tile<BR, BZ>([&](int lr, int lc) {
+    const int j = j0 + lr, k = k0 + lc;
+    if (j >= Nr || k >= Nz) return;
+    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+    const C* p = sPsi + (lr + G::HP) * G::PZ + (lc + G::HP);
+    const C psi = p[0];
+    const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
+    const S* fp = fin + (size_t)j * P + k;
+    C f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fp[i * plane]) + C(w_(i)) * sb;
+    const C rho = moment0(f);
+    const C jz = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    const C jr = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
+    const int Z = G::PZ;
+    const C sz = C(1.0 / 9.0) * (p[1] - p[-1]) +
+                 C(1.0 / 36.0) * ((p[Z + 1] - p[Z - 1]) + (p[-Z + 1] - p[-Z - 1]));
+    const C sr = C(1.0 / 9.0) * (p[Z] - p[-Z]) +
+                 C(1.0 / 36.0) * ((p[Z + 1] - p[-Z + 1]) + (p[Z - 1] - p[-Z - 1]));
+    C Fz = -Gc * psi * sz, Fr = -Gc * psi * sr;
+    if (ax) {
+      const C* dr = sDr + (lr + G::HD) * G::DZ + (lc + G::HD);
+      const C Drr = iso_r(dr, G::DZ);
+      const C Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD), 1);
+      const C g = gfac * psi * inv_r;
+      Fz += g * Dzr;
+      Fr += g * (Drr - dr[0] * inv_r);
+    }
+    Fz += rho * gz;
+    const C inv_rho = rcp_c(rho);
+    C* o = uv + (size_t)j * P + k;
+    o[0] = (jz + C(0.5) * Fz) * inv_rho;
+    o[plane] = (jr + C(0.5) * Fr) * inv_rho;
+    o[2 * plane] = (jz + tau * Fz) * inv_rho;
+    o[3 * plane] = (jr + tau * Fr) * inv_rho;
+  });
+}
+
+template <class C, int BZ, int BR>
+struct GeoB {
+  static constexpr int HF = 3;
+  static constexpr int FZ = BZ + 2 * HF, FR = BR + 2 * HF;
+  static constexpr int SZ = BZ + 2, SR = BR + 2;
+  static constexpr int nF = FZ * FR, nS = SZ * SR;
+  static constexpr int int_bytes = (FZ * 4 + 15) / 16 * 16;
+  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(2 * nF + 13 * nS);
+};
+
+template <class S, int BZ, int BR>
+__global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__ descs,
+                                                    const int* __restrict__ tile_inst, int toff,
+                                                    int parity) {
+  using C = typename Store<S>::C;
+  using G = GeoB<C, BZ, BR>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* colmap = reinterpret_cast<int*>(smem_raw);
+  C* sUz = reinterpret_cast<C*>(smem_raw + G::int_bytes);
+  C* sUr = sUz + G::nF;
+  C* sRho = sUr + G::nF;
+  C* sS = sRho + G::nS;
+  C* sHz = sS + G::nS;
+  C* sHr = sHz + G::nS;
+  C* sFs = sHr + G::nS;
+  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const InstDesc& D = descs[T.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  const size_t plane = (size_t)P * Nr;
+  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
+  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
+  const C* __restrict__ uv = static_cast<const C*>(D.uv);
+  const bool ax = D.axisym != 0;
+  const int shift = D.shift;
+  const C tau = C(D.tau), omega = C(1) / tau, rho0 = C(D.rho0), rref = C(D.rho_ref),
+          inv_rho0 = rcp_c(rho0);
+  const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
+
+  for (int i = threadIdx.x; i < G::FZ; i += NT) colmap[i] = wrapz(k0 - G::HF + i, Nz);
+  __syncthreads();
+  // u on the tile + 3; ghost rows (depth 2) by the mirror rules of the fused kernel
+  if (ax) {
+    for_tile<G::FR, G::FZ>([&](int lr, int lc) {
+      const int j = j0 - G::HF + lr;
+      int m = j;
+      C sgz = C(1), sgr = C(1);
+      if (j == -1 || j == -2) {
+        m = -1 - j;
+        sgr = C(-1);
+      } else if (j == Nr || j == Nr + 1) {
+        m = 2 * Nr - 1 - j;
+        sgr = C(-1);
+        sgz = noslip ? C(-1) : C(1);
+      } else if (j < 0 || j >= Nr) {
+        return;  // never read
+      }
+      const size_t o = (size_t)m * P + colmap[lc];
+      sUz[lr * G::FZ + lc] = sgz * uv[o];
+      sUr[lr * G::FZ + lc] = sgr * uv[plane + o];
+    });
+  }
+  // populations on the tile + 1: rho and the collision towards f^eq(rho, u^eq)
+  for_tile<G::SR, G::SZ>([&](int lr, int lc) {
+    const int j = j0 - 1 + lr;
+    if (j < 0 || j >= Nr) return;
+    const size_t o = (size_t)j * P + colmap[lc + G::HF - 1];
+    const C sb = shift_base(shift, psin[o], inv_rho0, rho0, rref);
+    C f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fin[i * plane + o]) + C(w_(i)) * sb;
+    const C rho = moment0(f);
+    const C vz = uv[2 * plane + o], vr = uv[3 * plane + o];
+    C fe[9];
+    equilibrium(rho, vz, vr, fe);
+    const int si = lr * G::SZ + lc;
+    sRho[si] = rho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = f[i] + (fe[i] - f[i]) * omega;
+  });
+  __syncthreads();
+  // gradients and sources on the tile + 1
+  const bool link = D.src == AMLBM_SRC_LINK;
+  for_tile<G::SR, G::SZ>([&](int lr, int lc) {
+    const int j = j0 - 1 + lr;
+    if (j < 0 || j >= Nr) return;
+    const int si = lr * G::SZ + lc;
+    C S_ = C(0), Hz = C(0), Hr = C(0);
+    if (ax) {
+      const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+      const int fi = (lr + 2) * G::FZ + (lc + 2);
+      const C druz = iso_r(sUz + fi, G::FZ);
+      const C dzur = iso_z(sUr + fi, G::FZ);
+      const C drur = iso_r(sUr + fi, G::FZ);
+      const C rho = sRho[si], uz = sUz[fi], ur = sUr[fi];
+      const C mu = rho * (tau - C(0.5)) * C(1.0 / 3.0);
+      S_ = -rho * ur * inv_r;
+      Hz = (mu * (druz + dzur) - rho * ur * uz) * inv_r;
+      Hr = (C(2) * mu * (drur - ur * inv_r) - rho * ur * ur) * inv_r;
+      const C hw = link ? C(0.5) : C(1);
+      C h[9];
+      sources(S_, Hz, Hr, h);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] += hw * h[i];
+    }
+    sS[si] = S_;
+    sHz[si] = Hz;
+    sHr[si] = Hr;
+  });
+  __syncthreads();
+  S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
+  C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
+  for_tile<BR, BZ>([&](int lr, int lc) {
+    const int j = j0 + lr, k = k0 + lc;
+    if (j >= Nr || k >= Nz) return;
+    const bool edge = (j == 0) || (j == Nr - 1);
+    C fn[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
+      if (edge) {
+        if (cr_(i) > 0 && j == 0) {
+          sl = lr + 1; ii = mirror_(i);
+        } else if (cr_(i) < 0 && j == Nr - 1) {
+          sl = lr + 1;
+          if (noslip) { sc = lc + 1; ii = opp_(i); }
+          else { ii = mirror_(i); }
+        }
+      }
+      fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
+    }
+    if (link) {
+      const int di = (lr + 1) * G::SZ + (lc + 1);
+      C h[9];
+      sources(sS[di], sHz[di], sHr[di], h);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fn[i] += C(0.5) * h[i];
+    }
+    const C rho = moment0(fn);
+    const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
+    const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
+    S* o = fout + (size_t)j * P + k;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+    psout[(size_t)j * P + k] = psi;
+  });
+}
+
 // f = f^eq(rho, u) (no force shift) and psi of the new state.
 template <class S>
 __global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const double* rho_in,
@@ -661,24 +909,69 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
   return cudaGetLastError();
 }
 
+template <class S, int BZ, int BR>
+cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
+                           cudaStream_t s) {
+  using C = typename Store<S>::C;
+  constexpr size_t sa = GeoA<C, BZ, BR>::bytes, sbb = GeoB<C, BZ, BR>::bytes;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(force_kernel<S, BZ, BR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(stream_kernel<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sbb);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  force_kernel<S, BZ, BR><<<ntiles, NT, sa, s>>>(d, ti, toff, parity);
+  stream_kernel<S, BZ, BR><<<ntiles, NT, sbb, s>>>(d, ti, toff, parity);
+  return cudaGetLastError();
+}
+
 // Tile shapes compiled for each storage form.
-struct TileEntry { int storage, tz, tr; };
-#define AMLBM_TILES_16(ST) \
-  {ST, 32, 8}, {ST, 64, 8}, {ST, 58, 8}, {ST, 58, 16}, {ST, 26, 16}, {ST, 32, 16}, {ST, 122, 8}
+struct TileEntry { int storage, sched, tz, tr; };
+#define AMLBM_TILES_16(ST)                                                                    \
+  {ST, SCHED_FUSED, 32, 8}, {ST, SCHED_FUSED, 64, 8}, {ST, SCHED_FUSED, 58, 8},               \
+  {ST, SCHED_FUSED, 58, 16}, {ST, SCHED_FUSED, 26, 16}, {ST, SCHED_FUSED, 32, 16},            \
+  {ST, SCHED_FUSED, 122, 8}, {ST, SCHED_SPLIT, 32, 8}, {ST, SCHED_SPLIT, 64, 8},              \
+  {ST, SCHED_SPLIT, 32, 16}, {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 128, 8},            \
+  {ST, SCHED_SPLIT, 64, 4}
 constexpr TileEntry kTiles[] = {
-    {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 64, 8}, {AMLBM_STORE_F64, 58, 8}, {AMLBM_STORE_F64, 26, 8},
+    {AMLBM_STORE_F64, SCHED_FUSED, 32, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 64, 8},
+    {AMLBM_STORE_F64, SCHED_FUSED, 58, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 26, 8},
+    {AMLBM_STORE_F64, SCHED_SPLIT, 32, 8}, {AMLBM_STORE_F64, SCHED_SPLIT, 64, 8},
+    {AMLBM_STORE_F64, SCHED_SPLIT, 32, 16},
     AMLBM_TILES_16(AMLBM_STORE_F32), AMLBM_TILES_16(AMLBM_STORE_F16), AMLBM_TILES_16(AMLBM_STORE_BF16),
 };
 #undef AMLBM_TILES_16
 
 template <class S>
-cudaError_t dispatch(bool macro, int tz, int tr, const InstDesc* d, const int* ti, int nt, int toff,
-                     int par, cudaStream_t s) {
+cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, const int* ti, int nt,
+                     int toff, int par, cudaStream_t s) {
   if (nt <= 0) return cudaSuccess;
+  if (sched == SCHED_SPLIT && !macro) {
+#define AMLBM_SPLIT(TZ, TR) \
+  if (tz == TZ && tr == TR) return launch_split_t<S, TZ, TR>(d, ti, nt, toff, par, s);
+    AMLBM_SPLIT(32, 8)
+    AMLBM_SPLIT(64, 8)
+    AMLBM_SPLIT(32, 16)
+    if constexpr (!std::is_same<S, double>::value) {
+      AMLBM_SPLIT(64, 16)
+      AMLBM_SPLIT(128, 8)
+      AMLBM_SPLIT(64, 4)
+    }
+#undef AMLBM_SPLIT
+    return cudaErrorInvalidValue;
+  }
 #define AMLBM_TILE(TZ, TR)                                                \
   if (tz == TZ && tr == TR)                                               \
     return macro ? launch_t<S, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
                  : launch_t<S, TZ, TR, 0>(d, ti, nt, toff, par, s);
+  if (macro) {  // read-back always uses a fused tile compiled for every storage
+    AMLBM_TILE(32, 8)
+    return cudaErrorInvalidValue;
+  }
   AMLBM_TILE(32, 8)
   AMLBM_TILE(64, 8)
   AMLBM_TILE(58, 8)
@@ -694,29 +987,29 @@ cudaError_t dispatch(bool macro, int tz, int tr, const InstDesc* d, const int* t
   return cudaErrorInvalidValue;
 }
 
-cudaError_t dispatch_storage(int storage, bool macro, int tz, int tr, const InstDesc* d,
+cudaError_t dispatch_storage(int storage, bool macro, int sched, int tz, int tr, const InstDesc* d,
                              const int* ti, int nt, int toff, int par, cudaStream_t s) {
   switch (storage) {
-    case AMLBM_STORE_F64: return dispatch<double>(macro, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_F32: return dispatch<float>(macro, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_F16: return dispatch<__half>(macro, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_BF16: return dispatch<__nv_bfloat16>(macro, tz, tr, d, ti, nt, toff, par, s);
+    case AMLBM_STORE_F64: return dispatch<double>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
+    case AMLBM_STORE_F32: return dispatch<float>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
+    case AMLBM_STORE_F16: return dispatch<__half>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
+    case AMLBM_STORE_BF16: return dispatch<__nv_bfloat16>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-bool tile_supported(int storage, int tz, int tr) {
+bool tile_supported(int storage, int sched, int tz, int tr) {
   for (const auto& e : kTiles)
-    if (e.storage == storage && e.tz == tz && e.tr == tr) return true;
+    if (e.storage == storage && e.sched == sched && e.tz == tz && e.tr == tr) return true;
   return false;
 }
 
-int tile_list(int storage, int* tz, int* tr, int cap) {
+int tile_list(int storage, int sched, int* tz, int* tr, int cap) {
   int n = 0;
   for (const auto& e : kTiles)
-    if (e.storage == storage) {
+    if (e.storage == storage && e.sched == sched) {
       if (n < cap && tz && tr) { tz[n] = e.tz; tr[n] = e.tr; }
       ++n;
     }
@@ -732,13 +1025,13 @@ size_t step_smem_bytes(int storage, int tz, int tr) {
   return ib + c * (size_t)(nA + 3 * nF + 9 * nS);
 }
 
-cudaError_t launch_step(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
-                        int toff, int parity, cudaStream_t s) {
-  return dispatch_storage(storage, false, tz, tr, d, ti, nt, toff, parity, s);
+cudaError_t launch_step(int storage, int sched, int tz, int tr, const InstDesc* d, const int* ti,
+                        int nt, int toff, int parity, cudaStream_t s) {
+  return dispatch_storage(storage, false, sched, tz, tr, d, ti, nt, toff, parity, s);
 }
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                          int toff, int parity, cudaStream_t s) {
-  return dispatch_storage(storage, true, tz, tr, d, ti, nt, toff, parity, s);
+  return dispatch_storage(storage, true, SCHED_FUSED, tz, tr, d, ti, nt, toff, parity, s);
 }
 
 cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
