@@ -18,6 +18,7 @@ Under torchrun (N > 1) every rank runs its own 64-instance batch (seeds offset b
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -41,13 +42,27 @@ WORKLOAD = ("batched sweep: 64 axisymmetric drops, R~U[10,60], grid 4R x 2R, G~U
             "tau~U[0.6,1.2], a2~U[0,0.08] on odd instances, seeds 1234+k")
 
 
-def config(sites, storage=STORAGE, tile=None):
+def config(sites, storage=STORAGE, tile=None, schedule=None):
     return {"workload": WORKLOAD, "instances": 64, "sites_per_step": int(sites),
-            "storage": f"{storage} shifted by W_i*rho_ref" if storage in ("f16", "bf16") else storage,
+            "storage": (f"{storage}, f_i - W_i*rho(psi) (site density recovered from psi)"
+                        if storage in ("f16", "bf16") else storage),
             "arithmetic": "f64" if storage == "f64" else "f32",
-            "tile": list(tile) if tile else None,
+            "schedule": schedule, "tile": list(tile) if tile else None,
             "l2": "flushed before every timed step (256 MB write); state 28 MB < L2",
-            "launch": "one kernel per timestep for all 64 instances"}
+            "launch": "every tile of all 64 instances in one launch per kernel per timestep"}
+
+
+def profiled_traffic(kernel_src):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    d = json.load(open(p))
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    if d.get("source_sha256") != sha:
+        return None, d.get("kernel")
+    return d.get("dram_bytes_per_launch"), d.get("kernel")
 
 
 def peaks():
@@ -114,9 +129,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seed0(rank):
+    """First seed of a rank's 64-instance batch: ranks run disjoint, independent batches."""
+    return 1234 + 64 * rank
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The largest per-rank value (the whole job is as slow as its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(sites_per_rank, steps, max_ms, world):
+    """Whole-job lattice updates per second (millions): every rank's sites, over the
+    slowest rank's time."""
+    return world * sites_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
 def build_batch(storage, rank, tile=None, graph_chunk=0, stream=None):
     from paper_1310_1871_gb300 import amlbm
-    inst = I.batch_sweep(64, seed0=1234 + 64 * rank)
+    inst = I.batch_sweep(64, seed0=rank_seed0(rank))
     specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
     b = amlbm.Batch(specs, storage=storage, tile=tile, graph_chunk=graph_chunk, stream=stream)
     for k, x in enumerate(inst):
@@ -155,6 +192,7 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         b, inst = build_batch(STORAGE, rank, stream=stream)
         sites = b.sites
+        sched, tile, lps = b.schedule, b.tile, b.launches_per_step
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -162,13 +200,10 @@ def run_gpu(args):
             t0 = time.perf_counter()
             times = time_steps(torch, b, args.steps, args.warmup, flush, stream)
             wall = time.perf_counter() - t0
-        total_ms = float(sum(times))
+        total_ms = max_over_ranks(float(sum(times)), world, "cuda")
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dist.barrier()
-            total_ms = float(t.item())
-        mlups = world * sites * args.steps / (total_ms * 1e-3) / 1e6
+        mlups = job_mlups(sites, args.steps, total_ms, world)
         avg_ms = total_ms / args.steps
         hbm, kind = peaks()
         achieved = BYTES_PER_LU[STORAGE] * sites / (avg_ms * 1e-3) / 1e9
@@ -193,24 +228,27 @@ def run_gpu(args):
                 b.diagnostics(k, zc=x.zc, R=x.R, rho_l=x.rho_l, rho_v=x.rho_v, check=False)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e_val = world * sites * e2e_steps / e2e_s / 1e6
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_val = world * sites * e2e_steps / float(t.item()) / 1e6
+        e2e_val = job_mlups(sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3, world)
         b.close()
 
         # the same workload in the other storage forms (plain FP64 is the
         # parity form; FP32 the unshifted single-precision form)
         compare = {}
+        adjoint = None
         if rank == 0 and not args.no_compare:
             for st in ("f64", "f32"):
                 bb, _ = build_batch(st, rank, stream=stream)
                 tt = time_steps(torch, bb, min(args.steps, 200), 3, flush, stream)
-                compare[st] = round(bb.sites * len(tt) / (sum(tt) * 1e-3) / 1e6, 1)
+                compare[st] = {"mlups": round(bb.sites * len(tt) / (sum(tt) * 1e-3) / 1e6, 1),
+                               "schedule": bb.schedule, "tile": list(bb.tile)}
                 bb.close()
-            compare[STORAGE] = round(mlups / world, 1)
+            compare[STORAGE] = {"mlups": round(mlups / world, 1), "schedule": sched, "tile": list(tile)}
+            compare["bf16_over_f64"] = round(compare[STORAGE]["mlups"] / compare["f64"]["mlups"], 2)
+            adjoint = adjoint_cost(torch)
 
+    traffic, tkernel = profiled_traffic(os.path.join(ROOT, "paper_1310_1871_gb300", "csrc", "amlbm_step.cu"))
+    kname = (f"lbm_persistent<__nv_bfloat16, {tile[0]}, {tile[1]}>" if sched == "fused"
+             else f"stream_kernel<__nv_bfloat16, {tile[0]}, {tile[1]}> + force_kernel")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(seconds=args.cpu_seconds)
@@ -219,24 +257,53 @@ def run_gpu(args):
             "metric": METRIC, "value": round(mlups, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config(sites),
+            "data": "synthetic", "config": config(sites, tile=tile, schedule=sched),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "traffic": None,
-                         "peak_kind": kind, "bytes_per_lu": BYTES_PER_LU[STORAGE],
-                         "kernel": "step_kernel<__nv_bfloat16>"},
+                         "frac": round(achieved / hbm, 4),
+                         "traffic": (round(traffic) if traffic and tkernel == kname else None),
+                         "peak_kind": f"{kind} (HBM copy bandwidth)", "bytes_per_lu": BYTES_PER_LU[STORAGE],
+                         "kernel": kname,
+                         "limiter": "instruction issue of the per-site stencil chain, not HBM"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "amlbm_batch_init_fields x64 (pinned host) + amlbm_batch_step(1) + "
                             "amlbm_batch_diagnostics x64"},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * lps,
             "clocks": clk.summary(),
             "compare_mlups": compare or None,
+            "adjoint": adjoint if (rank == 0 and not args.no_compare) else None,
             "wall_s_timed_loop": round(wall, 3),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def adjoint_cost(torch, T=2000):
+    """Cost of the discrete adjoint on the differentiable drop (512 x 128, R = 48, 16
+    Legendre amplitudes, a2^2 objective, checkpoints every 100 steps), FP32 and FP64:
+    wall time of amlbm_adjoint (forward with checkpoints + recomputation + reverse
+    sweep) over the wall time of the forward run alone."""
+    from paper_1310_1871_gb300 import amlbm
+    amps = I.legendre_amplitudes(16, 0.02, seed=2024)
+    out = {"workload": "differentiable drop 512 x 128, R=48, 16 amplitudes, J = a2(T)^2", "T": T,
+           "ckpt_every": 100}
+    for st in ("f32", "f64"):
+        lat = amlbm.Lattice(512, 128, tau=1.0, G=-5.0, storage=st)
+        lat.objective(200, amps, 256.0, 48.0)  # warm-up (kernel attributes, workspace)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.objective(T, amps, 256.0, 48.0)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        lat.adjoint(T, amps, 256.0, 48.0, ckpt_every=100)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        out[st] = {"forward_s": round(tf, 4), "adjoint_s": round(ta, 4), "ratio": round(ta / tf, 2)}
+        lat.close()
+    return out
 
 
 def cpu_baseline(seconds=15.0):

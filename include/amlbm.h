@@ -269,8 +269,11 @@ int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const doub
 int amlbm_batch_step(amlbm_batch* b, int n);
 int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f);
 int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out);
-/* Sites of all instances (the work of one batch timestep) and kernel launches per step. */
+/* Sites of all instances (the work of one batch timestep). */
 long long amlbm_batch_sites(const amlbm_batch* b);
+/* The schedule and tile the batch runs with, and kernel launches per timestep. */
+int amlbm_batch_config(const amlbm_batch* b, int* schedule, int* tile_z, int* tile_r,
+                       int* launches_per_step);
 void amlbm_batch_destroy(amlbm_batch* b);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */

@@ -80,7 +80,7 @@ EXPORTS = [
     "amlbm_batch_create", "amlbm_batch_init_fields", "amlbm_batch_step", "amlbm_batch_read",
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
     "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
-    "amlbm_objective",
+    "amlbm_objective", "amlbm_batch_config",
 ]
 
 
@@ -123,6 +123,7 @@ def load(build_if_missing: bool = True):
         lib.amlbm_batch_diagnostics.argtypes = [vp, ip, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
         lib.amlbm_batch_sites.argtypes = [vp]
         lib.amlbm_batch_sites.restype = ctypes.c_longlong
+        lib.amlbm_batch_config.argtypes = [vp] + [ctypes.POINTER(ip)] * 4
         lib.amlbm_batch_destroy.argtypes = [vp]
         lib.amlbm_batch_destroy.restype = None
         lib.amlbm_last_error.restype = ctypes.c_char_p
@@ -222,6 +223,12 @@ class Batch:
         self.h = h
         self.storage = storage
         self.sites = int(self.lib.amlbm_batch_sites(h))
+        sc, tz, tr, nl = (ctypes.c_int() for _ in range(4))
+        _check(self.lib, self.lib.amlbm_batch_config(h, ctypes.byref(sc), ctypes.byref(tz), ctypes.byref(tr),
+                                                     ctypes.byref(nl)))
+        self.schedule = {1: "fused", 2: "split"}[sc.value]
+        self.tile = (tz.value, tr.value)
+        self.launches_per_step = nl.value
 
     def init_fields(self, k, rho, uz=None, ur=None):
         s = self.specs[k]

@@ -54,16 +54,17 @@ amlbm_bc default_bc() {
   return b;
 }
 
-// Schedule and tile when the caller gives none: the split schedule with the
-// first tile of a preference list (fastest first on the 64-drop sweep) that
-// still gives every SM two CTAs over the whole batch, else the smallest tile.
+// Schedule and tile when the caller gives none (fastest on the 64-drop sweep on
+// GB300): FP32 arithmetic forms take the fused schedule with the first tile of a
+// preference list that still gives every SM two CTAs over the whole batch; the
+// FP64 form, bound by FP64 arithmetic, takes the split schedule (less
+// recomputation).
 void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched, int* tz, int* tr) {
-  static const int pref64[][2] = {{32, 16}, {64, 8}, {32, 8}};
-  static const int pref32[][2] = {{64, 8}, {32, 16}, {64, 4}, {32, 8}};
+  static const int pref64[][2] = {{32, 16}, {32, 8}, {32, 8}};
+  static const int pref32[][2] = {{26, 16}, {64, 8}, {32, 8}};
   const bool f64 = storage == AMLBM_STORE_F64;
-  const int n = f64 ? 3 : 4;
-  *sched = amlbm::SCHED_SPLIT;
-  for (int c = 0; c < n; ++c) {
+  *sched = f64 ? amlbm::SCHED_SPLIT : amlbm::SCHED_FUSED;
+  for (int c = 0; c < 3; ++c) {
     const int z = f64 ? pref64[c][0] : pref32[c][0], r = f64 ? pref64[c][1] : pref32[c][1];
     long long tiles = 0;
     for (const auto& I : inst) tiles += (long long)((I.Nz + z - 1) / z) * ((I.Nr + r - 1) / r);
@@ -111,7 +112,7 @@ int validate(const amlbm_instance& I, int idx) {
 
 struct Layout {
   size_t total = 0;
-  size_t desc = 0, tiles = 0, rb_tiles = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
+  size_t desc = 0, tiles = 0, rb_tiles = 0, ctr = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
          unpack = 0;
   std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur;
   int ntiles = 0, rb_ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
@@ -132,6 +133,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   L.desc = take(n * sizeof(InstDesc));
   L.tiles = take((size_t)L.ntiles * sizeof(int));
   L.rb_tiles = take((size_t)L.rb_ntiles * sizeof(int));
+  L.ctr = take(2 * sizeof(int));
   L.diag_part = take((size_t)L.diag_nblk * 8 * sizeof(double));
   L.diag_cols = take((size_t)L.maxNz * sizeof(double));
   L.diag_out = take(16 * sizeof(double));
@@ -166,6 +168,7 @@ struct amlbm_batch {
   InstDesc* d_desc = nullptr;
   int* d_tiles = nullptr;
   int* d_rb_tiles = nullptr;
+  int* d_ctr = nullptr;  // tile counters of the persistent step (one per parity)
   int parity = 0;
   long long sites = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -180,7 +183,7 @@ namespace {
 int launch_steps_direct(amlbm_batch* b, int n) {
   for (int s = 0; s < n; ++s) {
     const cudaError_t e = amlbm::launch_step(b->storage, b->sched, b->tz, b->tr, b->d_desc, b->d_tiles,
-                                             b->L.ntiles, 0, b->parity, b->stream);
+                                             b->L.ntiles, 0, b->parity, b->stream, b->d_ctr);
     if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
     b->parity ^= 1;
   }
@@ -195,7 +198,7 @@ int ensure_graph(amlbm_batch* b, int parity) {
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < b->graph_chunk && e == cudaSuccess; ++s) {
     e = amlbm::launch_step(b->storage, b->sched, b->tz, b->tr, b->d_desc, b->d_tiles, b->L.ntiles, 0, p,
-                           b->stream);
+                           b->stream, b->d_ctr);
     p ^= 1;
   }
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -310,6 +313,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   b->d_desc = reinterpret_cast<InstDesc*>(b->arena + L.desc);
   b->d_tiles = reinterpret_cast<int*>(b->arena + L.tiles);
   b->d_rb_tiles = reinterpret_cast<int*>(b->arena + L.rb_tiles);
+  b->d_ctr = reinterpret_cast<int*>(b->arena + L.ctr);
   cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), b->desc.size() * sizeof(InstDesc),
                                   cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
@@ -318,6 +322,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_rb_tiles, rb_tiles.data(), rb_tiles.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     if (b->owns) cudaFree(b->arena);
@@ -490,6 +495,15 @@ int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, 
 }
 
 long long amlbm_batch_sites(const amlbm_batch* b) { return b ? b->sites : 0; }
+
+int amlbm_batch_config(const amlbm_batch* b, int* schedule, int* tile_z, int* tile_r, int* launches_per_step) {
+  if (!b) return fail(AMLBM_EINVAL, "NULL batch");
+  if (schedule) *schedule = b->sched;
+  if (tile_z) *tile_z = b->tz;
+  if (tile_r) *tile_r = b->tr;
+  if (launches_per_step) *launches_per_step = b->sched == amlbm::SCHED_SPLIT ? 2 : 1;
+  return AMLBM_OK;
+}
 
 void amlbm_batch_destroy(amlbm_batch* b) {
   if (!b) return;

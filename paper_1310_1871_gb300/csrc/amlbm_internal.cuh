@@ -32,8 +32,11 @@ struct InstDesc {
 // [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
 // (force kernel, then collide-stream kernel).
 enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
+// ctr (two ints, zero at creation) makes the fused schedule a persistent grid
+// taking tiles from a counter; nullptr launches one CTA per tile.
 cudaError_t launch_step(int storage, int schedule, int tz, int tr, const InstDesc* d_desc,
-                        const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
+                        const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s,
+                        int* ctr);
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d_desc,
                          const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
 cudaError_t launch_init(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,

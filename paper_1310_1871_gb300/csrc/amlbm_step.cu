@@ -171,18 +171,31 @@ __device__ __forceinline__ void sources(C S_, C Hz, C Hr, C* h) {
   h[0] = S_ - ((h[2] + h[4]) + ((h[1] + h[3]) + ((h[5] + h[6]) + (h[7] + h[8]))));
 }
 
-// 256 threads per CTA.  Every 2D region of a tile is walked as warp tasks: a
-// task is a 32-wide segment of one row, so each warp reads and writes one
-// contiguous run of a row and branches that depend on the row never diverge.
+// 256 threads per CTA.  A 2D region of a tile whose width is a multiple of 32
+// is walked as warp tasks: a task is a 32-wide segment of one row, so each warp
+// reads and writes one contiguous run of a row and branches that depend on the
+// row never diverge.
 constexpr int NT = 256, NWARP = NT / 32;
 
+//
+// A region whose width is not a multiple of 32 would leave lanes idle in its
+// last segment of every row (a 36-wide row costs 64 lanes), so such regions
+// are walked with a flat index instead (the division is by a compile-time
+// constant); a warp may then span two rows.
 template <int ROWS, int W, class F>
 __device__ __forceinline__ void for_tile(F&& body) {
-  constexpr int SEGS = (W + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  for (int t = threadIdx.x >> 5; t < ROWS * SEGS; t += NWARP) {
-    const int lr = t / SEGS, lc = (t - lr * SEGS) * 32 + lane;
-    if (lc < W) body(lr, lc);
+  if constexpr (W % 32 == 0) {
+    constexpr int SEGS = W / 32;
+    const int lane = threadIdx.x & 31;
+    for (int t = threadIdx.x >> 5; t < ROWS * SEGS; t += NWARP) {
+      const int lr = t / SEGS, lc = (t - lr * SEGS) * 32 + lane;
+      body(lr, lc);
+    }
+  } else {
+    for (int t = threadIdx.x; t < ROWS * W; t += NT) {
+      const int lr = t / W, lc = t - lr * W;
+      body(lr, lc);
+    }
   }
 }
 
@@ -207,10 +220,9 @@ struct Tile {
   int inst, k0, j0;
 };
 
-__device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_inst, int toff, int BZ,
+__device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_inst, int b, int BZ,
                                         int BR, bool readback = false) {
   Tile t;
-  const int b = blockIdx.x + toff;
   t.inst = tile_inst[b];
   const int tb = readback ? descs[t.inst].rb_tile_base : descs[t.inst].tile_base;
   const int tz = readback ? descs[t.inst].rb_tiles_z : descs[t.inst].tiles_z;
@@ -223,11 +235,15 @@ __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_i
 // The fused update of one tile.  MODE 0: the timestep; MODE 1 (read-back):
 // only rho and u of the tile; MODE 2: the forward intermediates of the tile for
 // the adjoint (into `inter`, I_COUNT planes of `iplane` elements).
+// Resident CTAs per SM the register allocation must allow: five for the FP32
+// arithmetic forms (their tiles use at most ~40 KB of shared memory).
+template <class S>
+struct MinBlocks { static constexpr int value = std::is_same<S, double>::value ? 1 : 5; };
+
 template <class S, int BZ, int BR, int MODE>
-__global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ descs,
-                                                 const int* __restrict__ tile_inst, int toff,
-                                                 int parity, typename Store<S>::C* __restrict__ inter,
-                                                 size_t iplane) {
+__device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
+                                         const int* __restrict__ tile_inst, int tile, int parity,
+                                         typename Store<S>::C* __restrict__ inter, size_t iplane) {
   constexpr bool READBACK = MODE == 1;
   using C = typename Store<S>::C;
   using G = Geo<C, BZ, BR>;
@@ -246,7 +262,7 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
   C* sUr = sUz + G::nF;
   C* sFs = sUr + G::nF;
 
-  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR, READBACK);
+  const Tile T = tile_of(descs, tile_inst, tile, BZ, BR, READBACK);
   const InstDesc& D = descs[T.inst];
   const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
   const size_t plane = (size_t)P * Nr;
@@ -491,6 +507,36 @@ __global__ void __launch_bounds__(NT) lbm_kernel(const InstDesc* __restrict__ de
 }
 
 
+template <class S, int BZ, int BR, int MODE>
+__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(const InstDesc* __restrict__ descs,
+                                                 const int* __restrict__ tile_inst, int toff,
+                                                 int parity, typename Store<S>::C* __restrict__ inter,
+                                                 size_t iplane) {
+  lbm_tile<S, BZ, BR, MODE>(descs, tile_inst, blockIdx.x + toff, parity, inter, iplane);
+}
+
+// The timestep as a persistent grid (as many CTAs as fit on the GPU at once):
+// CTAs take tiles from a counter in the order of the tile list until none is
+// left, so uneven lattices and ragged tiles leave no partial last wave.
+// ctr[parity] counts this step's tiles; ctr[parity ^ 1], last used by the
+// previous step (which the stream has completed), is reset for the next one.
+// No CTA waits on another.
+template <class S, int BZ, int BR>
+__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
+    const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
+    int* __restrict__ ctr) {
+  __shared__ int s_tile;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr[parity ^ 1] = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[parity], 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) return;
+    lbm_tile<S, BZ, BR, 0>(descs, tile_inst, t, parity, nullptr, 0);
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ split schedule --
 // The same update as lbm_kernel MODE 0 in two kernels, so that the heavy
 // per-site chain runs once per site instead of on a halo of 3:
@@ -524,7 +570,7 @@ __global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ 
   C* sPsi = reinterpret_cast<C*>(smem_raw + G::int_bytes);
   C* sDr = sPsi + G::nP;
   C* sD1 = sDr + G::nD;
-  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const Tile T = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
   const InstDesc& D = descs[T.inst];
   const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
   const size_t plane = (size_t)P * Nr;
@@ -615,7 +661,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
   C* sHz = sS + G::nS;
   C* sHr = sHz + G::nS;
   C* sFs = sHr + G::nS;
-  const Tile T = tile_of(descs, tile_inst, toff, BZ, BR);
+  const Tile T = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
   const InstDesc& D = descs[T.inst];
   const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
   const size_t plane = (size_t)P * Nr;
@@ -894,18 +940,36 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_kernel(const InstDesc* __r
 
 template <class S, int BZ, int BR, int MODE>
 cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
-                     cudaStream_t s, void* inter = nullptr, size_t iplane = 0) {
+                     cudaStream_t s, void* inter = nullptr, size_t iplane = 0, int* ctr = nullptr) {
   using C = typename Store<S>::C;
   constexpr size_t smem = Geo<C, BZ, BR>::bytes;
   static bool attr = false;
+  static int grid_cap = 0;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && MODE == 0)
+      e = cudaFuncSetAttribute(lbm_persistent<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
     if (e != cudaSuccess) return e;
+    if (MODE == 0) {
+      int dev = 0, sms = 0, per_sm = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm_persistent<S, BZ, BR>, NT, smem);
+      if (e != cudaSuccess) return e;
+      grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+    }
     attr = true;
   }
-  lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
-                                                       iplane);
+  if (MODE == 0 && ctr && toff == 0) {
+    const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+    lbm_persistent<S, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
+  } else {
+    lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
+                                                         iplane);
+  }
   return cudaGetLastError();
 }
 
@@ -936,7 +1000,7 @@ struct TileEntry { int storage, sched, tz, tr; };
   {ST, SCHED_FUSED, 58, 16}, {ST, SCHED_FUSED, 26, 16}, {ST, SCHED_FUSED, 32, 16},            \
   {ST, SCHED_FUSED, 122, 8}, {ST, SCHED_SPLIT, 32, 8}, {ST, SCHED_SPLIT, 64, 8},              \
   {ST, SCHED_SPLIT, 32, 16}, {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 128, 8},            \
-  {ST, SCHED_SPLIT, 64, 4}
+  {ST, SCHED_SPLIT, 64, 4}, {ST, SCHED_FUSED, 32, 32}, {ST, SCHED_FUSED, 64, 16}
 constexpr TileEntry kTiles[] = {
     {AMLBM_STORE_F64, SCHED_FUSED, 32, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 64, 8},
     {AMLBM_STORE_F64, SCHED_FUSED, 58, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 26, 8},
@@ -948,7 +1012,7 @@ constexpr TileEntry kTiles[] = {
 
 template <class S>
 cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, const int* ti, int nt,
-                     int toff, int par, cudaStream_t s) {
+                     int toff, int par, cudaStream_t s, int* ctr) {
   if (nt <= 0) return cudaSuccess;
   if (sched == SCHED_SPLIT && !macro) {
 #define AMLBM_SPLIT(TZ, TR) \
@@ -967,7 +1031,7 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
 #define AMLBM_TILE(TZ, TR)                                                \
   if (tz == TZ && tr == TR)                                               \
     return macro ? launch_t<S, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
-                 : launch_t<S, TZ, TR, 0>(d, ti, nt, toff, par, s);
+                 : launch_t<S, TZ, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
   if (macro) {  // read-back always uses a fused tile compiled for every storage
     AMLBM_TILE(32, 8)
     return cudaErrorInvalidValue;
@@ -982,18 +1046,21 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
     AMLBM_TILE(26, 16)
     AMLBM_TILE(32, 16)
     AMLBM_TILE(122, 8)
+    AMLBM_TILE(32, 32)
+    AMLBM_TILE(64, 16)
   }
 #undef AMLBM_TILE
   return cudaErrorInvalidValue;
 }
 
 cudaError_t dispatch_storage(int storage, bool macro, int sched, int tz, int tr, const InstDesc* d,
-                             const int* ti, int nt, int toff, int par, cudaStream_t s) {
+                             const int* ti, int nt, int toff, int par, cudaStream_t s, int* ctr) {
   switch (storage) {
-    case AMLBM_STORE_F64: return dispatch<double>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_F32: return dispatch<float>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_F16: return dispatch<__half>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
-    case AMLBM_STORE_BF16: return dispatch<__nv_bfloat16>(macro, sched, tz, tr, d, ti, nt, toff, par, s);
+    case AMLBM_STORE_F64: return dispatch<double>(macro, sched, tz, tr, d, ti, nt, toff, par, s, ctr);
+    case AMLBM_STORE_F32: return dispatch<float>(macro, sched, tz, tr, d, ti, nt, toff, par, s, ctr);
+    case AMLBM_STORE_F16: return dispatch<__half>(macro, sched, tz, tr, d, ti, nt, toff, par, s, ctr);
+    case AMLBM_STORE_BF16:
+      return dispatch<__nv_bfloat16>(macro, sched, tz, tr, d, ti, nt, toff, par, s, ctr);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1026,12 +1093,12 @@ size_t step_smem_bytes(int storage, int tz, int tr) {
 }
 
 cudaError_t launch_step(int storage, int sched, int tz, int tr, const InstDesc* d, const int* ti,
-                        int nt, int toff, int parity, cudaStream_t s) {
-  return dispatch_storage(storage, false, sched, tz, tr, d, ti, nt, toff, parity, s);
+                        int nt, int toff, int parity, cudaStream_t s, int* ctr) {
+  return dispatch_storage(storage, false, sched, tz, tr, d, ti, nt, toff, parity, s, ctr);
 }
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                          int toff, int parity, cudaStream_t s) {
-  return dispatch_storage(storage, true, SCHED_FUSED, tz, tr, d, ti, nt, toff, parity, s);
+  return dispatch_storage(storage, true, SCHED_FUSED, tz, tr, d, ti, nt, toff, parity, s, nullptr);
 }
 
 cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
