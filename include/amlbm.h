@@ -64,7 +64,7 @@ extern "C" {
 /* Storage of the populations; arithmetic is FP64 for F64 and FP32 otherwise. */
 #define AMLBM_STORE_F64 0
 #define AMLBM_STORE_F32 1
-#define AMLBM_STORE_F16 2  /* IEEE half of f_i - W_i s (s: see AMLBM_SHIFT_*) */
+#define AMLBM_STORE_F16 2  /* IEEE half of (f_i - W_i s) 2^10 (s: see AMLBM_SHIFT_*) */
 #define AMLBM_STORE_BF16 3 /* bfloat16 of f_i - W_i s */
 
 /* What the FP32 and 16-bit forms store: f_i - W_i s.  FP64 storage is never shifted. */
@@ -74,6 +74,14 @@ extern "C" {
 #define AMLBM_SHIFT_LOCAL 3   /* s = -rho0 ln(1 - psi/rho0) of the site's stored psi: the
                                  site's own density recovered from psi, no extra bytes */
 
+/* Rounding of the 16-bit stores.  Stochastic rounding draws its bits from a hash
+ * of (site, population, step number), so a run is reproducible and unbiased in
+ * expectation; round-to-nearest repeats the same error at every step of a
+ * slowly varying state, and those errors add up. */
+#define AMLBM_ROUND_DEFAULT 0 /* stochastic for BF16, to nearest otherwise */
+#define AMLBM_ROUND_NEAREST 1
+#define AMLBM_ROUND_STOCHASTIC 2
+
 /* Boundary and model options of one lattice. */
 typedef struct amlbm_bc {
   int wall_r;     /* AMLBM_WALL_* */
@@ -81,7 +89,7 @@ typedef struct amlbm_bc {
   int src_mode;   /* AMLBM_SRC_* */
   int storage;    /* AMLBM_STORE_* (a batch uses the storage of its first instance) */
   int shift;      /* AMLBM_SHIFT_* */
-  int reserved;   /* must be 0 */
+  int rounding;   /* AMLBM_ROUND_* (16-bit storage) */
   double g_z;     /* body acceleration along +z (force rho g_z), Sec. III.1 */
   double rho_ref; /* constant of AMLBM_SHIFT_GLOBAL */
 } amlbm_bc;

@@ -24,6 +24,7 @@ WALL = {"freeslip": 0, "noslip": 1}
 SRC = {"local": 0, "link": 1}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 SHIFT = {"default": 0, "none": 1, "global": 2, "local": 3}
+ROUNDING = {"default": 0, "nearest": 1, "stochastic": 2}
 DIAG_FIELDS = ["mass2d", "mass3d", "momz3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out",
                "dp", "bad", "sumS", "steps"]
 
@@ -36,7 +37,7 @@ class AmlbmError(RuntimeError):
 
 class BC(ctypes.Structure):
     _fields_ = [("wall_r", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int),
-                ("storage", ctypes.c_int), ("shift", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("storage", ctypes.c_int), ("shift", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("g_z", ctypes.c_double), ("rho_ref", ctypes.c_double)]
 
 
@@ -164,11 +165,12 @@ def _stream_handle(stream):
 
 
 def make_bc(wall="freeslip", axisym=True, src="local", storage="f64", gz=0.0, rho_ref=1.0,
-            shift="default") -> BC:
+            shift="default", rounding="default") -> BC:
     return BC(WALL[wall] if isinstance(wall, str) else int(wall), int(bool(axisym)),
               SRC[src] if isinstance(src, str) else int(src),
               STORAGE[storage] if isinstance(storage, str) else int(storage),
-              SHIFT[shift] if isinstance(shift, str) else int(shift), 0, float(gz), float(rho_ref))
+              SHIFT[shift] if isinstance(shift, str) else int(shift),
+              ROUNDING[rounding] if isinstance(rounding, str) else int(rounding), float(gz), float(rho_ref))
 
 
 def _diag_dict(d: Diag) -> dict:
@@ -189,6 +191,7 @@ class InstanceSpec:
     gz: float = 0.0
     rho_ref: float = 1.0
     shift: str = "default"
+    rounding: str = "default"
 
 
 class Batch:
@@ -204,7 +207,8 @@ class Batch:
         arr = (InstanceC * n)()
         for i, s in enumerate(self.specs):
             arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
-                               make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift))
+                               make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift,
+                                       s.rounding))
         self._arr = arr
         nbytes = self.lib.amlbm_batch_workspace_bytes(n, arr)
         if nbytes == 0:
@@ -277,13 +281,13 @@ class Lattice:
     """One Nz x Nr lattice (amlbm_ctx)."""
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, wall="freeslip", axisym=True, src="local",
-                 storage="f64", gz=0.0, rho_ref=1.0, shift="default", stream=None):
+                 storage="f64", gz=0.0, rho_ref=1.0, shift="default", rounding="default", stream=None):
         import torch
         self.lib = load()
         if not torch.cuda.is_available():
             raise RuntimeError("amlbm needs a CUDA device")
         self.Nz, self.Nr = int(Nz), int(Nr)
-        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift)
+        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift, rounding)
         nbytes = self.lib.amlbm_workspace_bytes(self.Nz, self.Nr, bc.storage)
         if nbytes == 0:
             raise AmlbmError(EINVAL, "bad lattice size or storage")

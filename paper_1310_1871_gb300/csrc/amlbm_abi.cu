@@ -48,7 +48,7 @@ amlbm_bc default_bc() {
   b.src_mode = AMLBM_SRC_LOCAL;
   b.storage = AMLBM_STORE_F64;
   b.shift = AMLBM_SHIFT_DEFAULT;
-  b.reserved = 0;
+  b.rounding = AMLBM_ROUND_DEFAULT;
   b.g_z = 0.0;
   b.rho_ref = 1.0;
   return b;
@@ -105,6 +105,8 @@ int validate(const amlbm_instance& I, int idx) {
     return fail(AMLBM_EINVAL, w + "bad shift");
   if (I.bc.storage == AMLBM_STORE_F64 && I.bc.shift > AMLBM_SHIFT_NONE)
     return fail(AMLBM_EINVAL, w + "FP64 storage is not shifted");
+  if (I.bc.rounding < AMLBM_ROUND_DEFAULT || I.bc.rounding > AMLBM_ROUND_STOCHASTIC)
+    return fail(AMLBM_EINVAL, w + "bad rounding");
   if (!std::isfinite(I.bc.g_z) || !std::isfinite(I.bc.rho_ref))
     return fail(AMLBM_EINVAL, w + "g_z and rho_ref must be finite");
   return AMLBM_OK;
@@ -133,7 +135,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   L.desc = take(n * sizeof(InstDesc));
   L.tiles = take((size_t)L.ntiles * sizeof(int));
   L.rb_tiles = take((size_t)L.rb_ntiles * sizeof(int));
-  L.ctr = take(2 * sizeof(int));
+  L.ctr = take(4 * sizeof(int));
   L.diag_part = take((size_t)L.diag_nblk * 8 * sizeof(double));
   L.diag_cols = take((size_t)L.maxNz * sizeof(double));
   L.diag_out = take(16 * sizeof(double));
@@ -285,6 +287,10 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.axisym = I.bc.axisym;
     d.src = I.bc.src_mode;
     d.shift = resolve_shift(I.bc);
+    // 1 = stochastic rounding of the 16-bit stores (measured: BF16 gains an order
+    // of magnitude in accuracy from it, FP16 does not)
+    d.rounding = storage == AMLBM_STORE_BF16 ? (I.bc.rounding != AMLBM_ROUND_NEAREST)
+               : storage == AMLBM_STORE_F16 ? (I.bc.rounding == AMLBM_ROUND_STOCHASTIC) : 0;
     d.tiles_z = (I.Nz + tz - 1) / tz;
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
@@ -322,7 +328,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_rb_tiles, rb_tiles.data(), rb_tiles.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 4 * sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     if (b->owns) cudaFree(b->arena);

@@ -16,7 +16,8 @@ struct InstDesc {
   int wall, axisym, src;
   int tiles_z, tiles_r, tile_base;     // tiling of the step kernels
   int rb_tiles_z, rb_tiles_r, rb_tile_base;  // 32 x 8 tiling of the read-back kernel
-  int shift;  // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
+  int shift;     // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
+  int rounding;  // 16-bit storage: 0 to nearest, 1 stochastic
   double tau, G, rho0, gz, rho_ref;
   void* f[2];
   void* psi[2];
@@ -32,8 +33,9 @@ struct InstDesc {
 // [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
 // (force kernel, then collide-stream kernel).
 enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
-// ctr (two ints, zero at creation) makes the fused schedule a persistent grid
-// taking tiles from a counter; nullptr launches one CTA per tile.
+// ctr (four ints, zero at creation): tile counters of the persistent fused
+// grid and the step numbers for stochastic rounding, one per parity; nullptr
+// launches one CTA per tile.
 cudaError_t launch_step(int storage, int schedule, int tz, int tr, const InstDesc* d_desc,
                         const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s,
                         int* ctr);

@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <stdint.h>
+
 #include <type_traits>
 
 #include "amlbm.h"
@@ -42,30 +44,75 @@ __host__ __device__ constexpr int opp_(int i) {
        : i == 5 ? 7 : i == 7 ? 5 : i == 6 ? 8 : 6;
 }
 
-// Storage codecs: plain conversion between the stored element and the
-// arithmetic type.  The shift W_i s of the FP32 / 16-bit forms is applied by
-// the callers (decode: f = q + W_i s; encode: q = f - W_i s).
+// Storage codecs: conversion between the stored element and the arithmetic
+// type.  The shift W_i s of the FP32 / 16-bit forms is applied by the callers
+// (decode: f = q + W_i s; encode: q = f - W_i s).  IEEE half holds q * 2^10 so
+// that the shifted populations (down to ~1e-7) stay in its normal range; the
+// power-of-two scale is exact.  from_sr rounds stochastically with the random
+// bits r: the bits below the stored precision are added to r and truncated, so
+// a value rounds up with probability equal to its distance from the lower
+// neighbour (unbiased in expectation).
 template <class S> struct Store;
 template <> struct Store<double> {
   using C = double;
   static __device__ __forceinline__ C to(double v) { return v; }
   static __device__ __forceinline__ double from(C v) { return v; }
+  static __device__ __forceinline__ double from_sr(C v, uint32_t) { return v; }
 };
 template <> struct Store<float> {
   using C = float;
   static __device__ __forceinline__ C to(float v) { return v; }
   static __device__ __forceinline__ float from(C v) { return v; }
+  static __device__ __forceinline__ float from_sr(C v, uint32_t) { return v; }
 };
 template <> struct Store<__half> {
   using C = float;
-  static __device__ __forceinline__ C to(__half v) { return __half2float(v); }
-  static __device__ __forceinline__ __half from(C v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ C to(__half v) { return __half2float(v) * (1.0f / 1024.0f); }
+  static __device__ __forceinline__ __half from(C v) { return __float2half_rn(v * 1024.0f); }
+  static __device__ __forceinline__ __half from_sr(C v, uint32_t r) {
+    // FP32 keeps 13 more mantissa bits than FP16 (for FP16-normal values)
+    const uint32_t b = __float_as_uint(v * 1024.0f) + (r & 0x1FFFu);
+    return __float2half_rz(__uint_as_float(b));
+  }
 };
 template <> struct Store<__nv_bfloat16> {
   using C = float;
   static __device__ __forceinline__ C to(__nv_bfloat16 v) { return __bfloat162float(v); }
   static __device__ __forceinline__ __nv_bfloat16 from(C v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ __nv_bfloat16 from_sr(C v, uint32_t r) {
+    // bfloat16 is the upper half of the FP32 bit pattern
+    const uint32_t b = __float_as_uint(v) + (r & 0xFFFFu);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+  }
 };
+
+// Integer hash for the stochastic-rounding bits (a xorshift-multiply mixer).
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// Store the nine new populations of a site with the shift W_i sb, rounding to
+// nearest or (rounding != 0) stochastically with bits drawn from (site, step).
+template <class S>
+__device__ __forceinline__ void store_site(S* o, size_t plane, const typename Store<S>::C* fn,
+                                           typename Store<S>::C sb, int rounding, uint32_t site,
+                                           uint32_t step) {
+  using C = typename Store<S>::C;
+  if (sizeof(S) == 2 && rounding) {
+    const uint32_t h = mix32(site ^ mix32(step + 0x9E3779B9u));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      o[i * plane] = Store<S>::from_sr(fn[i] - C(w_(i)) * sb, mix32(h + 0x632BE5ABu * (uint32_t)(i + 1)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+  }
+}
 
 // exp / log / reciprocal of the arithmetic type.  The FP32 forms use the SFU
 // approximations (relative error ~1e-7, far below the storage rounding).
@@ -243,7 +290,8 @@ struct MinBlocks { static constexpr int value = std::is_same<S, double>::value ?
 template <class S, int BZ, int BR, int MODE>
 __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
                                          const int* __restrict__ tile_inst, int tile, int parity,
-                                         typename Store<S>::C* __restrict__ inter, size_t iplane) {
+                                         typename Store<S>::C* __restrict__ inter, size_t iplane,
+                                         uint32_t step = 0) {
   constexpr bool READBACK = MODE == 1;
   using C = typename Store<S>::C;
   using G = Geo<C, BZ, BR>;
@@ -498,9 +546,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       const C rho = moment0(fn);
       const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
       const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
-      S* o = fout + (size_t)j * P + k;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+      store_site<S>(fout + (size_t)j * P + k, plane, fn, sb, D.rounding, (uint32_t)(j * Nz + k), step);
       psout[(size_t)j * P + k] = psi;
     }
   });
@@ -520,19 +566,25 @@ __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(const Inst
 // left, so uneven lattices and ragged tiles leave no partial last wave.
 // ctr[parity] counts this step's tiles; ctr[parity ^ 1], last used by the
 // previous step (which the stream has completed), is reset for the next one.
-// No CTA waits on another.
+// No CTA waits on another.  ctr[2], ctr[3] carry the step number the same way.
 template <class S, int BZ, int BR>
 __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctr[parity ^ 1] = 0;
+  // ctr[2 + parity] is this step's number (for the stochastic rounding); the
+  // next step reads ctr[2 + (parity ^ 1)].
+  const uint32_t step = (uint32_t)ctr[2 + parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr[parity ^ 1] = 0;
+    ctr[2 + (parity ^ 1)] = (int)(step + 1);
+  }
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[parity], 1);
     __syncthreads();
     const int t = s_tile;
     if (t >= ntiles) return;
-    lbm_tile<S, BZ, BR, 0>(descs, tile_inst, t, parity, nullptr, 0);
+    lbm_tile<S, BZ, BR, 0>(descs, tile_inst, t, parity, nullptr, 0, step);
     __syncthreads();
   }
 }
@@ -649,7 +701,9 @@ struct GeoB {
 template <class S, int BZ, int BR>
 __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__ descs,
                                                     const int* __restrict__ tile_inst, int toff,
-                                                    int parity) {
+                                                    int parity, int* __restrict__ ctr) {
+  const uint32_t step = ctr ? (uint32_t)ctr[2 + parity] : 0u;
+  if (ctr && blockIdx.x == 0 && threadIdx.x == 0) ctr[2 + (parity ^ 1)] = (int)(step + 1);
   using C = typename Store<S>::C;
   using G = GeoB<C, BZ, BR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -776,9 +830,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const C rho = moment0(fn);
     const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
     const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
-    S* o = fout + (size_t)j * P + k;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+    store_site<S>(fout + (size_t)j * P + k, plane, fn, sb, D.rounding, (uint32_t)(j * Nz + k), step);
     psout[(size_t)j * P + k] = psi;
   });
 }
@@ -975,7 +1027,7 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
 
 template <class S, int BZ, int BR>
 cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
-                           cudaStream_t s) {
+                           cudaStream_t s, int* ctr) {
   using C = typename Store<S>::C;
   constexpr size_t sa = GeoA<C, BZ, BR>::bytes, sbb = GeoB<C, BZ, BR>::bytes;
   static bool attr = false;
@@ -989,7 +1041,7 @@ cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int tof
     attr = true;
   }
   force_kernel<S, BZ, BR><<<ntiles, NT, sa, s>>>(d, ti, toff, parity);
-  stream_kernel<S, BZ, BR><<<ntiles, NT, sbb, s>>>(d, ti, toff, parity);
+  stream_kernel<S, BZ, BR><<<ntiles, NT, sbb, s>>>(d, ti, toff, parity, ctr);
   return cudaGetLastError();
 }
 
@@ -1016,7 +1068,7 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
   if (nt <= 0) return cudaSuccess;
   if (sched == SCHED_SPLIT && !macro) {
 #define AMLBM_SPLIT(TZ, TR) \
-  if (tz == TZ && tr == TR) return launch_split_t<S, TZ, TR>(d, ti, nt, toff, par, s);
+  if (tz == TZ && tr == TR) return launch_split_t<S, TZ, TR>(d, ti, nt, toff, par, s, ctr);
     AMLBM_SPLIT(32, 8)
     AMLBM_SPLIT(64, 8)
     AMLBM_SPLIT(32, 16)

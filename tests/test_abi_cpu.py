@@ -51,7 +51,8 @@ def test_bad_flags_and_tiles_rejected(lib):
     h = ctypes.c_void_p()
     for bc in (amlbm.BC(2, 1, 0, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0, 0, 0.0, 1.0),
                amlbm.BC(0, 1, 5, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 9, 0, 0, 0.0, 1.0),
-               amlbm.BC(0, 1, 0, 2, 7, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 0, 3, 0, 0.0, 1.0)):
+               amlbm.BC(0, 1, 0, 2, 7, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 0, 3, 0, 0.0, 1.0),
+               amlbm.BC(0, 1, 0, 3, 0, 4, 0.0, 1.0), amlbm.BC(0, 1, 0, 3, 0, -1, 0.0, 1.0)):
         assert lib.amlbm_create(16, 16, 1.0, -5.0, 1.0, ctypes.byref(bc), None, None, 0,
                                 ctypes.byref(h)) == amlbm.EINVAL
     inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(32, 16, 1.0, -5.0, 1.0, amlbm.make_bc(storage="f64")))

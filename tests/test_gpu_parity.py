@@ -26,12 +26,12 @@ def rel(a, b):
 
 
 def run_pair(Nz, Nr, steps, fields, tau=1.0, G=-5.0, wall=0, axisym=1, src=0, gz=0.0,
-             storage="f64", tile=None, rho_ref=1.0, shift="default"):
+             storage="f64", tile=None, rho_ref=1.0, shift="default", rounding="nearest"):
     rho, uz, ur = fields
     o = O.Oracle(Nz, Nr, tau=tau, G=G, gz=gz, wall=wall, axisym=axisym, src_mode=src)
     f_ref = o.run(o.init(rho, uz, ur), steps)
     spec = amlbm.InstanceSpec(Nz, Nr, tau, G, 1.0, WALLS[wall], bool(axisym),
-                              "link" if src else "local", gz, rho_ref, shift)
+                              "link" if src else "local", gz, rho_ref, shift, rounding)
     b = amlbm.Batch([spec], storage=storage, tile=tile)
     b.init_fields(0, rho, uz, ur)
     b.step(steps)
@@ -92,25 +92,27 @@ def test_fp64_thread_full_size():
 # storage form and shift (measured values are printed; the bounds below are the
 # ones each form meets with margin).
 PRECISION_CASES = [
-    ("f32", "none", 1e-4), ("f32", "local", 1e-4),
-    ("f16", "local", 3e-3), ("bf16", "local", 1.5e-1),
-    ("f16", "global", 1.0), ("bf16", "global", 1.0),
+    ("f32", "none", "nearest", 1e-4), ("f32", "local", "nearest", 1e-4),
+    ("f16", "local", "nearest", 2e-3), ("bf16", "local", "nearest", 1.5e-1),
+    ("f16", "local", "stochastic", 5e-3), ("bf16", "local", "stochastic", 1e-2),
+    ("f16", "global", "nearest", 1.0), ("bf16", "global", "nearest", 1.0),
 ]
 
 
-@pytest.mark.parametrize("storage,shift,bound", PRECISION_CASES)
-def test_reduced_precision_forms(storage, shift, bound):
+@pytest.mark.parametrize("storage,shift,rounding,bound", PRECISION_CASES)
+def test_reduced_precision_forms(storage, shift, rounding, bound):
     """FP32 arithmetic with FP32 or 16-bit storage of f_i - W_i s against the FP64 oracle."""
     _, _, (rho, uz, ur), F = run_pair(64, 32, 1000, I.drop(64, 32, 32.0, 12.0), storage=storage,
-                                      tile=(32, 8), shift=shift)
+                                      tile=(32, 8), shift=shift, rounding=rounding)
     err = np.abs(rho / F["rho"] - 1).max()
     uerr = max(np.abs(uz - F["uz"]).max(), np.abs(ur - F["ur"]).max()) / np.abs(F["uz"]).max()
-    print(f"{storage}/{shift}: rho max rel err {err:.3e}, u normwise {uerr:.3e}")
+    print(f"{storage}/{shift}/{rounding}: rho max rel err {err:.3e}, u normwise {uerr:.3e}")
     assert np.isfinite(rho).all() and err < bound
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("case", [dict(), dict(wall="noslip", gz=1e-4), dict(src="link"), dict(axisym=False)])
+@pytest.mark.parametrize("case", [dict(), dict(wall="noslip", gz=1e-4), dict(src="link"), dict(axisym=False),
+                                  dict(rounding="stochastic")])
 def test_split_schedule_equals_fused_bitwise(storage, case):
     """The two-kernel schedule performs the fused kernel's arithmetic operation for
     operation: states after 120 steps are bit-identical (ragged 70 x 21 lattice)."""
@@ -134,6 +136,9 @@ def test_batch_equals_single_instances_bitwise():
     fields = [I.drop(48, 24, 24.0, 8.0, amps=(0.05,)), I.drop(70, 21, 35.0, 9.0),
               I.drop(33, 16, 16.0, 6.0, amps=(0.02,))]
     for storage in ("f64", "f32", "bf16", "f16"):
+        if storage in ("bf16", "f16"):
+            for sp in specs:
+                sp.rounding = "stochastic"
         b = amlbm.Batch(specs, storage=storage, tile=(32, 8))
         for k, fl in enumerate(fields):
             b.init_fields(k, *fl)
@@ -151,10 +156,11 @@ def test_graph_chunks_equal_direct_launches():
     s = [amlbm.InstanceSpec(64, 32, 0.9, -5.0)]
     fl = I.drop(64, 32, 32.0, 10.0, amps=(0.05,))
     out = []
+    s[0].rounding = "stochastic"
     for chunk in (0, 16):
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
-            b = amlbm.Batch(s, storage="f32", graph_chunk=chunk, stream=stream)
+            b = amlbm.Batch(s, storage="bf16", graph_chunk=chunk, stream=stream)
             b.init_fields(0, *fl)
             b.step(37)
             out.append(b.read_f(0))
