@@ -277,6 +277,26 @@ int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const doub
 int amlbm_batch_step(amlbm_batch* b, int n);
 int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f);
 int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out);
+/* Every instance at once, f = f^eq(rho, u) as amlbm_batch_init_fields does per
+ * instance (the initial state of Sec. II), from caller-owned host arrays that
+ * hold all instances back to back in instance order: instance k's [Nr][Nz]
+ * block starts at the sum of Nz*Nr over the instances before it, and the total
+ * length is amlbm_batch_sites().  uz and ur may be NULL (zero velocity).  One
+ * host-to-device copy per array and one kernel launch; rho is checked on the
+ * device and the call returns AMLBM_EINVAL, with every instance's state
+ * unchanged, if any value is not positive and finite.  Resets every instance's
+ * step count and restarts the stochastic-rounding stream, so that the steps
+ * that follow equal those of a newly created batch.  Synchronises the batch
+ * stream. */
+int amlbm_batch_init_all(amlbm_batch* b, const double* rho, const double* uz, const double* ur);
+/* The diagnostics of every instance in one pass (one read-back launch, one
+ * partial-sum launch, one final launch, one device-to-host copy): dp holds n
+ * parameter sets (NULL: the defaults of amlbm_batch_diagnostics), out receives
+ * n results, each equal to what amlbm_batch_diagnostics gives for that
+ * instance.  Returns AMLBM_EUNSTABLE, after filling every output, if any
+ * instance has a non-finite or non-positive density (the message names the
+ * first).  Synchronises the batch stream. */
+int amlbm_batch_diagnostics_all(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out);
 /* Sites of all instances (the work of one batch timestep). */
 long long amlbm_batch_sites(const amlbm_batch* b);
 /* The schedule and tile the batch runs with, and kernel launches per timestep. */

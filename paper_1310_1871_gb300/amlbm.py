@@ -81,7 +81,7 @@ EXPORTS = [
     "amlbm_batch_create", "amlbm_batch_init_fields", "amlbm_batch_step", "amlbm_batch_read",
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
     "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
-    "amlbm_objective", "amlbm_batch_config",
+    "amlbm_objective", "amlbm_batch_config", "amlbm_batch_init_all", "amlbm_batch_diagnostics_all",
 ]
 
 
@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
         lib.amlbm_batch_step.argtypes = [vp, ip]
         lib.amlbm_batch_read.argtypes = [vp, ip, dp, dp, dp, dp]
         lib.amlbm_batch_diagnostics.argtypes = [vp, ip, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
+        lib.amlbm_batch_init_all.argtypes = [vp, dp, dp, dp]
+        lib.amlbm_batch_diagnostics_all.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
         lib.amlbm_batch_sites.argtypes = [vp]
         lib.amlbm_batch_sites.restype = ctypes.c_longlong
         lib.amlbm_batch_config.argtypes = [vp] + [ctypes.POINTER(ip)] * 4
@@ -264,6 +266,40 @@ class Batch:
         if rc not in (OK, EUNSTABLE) or (check and rc != OK):
             _check(self.lib, rc)
         return _diag_dict(d)
+
+    def _flat(self, a):
+        if a is None:
+            return None
+        if isinstance(a, (list, tuple)):
+            a = np.concatenate([np.ravel(x) for x in a])
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        if a.size != self.sites:
+            raise ValueError(f"expected {self.sites} values (all instances back to back), got {a.size}")
+        return a
+
+    def init_all(self, rho, uz=None, ur=None):
+        """Every instance at once (amlbm_batch_init_all): rho, uz, ur hold all
+        instances back to back in instance order, each [Nr][Nz], or are lists of
+        per-instance arrays."""
+        rho, uz, ur = self._flat(rho), self._flat(uz), self._flat(ur)
+        _check(self.lib, self.lib.amlbm_batch_init_all(self.h, _dptr(rho), _dptr(uz), _dptr(ur)))
+
+    def diagnostics_all(self, params=None, check=True):
+        """Diagnostics of every instance in one pass (amlbm_batch_diagnostics_all);
+        params: one dict per instance with zc, R, rho_l, rho_v (None: defaults)."""
+        n = len(self.specs)
+        dp = None
+        if params is not None:
+            dp = (DiagParams * n)()
+            for k, (s, q) in enumerate(zip(self.specs, params)):
+                zc = q.get("zc")
+                dp[k] = DiagParams(s.Nz / 2 if zc is None else float(zc), float(q.get("R", 1.0)),
+                                   float(q.get("rho_l", 2.0)), float(q.get("rho_v", 0.1)))
+        out = (Diag * n)()
+        rc = self.lib.amlbm_batch_diagnostics_all(self.h, dp, out)
+        if rc not in (OK, EUNSTABLE) or (check and rc != OK):
+            _check(self.lib, rc)
+        return [_diag_dict(d) for d in out]
 
     def close(self):
         if getattr(self, "h", None):

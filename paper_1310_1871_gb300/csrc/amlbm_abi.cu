@@ -115,9 +115,11 @@ int validate(const amlbm_instance& I, int idx) {
 struct Layout {
   size_t total = 0;
   size_t desc = 0, tiles = 0, rb_tiles = 0, ctr = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
-         unpack = 0;
+         unpack = 0, site_off = 0, diag_jobs = 0;
   std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur;
   int ntiles = 0, rb_ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
+  int all_nblk = 0;  // partial-sum blocks of a diagnostics pass over every instance
+  long long sumN = 0, sumNz = 0;
 };
 
 Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz, int tr) {
@@ -131,15 +133,20 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
     L.maxN = std::max(L.maxN, I.Nz * I.Nr);
     L.maxNz = std::max(L.maxNz, I.Nz);
     L.diag_nblk = std::max(L.diag_nblk, amlbm::diag_blocks(I.Nz, I.Nr));
+    L.all_nblk += amlbm::diag_blocks(I.Nz, I.Nr);
+    L.sumN += (long long)I.Nz * I.Nr;
+    L.sumNz += I.Nz;
   }
   L.desc = take(n * sizeof(InstDesc));
   L.tiles = take((size_t)L.ntiles * sizeof(int));
   L.rb_tiles = take((size_t)L.rb_ntiles * sizeof(int));
-  L.ctr = take(4 * sizeof(int));
-  L.diag_part = take((size_t)L.diag_nblk * 8 * sizeof(double));
-  L.diag_cols = take((size_t)L.maxNz * sizeof(double));
-  L.diag_out = take(16 * sizeof(double));
-  L.upload = take((size_t)3 * L.maxN * sizeof(double));
+  L.ctr = take(5 * sizeof(int));  // two tile counters, two step counters, the init check count
+  L.diag_part = take((size_t)std::max(L.diag_nblk, L.all_nblk) * 8 * sizeof(double));
+  L.diag_cols = take((size_t)L.sumNz * sizeof(double));
+  L.diag_out = take(16 * n * sizeof(double));
+  L.diag_jobs = take(n * sizeof(amlbm::DiagJob));
+  L.site_off = take((n + 1) * sizeof(long long));
+  L.upload = take((size_t)3 * L.sumN * sizeof(double));
   L.unpack = take((size_t)9 * L.maxN * sizeof(double));
   for (const auto& I : inst) {
     const size_t plane = (size_t)pitch_of(I.Nz) * I.Nr;
@@ -328,7 +335,12 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_rb_tiles, rb_tiles.data(), rb_tiles.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 4 * sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 5 * sizeof(int), b->stream);
+  std::vector<long long> off(b->n + 1, 0);
+  for (int i = 0; i < b->n; ++i) off[i + 1] = off[i] + (long long)inst[i].Nz * inst[i].Nr;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->arena + L.site_off, off.data(), off.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     if (b->owns) cudaFree(b->arena);
@@ -405,14 +417,103 @@ int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double
   return AMLBM_OK;
 }
 
+void fill_diag(const double* h, long long steps, amlbm_diag* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
+  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
+  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
+  out->steps = (double)steps;
+}
+
+amlbm_diag_params diag_defaults(const InstDesc& d) {
+  amlbm_diag_params p;
+  p.zc = d.Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1;
+  return p;
+}
+
+// Every instance from host arrays holding them back to back.  The new state is
+// written into the buffers of the other parity, and becomes current only when
+// the device check finds every rho positive and finite.
+int init_all_host(amlbm_batch* b, const double* rho, const double* uz, const double* ur) {
+  if (!b) return fail(AMLBM_EINVAL, "NULL batch");
+  if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
+  const long long T = b->sites;
+  double* st = reinterpret_cast<double*>(b->arena + b->L.upload);
+  const long long* off = reinterpret_cast<const long long*>(b->arena + b->L.site_off);
+  int* bad = b->d_ctr + 4;
+  AMLBM_CK(cudaMemcpyAsync(st, rho, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (uz) AMLBM_CK(cudaMemcpyAsync(st + T, uz, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  if (ur) AMLBM_CK(cudaMemcpyAsync(st + 2 * T, ur, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  AMLBM_CK(cudaMemsetAsync(bad, 0, sizeof(int), b->stream));
+  const cudaError_t e = amlbm::launch_init_all(b->storage, b->d_desc, b->n, off, T, st, uz ? st + T : nullptr,
+                                               ur ? st + 2 * T : nullptr, b->parity ^ 1, bad, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("init kernel: ") + cudaGetErrorString(e));
+  int nbad = 0;
+  AMLBM_CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  if (nbad)
+    return fail(AMLBM_EINVAL, "rho must be positive and finite at every site (" + std::to_string(nbad) +
+                                  " sites are not); the state is unchanged");
+  b->parity ^= 1;
+  // tile counters and step numbers (the stochastic-rounding stream) restart
+  // from zero, as in a new batch
+  AMLBM_CK(cudaMemsetAsync(b->d_ctr, 0, 4 * sizeof(int), b->stream));
+  for (auto& s : b->steps) s = 0;
+  return AMLBM_OK;
+}
+
+// Every instance in one read-back launch, one partial-sum launch and one final
+// launch; out[k] for instance k.  Unstable instances are reported after every
+// output is filled.
+int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) {
+  if (!b) return fail(AMLBM_EINVAL, "NULL batch");
+  if (!out) return fail(AMLBM_EINVAL, "out is NULL");
+  std::vector<amlbm::DiagJob> jobs(b->n);
+  int blk = 0, col = 0;
+  for (int k = 0; k < b->n; ++k) {
+    const InstDesc& d = b->desc[k];
+    const amlbm_diag_params p = dp ? dp[k] : diag_defaults(d);
+    if (!(p.R > 0) || !(p.rho_l != p.rho_v))
+      return fail(AMLBM_EINVAL, "diag params of instance " + std::to_string(k) + ": need R > 0, rho_l != rho_v");
+    amlbm::DiagJob& J = jobs[k];
+    J.zc = p.zc; J.R = p.R; J.rho_l = p.rho_l; J.rho_v = p.rho_v;
+    J.inst = k;
+    J.blk0 = blk;
+    J.nblk = amlbm::diag_blocks(d.Nz, d.Nr);
+    J.col0 = col;
+    blk += J.nblk;
+    col += d.Nz;
+  }
+  amlbm::DiagJob* d_jobs = reinterpret_cast<amlbm::DiagJob*>(b->arena + b->L.diag_jobs);
+  AMLBM_CK(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(jobs[0]), cudaMemcpyHostToDevice, b->stream));
+  cudaError_t e = amlbm::launch_macro(b->storage, 32, 8, b->d_desc, b->d_rb_tiles, b->L.rb_ntiles, 0,
+                                      b->parity, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
+  double* part = reinterpret_cast<double*>(b->arena + b->L.diag_part);
+  double* cols = reinterpret_cast<double*>(b->arena + b->L.diag_cols);
+  double* res = reinterpret_cast<double*>(b->arena + b->L.diag_out);
+  e = amlbm::launch_diag_all(b->storage, b->d_desc, d_jobs, b->n, blk, b->parity, part, cols, res, b->stream);
+  if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("diag kernels: ") + cudaGetErrorString(e));
+  std::vector<double> h((size_t)16 * b->n);
+  AMLBM_CK(cudaMemcpyAsync(h.data(), res, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  int first_bad = -1;
+  for (int k = 0; k < b->n; ++k) {
+    fill_diag(&h[(size_t)16 * k], b->steps[k], &out[k]);
+    if (out[k].bad > 0 && first_bad < 0) first_bad = k;
+  }
+  if (first_bad >= 0)
+    return fail(AMLBM_EUNSTABLE, "non-finite or non-positive density in instance " + std::to_string(first_bad) +
+                                     " (" + std::to_string((long long)out[first_bad].bad) + " sites)");
+  return AMLBM_OK;
+}
+
 int diag_host(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out) {
   int rc = check_k(b, k);
   if (rc) return rc;
   if (!out) return fail(AMLBM_EINVAL, "out is NULL");
   const InstDesc& d = b->desc[k];
-  amlbm_diag_params p;
-  if (dp) p = *dp;
-  else { p.zc = d.Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1; }
+  const amlbm_diag_params p = dp ? *dp : diag_defaults(d);
   if (!(p.R > 0) || !(p.rho_l != p.rho_v)) return fail(AMLBM_EINVAL, "diag params: need R > 0, rho_l != rho_v");
   rc = macro_for(b, k);
   if (rc) return rc;
@@ -426,11 +527,7 @@ int diag_host(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* ou
   double h[16];
   AMLBM_CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
   AMLBM_CK(cudaStreamSynchronize(b->stream));
-  std::memset(out, 0, sizeof(*out));
-  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
-  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
-  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
-  out->steps = (double)b->steps[k];
+  fill_diag(h, b->steps[k], out);
   if (out->bad > 0) return fail(AMLBM_EUNSTABLE, "non-finite or non-positive density at " +
                                                     std::to_string((long long)out->bad) + " sites");
   return AMLBM_OK;
@@ -498,6 +595,14 @@ int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur,
 
 int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out) {
   return diag_host(b, k, dp, out);
+}
+
+int amlbm_batch_init_all(amlbm_batch* b, const double* rho, const double* uz, const double* ur) {
+  return init_all_host(b, rho, uz, ur);
+}
+
+int amlbm_batch_diagnostics_all(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) {
+  return diag_all_host(b, dp, out);
 }
 
 long long amlbm_batch_sites(const amlbm_batch* b) { return b ? b->sites : 0; }

@@ -1,0 +1,256 @@
+// Diagnostics of a lattice state: FP64 sums over the meridional sites and the
+// interface radius of every column, for one instance or for every instance of
+// a batch in the same three launches.
+//
+// Quantities (r = j + 1/2 is the node radius, sums over real sites):
+//   mass2d = sum rho, mass3d = sum 2 pi r rho (the volume integral of the
+//   axisymmetric density, Sec. II.A), momz3d = sum 2 pi r rho u_z,
+//   E_ke = pi sum r rho |u|^2 (the kinetic energy whose constancy marks the
+//   steady pipe flow, Sec. III.A), max |u|, the l = 2 moment a_2 of the liquid
+//   fraction about the drop centre (Sec. III.C), the r-intercept of the
+//   interface on the centre column and its minimum over z (the neck of a thread,
+//   Sec. III.D), and the Shan-Chen pressure p = rho/3 + G psi^2/6 (the equation
+//   of state of Sec. II.B with c_s^2 = 1/3) inside and outside the drop.
+//
+// The read-back kernel must have written rho, u_z, u_r of the state into the
+// instance's rho_out / uz_out / ur_out arrays first.
+
+#include <cuda_runtime.h>
+
+#include "amlbm.h"
+#include "amlbm_internal.cuh"
+
+namespace amlbm {
+namespace {
+
+constexpr int DIAG_NT = 256;
+constexpr int DIAG_WARPS = DIAG_NT / 32;
+constexpr int NSUM = 8;  // mass2d mass3d momz3d Eke q2 sumS bad | umax (max-reduced)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Interface radius of column k, one warp: the first row (from the axis) whose
+// density is below mid, interpolated linearly against the row before it; 0 when
+// row 0 is already below, Nr when no row is.  Rows are scanned 32 at a time.
+__device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr, int k, double mid) {
+  const int lane = threadIdx.x & 31;
+  for (int j0 = 0; j0 < Nr; j0 += 32) {
+    const int j = j0 + lane;
+    const bool below = j < Nr && rho[(size_t)j * Nz + k] < mid;
+    const unsigned m = __ballot_sync(0xffffffffu, below);
+    if (m) {
+      const int jf = j0 + __ffs(m) - 1;
+      if (jf == 0) return 0.0;
+      const double v0 = rho[(size_t)(jf - 1) * Nz + k], v = rho[(size_t)jf * Nz + k];
+      return (jf - 1 + 0.5) + (v0 - mid) / (v0 - v);
+    }
+  }
+  return double(Nr);
+}
+
+// Block blk of the nblk blocks of job J: partial sums over the sites
+// blk*NT + tid + m*nblk*NT into partials[(J.blk0 + blk) * NSUM + q], and the
+// radii of the columns blk*WARPS + warp + m*nblk*WARPS into cols[J.col0 + k].
+__device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, double* partials,
+                              double* cols) {
+  const int Nz = D.Nz, Nr = D.Nr, N = Nz * Nr;
+  const double pi = 3.14159265358979323846;
+  double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int n = blk * DIAG_NT + threadIdx.x; n < N; n += J.nblk * DIAG_NT) {
+    const int j = n / Nz, k = n - j * Nz;
+    const double r = j + 0.5, rho = D.rho_out[n], uz = D.uz_out[n], ur = D.ur_out[n];
+    const double u2 = uz * uz + ur * ur;
+    acc[0] += rho;
+    acc[1] += 2 * pi * r * rho;
+    acc[2] += 2 * pi * r * rho * uz;
+    acc[3] += pi * r * rho * u2;
+    const double dz = k - J.zc;
+    acc[4] += 2 * pi * r * (rho - J.rho_v) / (J.rho_l - J.rho_v) * (dz * dz - 0.5 * r * r);
+    acc[5] += -rho * ur / r;
+    const bool bad = !(rho > 0) || !isfinite(rho) || !isfinite(u2);
+    acc[6] += bad ? 1.0 : 0.0;
+    acc[7] = fmax(acc[7], bad ? 0.0 : sqrt(u2));
+  }
+  __shared__ double red[DIAG_WARPS][NSUM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NSUM - 1; ++q) acc[q] = warp_sum(acc[q]);
+  acc[NSUM - 1] = warp_max(acc[NSUM - 1]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NSUM; ++q) red[warp][q] = acc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NSUM) {
+    const int q = threadIdx.x;
+    double v = red[0][q];
+    for (int w = 1; w < DIAG_WARPS; ++w) v = q == NSUM - 1 ? fmax(v, red[w][q]) : v + red[w][q];
+    partials[(size_t)(J.blk0 + blk) * NSUM + q] = v;
+  }
+  const double mid = 0.5 * (J.rho_l + J.rho_v);
+  for (int k = blk * DIAG_WARPS + warp; k < Nz; k += J.nblk * DIAG_WARPS) {
+    const double rad = col_radius_warp(D.rho_out, Nz, Nr, k, mid);
+    if (lane == 0) cols[J.col0 + k] = rad;
+  }
+}
+
+// One block: the job's partial sums and column radii reduced into out[16].
+template <class C>
+__device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, const double* partials,
+                            const double* cols, double* out) {
+  const int Nz = D.Nz, Nr = D.Nr;
+  double acc[NSUM + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300};
+  for (int b = threadIdx.x; b < J.nblk; b += DIAG_NT) {
+    const double* p = partials + (size_t)(J.blk0 + b) * NSUM;
+#pragma unroll
+    for (int q = 0; q < NSUM - 1; ++q) acc[q] += p[q];
+    acc[NSUM - 1] = fmax(acc[NSUM - 1], p[NSUM - 1]);
+  }
+  for (int k = threadIdx.x; k < Nz; k += DIAG_NT) acc[NSUM] = fmin(acc[NSUM], cols[J.col0 + k]);
+  __shared__ double red[DIAG_WARPS][NSUM + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NSUM - 1; ++q) acc[q] = warp_sum(acc[q]);
+  acc[NSUM - 1] = warp_max(acc[NSUM - 1]);
+  acc[NSUM] = warp_min(acc[NSUM]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q <= NSUM; ++q) red[warp][q] = acc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[NSUM + 1];
+#pragma unroll
+    for (int q = 0; q <= NSUM; ++q) t[q] = red[0][q];
+    for (int w = 1; w < DIAG_WARPS; ++w) {
+#pragma unroll
+      for (int q = 0; q < NSUM - 1; ++q) t[q] += red[w][q];
+      t[NSUM - 1] = fmax(t[NSUM - 1], red[w][NSUM - 1]);
+      t[NSUM] = fmin(t[NSUM], red[w][NSUM]);
+    }
+    const double pi = 3.14159265358979323846;
+    out[0] = t[0];
+    out[1] = t[1];
+    out[2] = t[2];
+    out[3] = t[3];
+    out[4] = t[7];
+    out[5] = 5.0 * t[4] / (4.0 * pi * pow(J.R, 5.0));
+    int kc = (int)llround(J.zc);
+    kc %= Nz;
+    if (kc < 0) kc += Nz;
+    out[6] = cols[J.col0 + kc];
+    out[7] = t[NSUM];
+    const C* psi = static_cast<const C*>(D.psi[parity]);
+    const double G = D.G;
+    auto pres = [&](int k, int j) {
+      const double rho = D.rho_out[(size_t)j * Nz + k], ps = double(psi[(size_t)j * D.P + k]);
+      return rho / 3.0 + G * ps * ps / 6.0;
+    };
+    const int ko = (kc + Nz / 2) % Nz;
+    out[8] = pres(kc, 0);
+    out[9] = pres(ko, Nr - 1);
+    out[10] = out[8] - out[9];
+    out[11] = t[6];
+    out[12] = t[5];
+    out[13] = out[14] = out[15] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(DIAG_NT) diag_partial_one(const InstDesc* __restrict__ descs, DiagJob J,
+                                                            double* partials, double* cols) {
+  partial_block(descs[J.inst], J, blockIdx.x, partials, cols);
+}
+
+template <class C>
+__global__ void __launch_bounds__(DIAG_NT) diag_final_one(const InstDesc* __restrict__ descs, DiagJob J,
+                                                          int parity, const double* partials,
+                                                          const double* cols, double* out) {
+  final_block<C>(descs[J.inst], J, parity, partials, cols, out);
+}
+
+// Every job of a batch: block b belongs to the job whose block range
+// [blk0, blk0 + nblk) holds b (jobs sorted by blk0).
+__global__ void __launch_bounds__(DIAG_NT) diag_partial_all(const InstDesc* __restrict__ descs,
+                                                            const DiagJob* __restrict__ jobs, int njobs,
+                                                            double* partials, double* cols) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].blk0 <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const DiagJob J = jobs[lo];
+  partial_block(descs[J.inst], J, blockIdx.x - J.blk0, partials, cols);
+}
+
+template <class C>
+__global__ void __launch_bounds__(DIAG_NT) diag_final_all(const InstDesc* __restrict__ descs,
+                                                          const DiagJob* __restrict__ jobs, int parity,
+                                                          const double* partials, const double* cols,
+                                                          double* out) {
+  const DiagJob J = jobs[blockIdx.x];
+  final_block<C>(descs[J.inst], J, parity, partials, cols, out + (size_t)16 * blockIdx.x);
+}
+
+}  // namespace
+
+int diag_blocks(int Nz, int Nr) {
+  const int N = Nz * Nr;
+  int nb = (N + DIAG_NT * 4 - 1) / (DIAG_NT * 4);
+  const int nbz = (Nz + DIAG_NT - 1) / DIAG_NT;
+  if (nb < nbz) nb = nbz;
+  if (nb > 1024) nb = 1024;
+  return nb < 1 ? 1 : nb;
+}
+
+cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr, int parity,
+                        double zc, double R, double rho_l, double rho_v, double* partials,
+                        int nblk, double* cols, double* out, cudaStream_t s) {
+  (void)Nz;
+  (void)Nr;
+  DiagJob J;
+  J.zc = zc;
+  J.R = R;
+  J.rho_l = rho_l;
+  J.rho_v = rho_v;
+  J.inst = inst;
+  J.blk0 = 0;
+  J.nblk = nblk;
+  J.col0 = 0;
+  diag_partial_one<<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
+  if (storage == AMLBM_STORE_F64)
+    diag_final_one<double><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
+  else
+    diag_final_one<float><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_jobs, int njobs,
+                            int total_blocks, int parity, double* partials, double* cols, double* out,
+                            cudaStream_t s) {
+  if (njobs < 1 || total_blocks < 1) return cudaErrorInvalidValue;
+  diag_partial_all<<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
+  if (storage == AMLBM_STORE_F64)
+    diag_final_all<double><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
+  else
+    diag_final_all<float><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
+  return cudaGetLastError();
+}
+
+}  // namespace amlbm

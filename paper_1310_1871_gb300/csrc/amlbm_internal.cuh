@@ -58,12 +58,31 @@ enum InterField {
 // f[0] / psi[0] hold that state, into inter (I_COUNT planes of plane elements).
 cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
                          int ntiles, void* inter, size_t plane, cudaStream_t s);
-// Diagnostics: partial sums into `partials` (nblk x 8 doubles, plus Nz column
-// radii), then a single-block pass into out[16].
+// Diagnostics (amlbm_diag.cu) of the state whose rho / u the read-back kernel
+// has written: partial sums into `partials` (nblk x 8 doubles) and the Nz column
+// radii into `cols`, then a single-block pass into out[16].
 cudaError_t launch_diag(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
                         int parity, double zc, double R, double rho_l, double rho_v,
                         double* partials, int nblk, double* cols, double* out, cudaStream_t s);
 int diag_blocks(int Nz, int Nr);
+// One instance's share of a batched diagnostics pass: its parameters, its
+// blocks [blk0, blk0 + nblk) of the partial-sum grid (nblk = diag_blocks) and
+// its columns [col0, col0 + Nz) of the radius array.
+struct DiagJob {
+  double zc, R, rho_l, rho_v;
+  int inst, blk0, nblk, col0;
+};
+// Every job in one partial launch (total_blocks = sum of nblk) and one final
+// launch (one block per job, out[16 * job]).
+cudaError_t launch_diag_all(int storage, const InstDesc* d_desc, const DiagJob* d_jobs, int njobs,
+                            int total_blocks, int parity, double* partials, double* cols, double* out,
+                            cudaStream_t s);
+// f = f^eq(rho, u) for every instance from device arrays holding all
+// instances back to back (site_off: n + 1 prefix offsets); counts the sites
+// whose rho is not positive and finite into *bad (which must start at zero).
+cudaError_t launch_init_all(int storage, const InstDesc* d_desc, int n, const long long* d_site_off,
+                            long long total, const double* rho, const double* uz, const double* ur,
+                            int parity, int* bad, cudaStream_t s);
 bool tile_supported(int storage, int schedule, int tz, int tr);
 int tile_list(int storage, int schedule, int* tz, int* tr, int cap);
 size_t step_smem_bytes(int storage, int tz, int tr);

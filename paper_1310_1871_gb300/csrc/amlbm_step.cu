@@ -836,28 +836,59 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
 }
 
 // f = f^eq(rho, u) (no force shift) and psi of the new state.
+// Site n = j*Nz + k of instance D: f = f^eq(rho, u) with u^eq = u (the
+// initial state of the scheme), stored in the instance's storage form, and psi.
 template <class S>
-__global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const double* rho_in,
-                            const double* uz_in, const double* ur_in, int parity) {
+__device__ __forceinline__ void init_site(const InstDesc& D, int n, double rho_d, double uz_d,
+                                          double ur_d, int parity) {
   using C = typename Store<S>::C;
-  const InstDesc& D = descs[inst];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= D.Nz * D.Nr) return;
   const int j = n / D.Nz, k = n - j * D.Nz;
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   S* f = static_cast<S*>(D.f[parity]);
   C* psi_out = static_cast<C*>(D.psi[parity]);
-  const C rho_i = C(rho_in[n]);
-  const C uz = uz_in ? C(uz_in[n]) : C(0), ur = ur_in ? C(ur_in[n]) : C(0);
   const C rho0 = C(D.rho0), rref = C(D.rho_ref);
   C fe[9];
-  equilibrium(rho_i, uz, ur, fe);
+  equilibrium(C(rho_d), C(uz_d), C(ur_d), fe);
   const C rho = moment0(fe);
   const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
   const C sb = shift_base(D.shift, psi, rcp_c(rho0), rho0, rref);
 #pragma unroll
   for (int i = 0; i < 9; ++i) f[i * plane + o] = Store<S>::from(fe[i] - C(w_(i)) * sb);
   psi_out[o] = psi;
+}
+
+template <class S>
+__global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const double* rho_in,
+                            const double* uz_in, const double* ur_in, int parity) {
+  const InstDesc& D = descs[inst];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= D.Nz * D.Nr) return;
+  init_site<S>(D, n, rho_in[n], uz_in ? uz_in[n] : 0.0, ur_in ? ur_in[n] : 0.0, parity);
+}
+
+// Every instance of a batch from arrays holding them back to back: global site
+// g belongs to the instance m with site_off[m] <= g < site_off[m + 1].  Sites
+// whose rho is not positive and finite are counted into *bad and the state is
+// written all the same (the caller writes into the buffers of the other parity
+// and discards them when *bad is non-zero).
+template <class S>
+__global__ void init_all_kernel(const InstDesc* __restrict__ descs, int n_inst,
+                                const long long* __restrict__ site_off, long long total,
+                                const double* rho_in, const double* uz_in, const double* ur_in,
+                                int parity, int* bad) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (site_off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const double rho = rho_in[g];
+  const bool ok = rho > 0 && isfinite(rho);
+  if (!ok) atomicAdd(bad, 1);
+  init_site<S>(descs[lo], (int)(g - site_off[lo]), ok ? rho : 1.0, uz_in ? uz_in[g] : 0.0,
+               ur_in ? ur_in[g] : 0.0, parity);
 }
 
 template <class S>
@@ -875,119 +906,6 @@ __global__ void unpack_kernel(const InstDesc* __restrict__ descs, int inst, int 
   const C sb = shift_base(D.shift, psi, rcp_c(C(D.rho0)), C(D.rho0), C(D.rho_ref));
 #pragma unroll
   for (int i = 0; i < 9; ++i) out[(size_t)i * N + n] = double(Store<S>::to(f[i * plane + o]) + C(w_(i)) * sb);
-}
-
-// ----------------------------------------------------------- diagnostics --
-constexpr int DIAG_NT = 256;
-constexpr int NSUM = 8;  // mass2d mass3d momz3d Eke q2 sumS bad umax
-
-__device__ __forceinline__ double col_radius(const double* rho, int Nz, int Nr, int k, double mid) {
-  for (int j = 0; j < Nr; ++j) {
-    const double v = rho[(size_t)j * Nz + k];
-    if (v < mid) {
-      if (j == 0) return 0.0;
-      const double v0 = rho[(size_t)(j - 1) * Nz + k];
-      return (j - 1 + 0.5) + (v0 - mid) / (v0 - v);
-    }
-  }
-  return double(Nr);
-}
-
-__global__ void __launch_bounds__(DIAG_NT) diag_partial_kernel(const InstDesc* __restrict__ descs,
-                                                               int inst, double zc, double rho_l,
-                                                               double rho_v, double* partials,
-                                                               double* cols) {
-  const InstDesc& D = descs[inst];
-  const int Nz = D.Nz, Nr = D.Nr, N = Nz * Nr;
-  const double pi = 3.14159265358979323846;
-  double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int n = blockIdx.x * DIAG_NT + threadIdx.x; n < N; n += gridDim.x * DIAG_NT) {
-    const int j = n / Nz, k = n - j * Nz;
-    const double r = j + 0.5, rho = D.rho_out[n], uz = D.uz_out[n], ur = D.ur_out[n];
-    const double u2 = uz * uz + ur * ur;
-    acc[0] += rho;
-    acc[1] += 2 * pi * r * rho;
-    acc[2] += 2 * pi * r * rho * uz;
-    acc[3] += pi * r * rho * u2;
-    const double dz = k - zc;
-    acc[4] += 2 * pi * r * (rho - rho_v) / (rho_l - rho_v) * (dz * dz - 0.5 * r * r);
-    acc[5] += -rho * ur / r;
-    const bool bad = !(rho > 0) || !isfinite(rho) || !isfinite(u2);
-    acc[6] += bad ? 1.0 : 0.0;
-    acc[7] = fmax(acc[7], bad ? 0.0 : sqrt(u2));
-  }
-  __shared__ double red[NSUM][DIAG_NT];
-#pragma unroll
-  for (int q = 0; q < NSUM; ++q) red[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int s = DIAG_NT / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-#pragma unroll
-      for (int q = 0; q < NSUM - 1; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
-      red[NSUM - 1][threadIdx.x] = fmax(red[NSUM - 1][threadIdx.x], red[NSUM - 1][threadIdx.x + s]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < NSUM) partials[blockIdx.x * NSUM + threadIdx.x] = red[threadIdx.x][0];
-  const double mid = 0.5 * (rho_l + rho_v);
-  for (int k = blockIdx.x * DIAG_NT + threadIdx.x; k < Nz; k += gridDim.x * DIAG_NT)
-    cols[k] = col_radius(D.rho_out, Nz, Nr, k, mid);
-}
-
-template <class C>
-__global__ void __launch_bounds__(DIAG_NT) diag_final_kernel(const InstDesc* __restrict__ descs,
-                                                             int inst, int parity, double zc,
-                                                             double R, const double* partials,
-                                                             int nblk, const double* cols,
-                                                             double* out) {
-  const InstDesc& D = descs[inst];
-  const int Nz = D.Nz, Nr = D.Nr;
-  __shared__ double red[NSUM + 1][DIAG_NT];
-  double acc[NSUM + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300};
-  for (int b = threadIdx.x; b < nblk; b += DIAG_NT) {
-#pragma unroll
-    for (int q = 0; q < NSUM - 1; ++q) acc[q] += partials[b * NSUM + q];
-    acc[NSUM - 1] = fmax(acc[NSUM - 1], partials[b * NSUM + NSUM - 1]);
-  }
-  for (int k = threadIdx.x; k < Nz; k += DIAG_NT) acc[NSUM] = fmin(acc[NSUM], cols[k]);
-#pragma unroll
-  for (int q = 0; q <= NSUM; ++q) red[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int s = DIAG_NT / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-#pragma unroll
-      for (int q = 0; q < NSUM - 1; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
-      red[NSUM - 1][threadIdx.x] = fmax(red[NSUM - 1][threadIdx.x], red[NSUM - 1][threadIdx.x + s]);
-      red[NSUM][threadIdx.x] = fmin(red[NSUM][threadIdx.x], red[NSUM][threadIdx.x + s]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double pi = 3.14159265358979323846;
-    out[0] = red[0][0];
-    out[1] = red[1][0];
-    out[2] = red[2][0];
-    out[3] = red[3][0];
-    out[4] = red[7][0];
-    out[5] = 5.0 * red[4][0] / (4.0 * pi * pow(R, 5.0));
-    int kc = (int)llround(zc);
-    kc %= Nz;
-    if (kc < 0) kc += Nz;
-    out[6] = cols[kc];
-    out[7] = red[NSUM][0];
-    const C* psi = static_cast<const C*>(D.psi[parity]);
-    const double G = D.G;
-    auto pres = [&](int k, int j) {
-      const double rho = D.rho_out[(size_t)j * Nz + k], ps = double(psi[(size_t)j * D.P + k]);
-      return rho / 3.0 + G * ps * ps / 6.0;
-    };
-    int ko = (kc + Nz / 2) % Nz;
-    out[8] = pres(kc, 0);
-    out[9] = pres(ko, Nr - 1);
-    out[10] = out[8] - out[9];
-    out[11] = red[6][0];
-    out[12] = red[5][0];
-  }
 }
 
 template <class S, int BZ, int BR, int MODE>
@@ -1176,6 +1094,26 @@ cudaError_t launch_init(int storage, const InstDesc* d, int inst, int Nz, int Nr
   return cudaGetLastError();
 }
 
+cudaError_t launch_init_all(int storage, const InstDesc* d, int n, const long long* site_off,
+                            long long total, const double* rho, const double* uz, const double* ur,
+                            int parity, int* bad, cudaStream_t s) {
+  if (total < 1) return cudaErrorInvalidValue;
+  const unsigned nb = (unsigned)((total + 255) / 256);
+  switch (storage) {
+    case AMLBM_STORE_F64:
+      init_all_kernel<double><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+    case AMLBM_STORE_F32:
+      init_all_kernel<float><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+    case AMLBM_STORE_F16:
+      init_all_kernel<__half><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+    case AMLBM_STORE_BF16:
+      init_all_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(int storage, const InstDesc* d, int inst, int Nz, int Nr, int parity,
                           double* out, cudaStream_t s) {
   const int N = Nz * Nr, nb = (N + 255) / 256;
@@ -1186,28 +1124,6 @@ cudaError_t launch_unpack(int storage, const InstDesc* d, int inst, int Nz, int 
     case AMLBM_STORE_BF16: unpack_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(d, inst, parity, out); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-int diag_blocks(int Nz, int Nr) {
-  const int N = Nz * Nr;
-  int nb = (N + DIAG_NT * 4 - 1) / (DIAG_NT * 4);
-  const int nbz = (Nz + DIAG_NT - 1) / DIAG_NT;
-  if (nb < nbz) nb = nbz;
-  if (nb > 1024) nb = 1024;
-  return nb < 1 ? 1 : nb;
-}
-
-cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr, int parity,
-                        double zc, double R, double rho_l, double rho_v, double* partials,
-                        int nblk, double* cols, double* out, cudaStream_t s) {
-  (void)Nr;
-  diag_partial_kernel<<<nblk, DIAG_NT, 0, s>>>(d, inst, zc, rho_l, rho_v, partials, cols);
-  if (storage == AMLBM_STORE_F64)
-    diag_final_kernel<double><<<1, DIAG_NT, 0, s>>>(d, inst, parity, zc, R, partials, nblk, cols, out);
-  else
-    diag_final_kernel<float><<<1, DIAG_NT, 0, s>>>(d, inst, parity, zc, R, partials, nblk, cols, out);
-  (void)Nz;
   return cudaGetLastError();
 }
 

@@ -1,0 +1,115 @@
+"""Whole-batch entry points: amlbm_batch_init_all and amlbm_batch_diagnostics_all
+give exactly what the per-instance calls give, and a rejected init leaves the
+state unchanged."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1310_1871_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1310_1871_gb300 import amlbm  # noqa: E402
+
+SPECS = [(48, 24, 0.9, -5.0, dict()), (70, 21, 0.75, -4.7, dict(wall="noslip")),
+         (33, 16, 1.1, -5.3, dict(src="link")), (40, 20, 1.0, -5.0, dict(axisym=False))]
+
+
+def make(storage, graph_chunk=0, stream=None):
+    specs = [amlbm.InstanceSpec(Nz, Nr, tau, G, **kw) for Nz, Nr, tau, G, kw in SPECS]
+    fields = []
+    for k, (Nz, Nr, _, _, _) in enumerate(SPECS):
+        rho, uz, ur = I.drop(Nz, Nr, Nz / 2, Nr / 2.5, amps=(0.04,))
+        fields.append((rho, uz + 0.01 * (k % 2), ur))
+    return amlbm.Batch(specs, storage=storage, tile=(32, 8), graph_chunk=graph_chunk, stream=stream), fields
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+def test_init_all_equals_per_instance_init(storage):
+    a, fields = make(storage)
+    b, _ = make(storage)
+    for k, fl in enumerate(fields):
+        a.init_fields(k, *fl)
+    b.init_all(*[[fl[q] for fl in fields] for q in range(3)])
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    a.step(25)
+    b.step(25)  # the step after a parity change takes every tile (counters reset)
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    a.close()
+    b.close()
+
+
+def test_init_all_with_graphs_and_repeated_calls():
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a, fields = make("bf16", graph_chunk=4, stream=stream)
+        b, _ = make("bf16", stream=stream)
+        cols = [[fl[q] for fl in fields] for q in range(3)]
+        for _ in range(3):  # each call flips the parity
+            a.init_all(*cols)
+            a.step(9)
+        b.init_all(*cols)
+        b.step(9)
+        for k in range(len(fields)):
+            assert np.array_equal(a.read_f(k), b.read_f(k)), k
+        a.close()
+        b.close()
+
+
+def test_init_all_rejects_bad_density_and_keeps_state():
+    b, fields = make("f32")
+    cols = [[fl[q] for fl in fields] for q in range(3)]
+    b.init_all(*cols)
+    b.step(5)
+    before = [b.read_f(k) for k in range(len(fields))]
+    bad = [np.array(x, copy=True) for x in cols[0]]
+    bad[2][3, 4] = np.nan
+    bad[0][0, 0] = -1.0
+    with pytest.raises(amlbm.AmlbmError) as e:
+        b.init_all(bad, cols[1], cols[2])
+    assert e.value.code == amlbm.EINVAL and "2 sites" in str(e.value)
+    for k in range(len(fields)):
+        assert np.array_equal(b.read_f(k), before[k]), k
+    b.step(3)  # still steps from the kept state
+    ref, _ = make("f32")
+    ref.init_all(*cols)
+    ref.step(8)
+    for k in range(len(fields)):
+        assert np.array_equal(b.read_f(k), ref.read_f(k)), k
+    b.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+def test_diagnostics_all_equals_per_instance(storage):
+    b, fields = make(storage)
+    for k, fl in enumerate(fields):
+        b.init_fields(k, *fl)
+    b.step(40)
+    params = [dict(zc=Nz / 2, R=Nr / 2.5, rho_l=1.93, rho_v=0.16) for Nz, Nr, _, _, _ in SPECS]
+    all_ = b.diagnostics_all(params)
+    for k, p in enumerate(params):
+        one = b.diagnostics(k, **p)
+        assert one == all_[k], k
+    assert b.diagnostics_all() == [b.diagnostics(k) for k in range(len(SPECS))]
+    b.close()
+
+
+def test_diagnostics_all_against_oracle():
+    Nz, Nr, tau, G, _ = SPECS[0]
+    b, fields = make("f64")
+    for k, fl in enumerate(fields):
+        b.init_fields(k, *fl)
+    b.step(60)
+    d = b.diagnostics_all([dict(zc=Nz / 2, R=Nr / 2.5, rho_l=1.93, rho_v=0.16)] * len(SPECS))[0]
+    o = O.Oracle(Nz, Nr, tau=tau, G=G)
+    e = o.diag(o.run(o.init(*fields[0]), 60), Nz / 2, Nr / 2.5, 1.93, 0.16)
+    for key in ("mass2d", "mass3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out", "dp"):
+        assert abs(d[key] - e[key]) <= 1e-10 * abs(e[key]), (key, d[key], e[key])
+    b.close()
