@@ -65,6 +65,16 @@ def profiled_traffic(kernel_src):
     return d.get("dram_bytes_per_launch"), d.get("kernel")
 
 
+def autotune_summary(tuned):
+    """The autotuner's five fastest candidates (schedule, tile, MLUPS on back-to-back steps)."""
+    if not tuned:
+        return None
+    c = sorted(tuned["candidates"], key=lambda x: x["ms_per_step"])
+    return {"chosen": [tuned["schedule"], tuned["tile"]], "cached": tuned.get("cached"),
+            "candidates": len(c),
+            "top": [[x["schedule"], x["tile"], round(x["mlups"], 1)] for x in c[:5]]}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -151,7 +161,7 @@ def job_mlups(sites_per_rank, steps, max_ms, world):
     return world * sites_per_rank * steps / (max_ms * 1e-3) / 1e6
 
 
-def build_batch(storage, rank, tile=None, graph_chunk=0, stream=None):
+def build_batch(storage, rank, tile="auto", graph_chunk=0, stream=None):
     from paper_1310_1871_gb300 import amlbm
     inst = I.batch_sweep(64, seed0=rank_seed0(rank))
     specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
@@ -193,6 +203,7 @@ def run_gpu(args):
         b, inst = build_batch(STORAGE, rank, stream=stream)
         sites = b.sites
         sched, tile, lps = b.schedule, b.tile, b.launches_per_step
+        tuned = b.tuned
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -259,7 +270,8 @@ def run_gpu(args):
             "metric": METRIC, "value": round(mlups, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(avg_ms, 6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config(sites, tile=tile, schedule=sched),
+            "data": "synthetic", "config": dict(config(sites, tile=tile, schedule=sched),
+                                                autotune=autotune_summary(tuned)),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4),
                          "traffic": (round(traffic) if traffic and tkernel == kname else None),

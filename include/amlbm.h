@@ -265,6 +265,25 @@ typedef struct amlbm_batch amlbm_batch;
  * returns the count (tz, tr may be NULL to query it). */
 int amlbm_tiles(int storage, int schedule, int* tz, int* tr, int cap);
 
+/* One candidate of the autotuner and its measured step time. */
+typedef struct amlbm_tune_result {
+  amlbm_tune tune;
+  double ms_per_step; /* fastest of three timed repeats, CUDA events on the stream */
+  double mlups;       /* sites of all instances / ms_per_step */
+} amlbm_tune_result;
+
+/* Autotuner (no counterpart in the paper, which fixes no launch shape): for the
+ * n instances (all with inst[0].bc.storage) it creates a temporary batch for
+ * every compiled (schedule, tile) pair, sets a resting drop on every lattice,
+ * runs 3 warm-up and 3 x `steps` timed timesteps on cuda_stream, and writes the
+ * fastest pair to *best (graph_chunk 0) and, when results is not NULL, up to cap
+ * candidates with their timings.  Every candidate computes the same state.
+ * Allocates and frees device memory for each candidate (it is not capturable)
+ * and synchronises the stream.  Returns the number of candidates timed (> 0)
+ * or a negative status. */
+int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void* cuda_stream,
+                   amlbm_tune* best, amlbm_tune_result* results, int cap);
+
 size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst);
 
 /* n independent lattices stepped together: one kernel launch per timestep covers

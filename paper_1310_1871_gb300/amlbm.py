@@ -71,6 +71,10 @@ class Tune(ctypes.Structure):
                 ("schedule", ctypes.c_int)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tune", Tune), ("ms_per_step", ctypes.c_double), ("mlups", ctypes.c_double)]
+
+
 SCHEDULE = {"auto": 0, "fused": 1, "split": 2}
 
 
@@ -82,6 +86,7 @@ EXPORTS = [
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
     "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
     "amlbm_objective", "amlbm_batch_config", "amlbm_batch_init_all", "amlbm_batch_diagnostics_all",
+    "amlbm_autotune",
 ]
 
 
@@ -122,6 +127,8 @@ def load(build_if_missing: bool = True):
         lib.amlbm_batch_step.argtypes = [vp, ip]
         lib.amlbm_batch_read.argtypes = [vp, ip, dp, dp, dp, dp]
         lib.amlbm_batch_diagnostics.argtypes = [vp, ip, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
+        lib.amlbm_autotune.argtypes = [ip, ctypes.POINTER(InstanceC), ip, vp, ctypes.POINTER(Tune),
+                                       ctypes.POINTER(TuneResult), ip]
         lib.amlbm_batch_init_all.argtypes = [vp, dp, dp, dp]
         lib.amlbm_batch_diagnostics_all.argtypes = [vp, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
         lib.amlbm_batch_sites.argtypes = [vp]
@@ -196,8 +203,41 @@ class InstanceSpec:
     rounding: str = "default"
 
 
+def instances_c(specs, storage):
+    """The amlbm_instance array of a list of InstanceSpec."""
+    specs = list(specs)
+    arr = (InstanceC * len(specs))()
+    for i, s in enumerate(specs):
+        arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
+                           make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift,
+                                   s.rounding))
+    return arr
+
+
+def autotune_raw(specs, storage, steps=20, stream=None):
+    """Run amlbm_autotune: returns (schedule, (tile_z, tile_r), [candidate dicts])."""
+    lib = load()
+    arr = instances_c(specs, storage)
+    sh, _ = _stream_handle(stream)
+    best = Tune()
+    cap = 128
+    res = (TuneResult * cap)()
+    n = lib.amlbm_autotune(len(arr), arr, int(steps), sh, ctypes.byref(best), res, cap)
+    if n < 0:
+        _check(lib, n)
+    names = {1: "fused", 2: "split"}
+    cands = [{"schedule": names[r.tune.schedule], "tile": [r.tune.tile_z, r.tune.tile_r],
+              "ms_per_step": r.ms_per_step, "mlups": r.mlups} for r in res[:min(n, cap)]]
+    return names[best.schedule], (best.tile_z, best.tile_r), cands
+
+
 class Batch:
-    """Independent lattices stepped together, one kernel launch per timestep."""
+    """Independent lattices stepped together, one kernel launch per timestep.
+
+    tile=None lets the library pick the launch shape by a size heuristic;
+    tile="auto" takes the autotuner's choice for these lattice shapes (cached,
+    see autotune.py); a (tile_z, tile_r) pair with schedule="fused" or "split"
+    forces one."""
 
     def __init__(self, specs, storage="f32", tile=None, graph_chunk=0, stream=None, schedule="auto"):
         import torch
@@ -206,11 +246,14 @@ class Batch:
             raise RuntimeError("amlbm needs a CUDA device")
         self.specs = list(specs)
         n = len(self.specs)
-        arr = (InstanceC * n)()
-        for i, s in enumerate(self.specs):
-            arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
-                               make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift,
-                                       s.rounding))
+        self.tuned = None
+        if isinstance(tile, str):
+            if tile != "auto":
+                raise ValueError("tile must be None, 'auto' or a (tile_z, tile_r) pair")
+            from . import autotune
+            self.tuned = autotune.tune(self.specs, storage, stream=stream)
+            schedule, tile = self.tuned["schedule"], tuple(self.tuned["tile"])
+        arr = instances_c(self.specs, storage)
         self._arr = arr
         nbytes = self.lib.amlbm_batch_workspace_bytes(n, arr)
         if nbytes == 0:

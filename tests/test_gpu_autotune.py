@@ -1,0 +1,77 @@
+"""The autotuner times every compiled schedule and tile, and its choice computes
+the same state as any other launch shape."""
+import numpy as np
+import pytest
+
+from paper_1310_1871_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1310_1871_gb300 import amlbm  # noqa: E402
+
+
+def sweep(n=6):
+    inst = I.batch_sweep(n, seed0=77)
+    return inst, [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f64"])
+def test_autotune_times_every_candidate(storage):
+    _, specs = sweep()
+    sched, tile, cands = amlbm.autotune_raw(specs, storage, steps=5)
+    n_expected = len(amlbm.tiles(storage, "fused")) + len(amlbm.tiles(storage, "split"))
+    assert len(cands) == n_expected
+    assert all(c["ms_per_step"] > 0 for c in cands)
+    fastest = min(cands, key=lambda c: c["ms_per_step"])
+    assert (fastest["schedule"], tuple(fastest["tile"])) == (sched, tile)
+
+
+def test_autotuned_batch_equals_fixed_tile(monkeypatch):
+    monkeypatch.setenv("AMLBM_TUNE_CACHE", "off")
+    inst, specs = sweep()
+    out = []
+    for tile in ("auto", (32, 8)):
+        b = amlbm.Batch(specs, storage="bf16", tile=tile)
+        for k, x in enumerate(inst):
+            b.init_fields(k, *x.make_fields())
+        b.step(30)
+        out.append([b.read_f(k) for k in range(len(inst))])
+        if tile == "auto":
+            assert b.tuned and (b.schedule, list(b.tile)) == (b.tuned["schedule"], b.tuned["tile"])
+        b.close()
+    for a, c in zip(*out):
+        # instance 3 (tau 0.62, G -5.48) goes unstable in the scheme itself within
+        # 15 steps (the FP64 oracle too): NaN must sit at the same sites
+        assert np.array_equal(a, c, equal_nan=True)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+def test_every_compiled_tile_gives_the_same_state(storage):
+    """Every (schedule, tile) the autotuner may choose computes the state of the
+    fused 32 x 8 launch bit for bit (uneven lattices, ragged tiles, both walls)."""
+    specs = [amlbm.InstanceSpec(70, 21, 0.8, -5.2), amlbm.InstanceSpec(45, 33, 1.0, -4.8, wall="noslip"),
+             amlbm.InstanceSpec(130, 9, 0.7, -5.0, src="link")]
+    fields = [I.drop(70, 21, 35.0, 8.0, amps=(0.05,)), I.drop(45, 33, 22.0, 10.0),
+              I.drop(130, 9, 65.0, 6.0)]
+
+    def run(schedule, tile):
+        b = amlbm.Batch(specs, storage=storage, tile=tile, schedule=schedule)
+        for k, fl in enumerate(fields):
+            b.init_fields(k, *fl)
+        b.step(12)
+        out = [b.read_f(k) for k in range(len(specs))]
+        b.close()
+        return out
+
+    ref = run("fused", (32, 8))
+    bad = []
+    for sched in ("fused", "split"):
+        for tile in amlbm.tiles(storage, sched):
+            got = run(sched, tile)
+            if not all(np.array_equal(a, c) for a, c in zip(ref, got)):
+                bad.append((sched, tile))
+    assert not bad, bad
