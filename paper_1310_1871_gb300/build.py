@@ -20,6 +20,10 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["amlbm_step.cu", "amlbm_abi.cu", "amlbm_diag.cu", "amlbm_noalloc.cu", "amlbm_adjoint.cu", "amlbm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# The step kernels state every fused multiply-add explicitly; no other multiply
+# and add may be fused by the compiler, so that a site computed in one packed
+# FP32x2 lane and in a scalar lane rounds identically.
+FILE_FLAGS = {"amlbm_step.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -45,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

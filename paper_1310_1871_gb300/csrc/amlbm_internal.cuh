@@ -19,6 +19,11 @@ struct InstDesc {
   int shift;     // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
   int rounding;  // 16-bit storage: 0 to nearest, 1 stochastic
   double tau, G, rho0, gz, rho_ref;
+  // the constants of the step, computed on the host in FP64 and also held
+  // rounded to FP32 (kernels read them without conversion or division):
+  // tau, 1/tau, -G, -G/18, g_z, rho0, 1/rho0, (tau - 1/2)/3, rho_ref
+  double k64[9];
+  float k32[9];
   void* f[2];
   void* psi[2];
   void* uv;         // split schedule: u_z, u_r, u^eq_z, u^eq_r, 4 planes [Nr][P] of the compute type
@@ -31,8 +36,10 @@ struct InstDesc {
 // Every launcher returns the cudaGetLastError() of its launch.
 // The step and macro kernels run CTAs for the flattened tiles
 // [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
-// (force kernel, then collide-stream kernel).
-enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
+// (force kernel, then collide-stream kernel), 3 paired (the fused update of two
+// side-by-side tiles per CTA in packed FP32x2 arithmetic; FP32-arithmetic
+// storage forms only; tz is the width of the pair).
+enum { SCHED_FUSED = 1, SCHED_SPLIT = 2, SCHED_PAIRED = 3 };
 // ctr (four ints, zero at creation): tile counters of the persistent fused
 // grid and the step numbers for stochastic rounding, one per parity; nullptr
 // launches one CTA per tile.
@@ -85,7 +92,6 @@ cudaError_t launch_init_all(int storage, const InstDesc* d_desc, int n, const lo
                             int parity, int* bad, cudaStream_t s);
 bool tile_supported(int storage, int schedule, int tz, int tr);
 int tile_list(int storage, int schedule, int* tz, int* tr, int cap);
-size_t step_smem_bytes(int storage, int tz, int tr);
 
 // Access to a lattice context for entry points defined outside the ABI file
 // (amlbm_abi.cu implements these).

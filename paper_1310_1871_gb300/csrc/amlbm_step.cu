@@ -1,6 +1,6 @@
 // Fused axisymmetric Shan-Chen LBM step for sm_103a (arXiv:1310.1871, Sec. II).
 //
-// One CTA updates one tile of BZ x BR sites of one lattice of a batch.  The
+// One CTA updates one tile of lattice sites of one lattice of a batch.  The
 // whole per-site chain of the paper's update runs inside the CTA:
 //   psi tile + halo 7 (from the previous step's psi, staged in shared memory)
 //   -> isotropic d_r psi and 1D d_r psi (Sec. II.D), halo 5
@@ -12,6 +12,15 @@
 // Global traffic per site and step: 9 populations read (halo re-reads hit L2),
 // 9 written, psi written once and read once (halo re-reads hit L2).
 // No tensor cores: the update is a stencil, not a contraction.
+//
+// The arithmetic is written once on "lane" types: F1 (one site in FP32), D1
+// (one site in FP64) and F2 (two sites in FP32, in the packed FP32x2
+// instructions of sm_100 and later: one FFMA2 / FADD2 / FMUL2 serves both).
+// The paired schedule gives each CTA two z-adjacent tiles of the same rows, one
+// per lane, so every stencil and every physics step is one packed instruction
+// for two sites.  Each operation is an explicitly rounded intrinsic (nothing is
+// left to the compiler's contraction), so a site gets the same bits from an F2
+// lane as from an F1 lane, in whichever kernel it is computed.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -44,49 +53,114 @@ __host__ __device__ constexpr int opp_(int i) {
        : i == 5 ? 7 : i == 7 ? 5 : i == 6 ? 8 : 6;
 }
 
+// ---------------------------------------------------------------- lanes --
+struct F1 { float v; };
+struct D1 { double v; };
+struct __align__(8) F2 { float2 v; };
+
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return {__fadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return {__fsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return {__fmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ F1 operator-(F1 a) { return {-a.v}; }
+__device__ __forceinline__ F1 fma(F1 a, F1 b, F1 c) { return {__fmaf_rn(a.v, b.v, c.v)}; }
+
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return {__dadd_rn(a.v, b.v)}; }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return {__dsub_rn(a.v, b.v)}; }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {__dmul_rn(a.v, b.v)}; }
+__device__ __forceinline__ D1 operator-(D1 a) { return {-a.v}; }
+__device__ __forceinline__ D1 fma(D1 a, D1 b, D1 c) { return {__fma_rn(a.v, b.v, c.v)}; }
+
+// a - b is a + (-b) exactly, so FADD2 with a negated operand rounds as FSUB.
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__fadd2_rn(a.v, (-b).v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+
+template <class T> struct Lane;
+template <> struct Lane<F1> { using C = float; static constexpr int N = 1; };
+template <> struct Lane<D1> { using C = double; static constexpr int N = 1; };
+template <> struct Lane<F2> { using C = float; static constexpr int N = 2; };
+
+template <class T> __device__ __forceinline__ T lit(double c);
+template <> __device__ __forceinline__ F1 lit<F1>(double c) { return {float(c)}; }
+template <> __device__ __forceinline__ D1 lit<D1>(double c) { return {c}; }
+template <> __device__ __forceinline__ F2 lit<F2>(double c) { return {make_float2(float(c), float(c))}; }
+
+__device__ __forceinline__ float lane(F1 a, int) { return a.v; }
+__device__ __forceinline__ double lane(D1 a, int) { return a.v; }
+__device__ __forceinline__ float lane(F2 a, int l) { return l ? a.v.y : a.v.x; }
+
+template <class T> __device__ __forceinline__ T pack(const typename Lane<T>::C* c);
+template <> __device__ __forceinline__ F1 pack<F1>(const float* c) { return {c[0]}; }
+template <> __device__ __forceinline__ D1 pack<D1>(const double* c) { return {c[0]}; }
+template <> __device__ __forceinline__ F2 pack<F2>(const float* c) { return {make_float2(c[0], c[1])}; }
+
+// Reciprocal and exponential, per lane.  FP32 uses the correctly rounded
+// reciprocal and the SFU exponential (relative error ~1e-7, far below the
+// storage rounding); FP64 the correctly rounded reciprocal and exp.
+__device__ __forceinline__ F1 rcp(F1 a) { return {__frcp_rn(a.v)}; }
+__device__ __forceinline__ D1 rcp(D1 a) { return {__drcp_rn(a.v)}; }
+__device__ __forceinline__ F2 rcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
+__device__ __forceinline__ F1 expl(F1 a) { return {__expf(a.v)}; }
+__device__ __forceinline__ D1 expl(D1 a) { return {exp(a.v)}; }
+__device__ __forceinline__ F2 expl(F2 a) { return {make_float2(__expf(a.v.x), __expf(a.v.y))}; }
+
+// ------------------------------------------------------------- storage --
 // Storage codecs: conversion between the stored element and the arithmetic
 // type.  The shift W_i s of the FP32 / 16-bit forms is applied by the callers
 // (decode: f = q + W_i s; encode: q = f - W_i s).  IEEE half holds q * 2^10 so
 // that the shifted populations (down to ~1e-7) stay in its normal range; the
 // power-of-two scale is exact.  from_sr rounds stochastically with the random
-// bits r: the bits below the stored precision are added to r and truncated, so
-// a value rounds up with probability equal to its distance from the lower
-// neighbour (unbiased in expectation).
+// word x: its top bits are added to the bits below the stored precision and the
+// sum is truncated, so a value rounds up with probability equal to its distance
+// from the lower neighbour (unbiased in expectation).
 template <class S> struct Store;
 template <> struct Store<double> {
   using C = double;
+  using T = D1;
   static __device__ __forceinline__ C to(double v) { return v; }
   static __device__ __forceinline__ double from(C v) { return v; }
   static __device__ __forceinline__ double from_sr(C v, uint32_t) { return v; }
 };
 template <> struct Store<float> {
   using C = float;
+  using T = F1;
   static __device__ __forceinline__ C to(float v) { return v; }
   static __device__ __forceinline__ float from(C v) { return v; }
   static __device__ __forceinline__ float from_sr(C v, uint32_t) { return v; }
 };
 template <> struct Store<__half> {
   using C = float;
+  using T = F1;
   static __device__ __forceinline__ C to(__half v) { return __half2float(v) * (1.0f / 1024.0f); }
   static __device__ __forceinline__ __half from(C v) { return __float2half_rn(v * 1024.0f); }
-  static __device__ __forceinline__ __half from_sr(C v, uint32_t r) {
+  static __device__ __forceinline__ __half from_sr(C v, uint32_t x) {
     // FP32 keeps 13 more mantissa bits than FP16 (for FP16-normal values)
-    const uint32_t b = __float_as_uint(v * 1024.0f) + (r & 0x1FFFu);
+    const uint32_t b = __float_as_uint(v * 1024.0f) + (x >> 19);
     return __float2half_rz(__uint_as_float(b));
   }
 };
 template <> struct Store<__nv_bfloat16> {
   using C = float;
+  using T = F1;
   static __device__ __forceinline__ C to(__nv_bfloat16 v) { return __bfloat162float(v); }
   static __device__ __forceinline__ __nv_bfloat16 from(C v) { return __float2bfloat16_rn(v); }
-  static __device__ __forceinline__ __nv_bfloat16 from_sr(C v, uint32_t r) {
+  static __device__ __forceinline__ __nv_bfloat16 from_sr(C v, uint32_t x) {
     // bfloat16 is the upper half of the FP32 bit pattern
-    const uint32_t b = __float_as_uint(v) + (r & 0xFFFFu);
+    const uint32_t b = __float_as_uint(v) + (x >> 16);
     return __ushort_as_bfloat16((unsigned short)(b >> 16));
   }
 };
 
-// Integer hash for the stochastic-rounding bits (a xorshift-multiply mixer).
+__device__ __forceinline__ float fma_c(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_c(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Random words of the stochastic rounding.  Each site seeds its own stream with
+// an integer hash (a xorshift-multiply mixer) of (site, step); the nine
+// populations then take successive states of the linear congruential generator
+// x <- 1664525 x + 1013904223 (mod 2^32) (Knuth / Numerical Recipes constants),
+// whose top bits are the ones the codecs use.
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352dU;
@@ -95,31 +169,28 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
   return x;
 }
+__device__ __forceinline__ uint32_t lcg_next(uint32_t x) { return x * 1664525u + 1013904223u; }
 
-// Store the nine new populations of a site with the shift W_i sb, rounding to
-// nearest or (rounding != 0) stochastically with bits drawn from (site, step).
+// Store the nine new populations fn[i] of one site with the shift W_i sb,
+// rounding to nearest or (rounding != 0) stochastically with words drawn from
+// (site, step).
 template <class S>
 __device__ __forceinline__ void store_site(S* o, size_t plane, const typename Store<S>::C* fn,
                                            typename Store<S>::C sb, int rounding, uint32_t site,
                                            uint32_t step) {
   using C = typename Store<S>::C;
   if (sizeof(S) == 2 && rounding) {
-    const uint32_t h = mix32(site ^ mix32(step + 0x9E3779B9u));
+    uint32_t x = mix32(site ^ mix32(step + 0x9E3779B9u));
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      o[i * plane] = Store<S>::from_sr(fn[i] - C(w_(i)) * sb, mix32(h + 0x632BE5ABu * (uint32_t)(i + 1)));
+    for (int i = 0; i < 9; ++i) {
+      x = lcg_next(x);
+      o[i * plane] = Store<S>::from_sr(fma_c(C(-w_(i)), sb, fn[i]), x);
+    }
   } else {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - C(w_(i)) * sb);
+    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fma_c(C(-w_(i)), sb, fn[i]));
   }
 }
-
-// exp / log / reciprocal of the arithmetic type.  The FP32 forms use the SFU
-// approximations (relative error ~1e-7, far below the storage rounding).
-__device__ __forceinline__ double exp_c(double x) { return exp(x); }
-__device__ __forceinline__ float exp_c(float x) { return __expf(x); }
-__device__ __forceinline__ double rcp_c(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_c(float x) { return __frcp_rn(x); }
 
 // Shift s of a site from its stored psi: 0 (none), rho_ref (global), or the
 // density recovered from psi, -rho0 ln(1 - psi/rho0) (local).  Writer and
@@ -151,6 +222,7 @@ __device__ __forceinline__ int reflect_row(int j, int Nr) {
   return j < 0 ? 0 : (j >= Nr ? Nr - 1 : j);
 }
 
+// ------------------------------------------------------------- physics --
 // Isotropic 4th-order first derivatives, Sec. II.D Eq. forthorder_firstderivativex:
 //   d_a phi(x) = (1/36) sum_i c_ia (8 phi(x + c_i) - phi(x + 2 c_i)).
 // p points at x in a row-major tile whose rows (r) are `st` apart.  The terms
@@ -158,77 +230,167 @@ __device__ __forceinline__ int reflect_row(int j, int Nr) {
 // field mirrored in z gives an exactly mirrored derivative: without this, the
 // rounding of the FP32 forms carries a net axial bias every step and a drop
 // drifts along the axis.
-template <class C>
-__device__ __forceinline__ C link8(const C* p, int dz, int dr, int st) {
-  return C(8) * p[dr * st + dz] - p[2 * dr * st + 2 * dz];
+template <class T>
+__device__ __forceinline__ T link8(const T* p, int dz, int dr, int st) {
+  return fma(lit<T>(8.0), p[dr * st + dz], -p[2 * dr * st + 2 * dz]);
 }
-template <class C>
-__device__ __forceinline__ C iso_r(const C* p, int st) {
-  const C a = link8(p, 0, 1, st) - link8(p, 0, -1, st);
-  const C b = (link8(p, 1, 1, st) + link8(p, -1, 1, st)) - (link8(p, 1, -1, st) + link8(p, -1, -1, st));
-  return (a + b) * C(1.0 / 36.0);
+template <class T>
+__device__ __forceinline__ T iso_r(const T* p, int st) {
+  const T a = link8(p, 0, 1, st) - link8(p, 0, -1, st);
+  const T b = (link8(p, 1, 1, st) + link8(p, -1, 1, st)) - (link8(p, 1, -1, st) + link8(p, -1, -1, st));
+  return (a + b) * lit<T>(1.0 / 36.0);
 }
-template <class C>
-__device__ __forceinline__ C iso_z(const C* p, int st) {
-  const C a = link8(p, 1, 0, st) - link8(p, -1, 0, st);
-  const C b = (link8(p, 1, 1, st) - link8(p, -1, 1, st)) + (link8(p, 1, -1, st) - link8(p, -1, -1, st));
-  return (a + b) * C(1.0 / 36.0);
+template <class T>
+__device__ __forceinline__ T iso_z(const T* p, int st) {
+  const T a = link8(p, 1, 0, st) - link8(p, -1, 0, st);
+  const T b = (link8(p, 1, 1, st) - link8(p, -1, 1, st)) + (link8(p, 1, -1, st) - link8(p, -1, -1, st));
+  return (a + b) * lit<T>(1.0 / 36.0);
 }
 // 1D 4th-order central difference with element step `step` (Sec. II.D).
-template <class C>
-__device__ __forceinline__ C d1(const C* p, int step) {
-  return (C(8) * (p[step] - p[-step]) - (p[2 * step] - p[-2 * step])) * C(1.0 / 12.0);
+template <class T>
+__device__ __forceinline__ T d1(const T* p, int step) {
+  return fma(lit<T>(8.0), p[step] - p[-step], -(p[2 * step] - p[-2 * step])) * lit<T>(1.0 / 12.0);
 }
 
-template <class C>
-__device__ __forceinline__ C feq(int i, C rho, C vz, C vr) {
-  const C cv = C(cz_(i)) * vz + C(cr_(i)) * vr;
-  const C vv = vz * vz + vr * vr;
-  return C(w_(i)) * rho * (C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * vv);
+// c_i . v of direction i
+template <class T>
+__device__ __forceinline__ T cdot(int i, T vz, T vr) {
+  switch (i) {
+    case 1: return vz;
+    case 2: return vr;
+    case 3: return -vz;
+    case 4: return -vr;
+    case 5: return vz + vr;
+    case 6: return vr - vz;
+    case 7: return -(vz + vr);
+    default: return vz - vr;
+  }
 }
-// rho = sum_i f_i, added in z-mirror pairs.
-template <class C>
-__device__ __forceinline__ C moment0(const C* f) {
+// rho = sum_i f_i and j = sum_i c_i f_i, added in z-mirror pairs.
+template <class T>
+__device__ __forceinline__ T moment0(const T* f) {
   return (f[0] + (f[2] + f[4])) + ((f[1] + f[3]) + ((f[5] + f[6]) + (f[7] + f[8])));
 }
-// h_i = W_i (S + (c_iz H_z + c_ir H_r) / c_s^2), Eq. condition_h.
-template <class C>
-__device__ __forceinline__ C source(int i, C S_, C Hz, C Hr) {
-  return C(w_(i)) * (S_ + C(3) * (C(cz_(i)) * Hz + C(cr_(i)) * Hr));
+template <class T>
+__device__ __forceinline__ T moment_z(const T* f) {
+  return (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
 }
-
-// The nine equilibria with f^eq_0 = rho - sum_{i>0} f^eq_i: the same value as
-// W_0 rho (1 - 1.5 u^2) in exact arithmetic, but the collision then conserves
-// mass to rounding.  With the directly evaluated f^eq_0 the FP32-rounded
-// weights do not sum to 1 and the FP32 forms gain mass every step (a 1.5e-5
-// drift over 1000 steps of the static drop, and a 1e-4 density error at the
-// interface).
-template <class C>
-__device__ __forceinline__ void equilibrium(C rho, C vz, C vr, C* fe) {
+template <class T>
+__device__ __forceinline__ T moment_r(const T* f) {
+  return (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
+}
+// The nine equilibria (Eq. feq; W_i rho (1 + 3 c.v + 4.5 (c.v)^2 - 1.5 v^2))
+// with f^eq_0 = rho - sum_{i>0} f^eq_i: the same value in exact arithmetic, but
+// the collision then conserves mass to rounding.  With the directly evaluated
+// f^eq_0 the FP32-rounded weights do not sum to 1 and the FP32 forms gain mass
+// every step (a 1.5e-5 drift over 1000 steps of the static drop, and a 1e-4
+// density error at the interface).
+template <class T>
+__device__ __forceinline__ void equilibrium(T rho, T vz, T vr, T* fe) {
+  const T A = fma(fma(vz, vz, vr * vr), lit<T>(-1.5), lit<T>(1.0));
+  const T r9 = rho * lit<T>(1.0 / 9.0), r36 = rho * lit<T>(1.0 / 36.0);
 #pragma unroll
-  for (int i = 1; i < 9; ++i) fe[i] = feq(i, rho, vz, vr);
+  for (int i = 1; i < 9; ++i) {
+    const T cv = cdot(i, vz, vr);
+    fe[i] = (i < 5 ? r9 : r36) * fma(fma(cv, lit<T>(4.5), lit<T>(3.0)), cv, A);
+  }
   fe[0] = rho - ((fe[2] + fe[4]) + ((fe[1] + fe[3]) + ((fe[5] + fe[6]) + (fe[7] + fe[8]))));
 }
-// The nine sources with h_0 = S - sum_{i>0} h_i, so that sum_i h_i = S to
-// rounding (the App. A zeroth moment) in every precision.
-template <class C>
-__device__ __forceinline__ void sources(C S_, C Hz, C Hr, C* h) {
+// h_i = W_i (S + (c_iz H_z + c_ir H_r) / c_s^2), Eq. condition_h, with
+// h_0 = S - sum_{i>0} h_i, so that sum_i h_i = S to rounding (the App. A
+// zeroth moment) in every precision.
+template <class T>
+__device__ __forceinline__ void sources(T S_, T Hz, T Hr, T* h) {
+  const T z3 = Hz * lit<T>(3.0), r3 = Hr * lit<T>(3.0);
 #pragma unroll
-  for (int i = 1; i < 9; ++i) h[i] = source(i, S_, Hz, Hr);
+  for (int i = 1; i < 9; ++i) h[i] = lit<T>(w_(i)) * (S_ + cdot(i, z3, r3));
   h[0] = S_ - ((h[2] + h[4]) + ((h[1] + h[3]) + ((h[5] + h[6]) + (h[7] + h[8]))));
 }
+// Shan-Chen neighbour sums sum_i W_i psi(x + c_i) c_i (Eq. scforce) around p.
+template <class T>
+__device__ __forceinline__ void sc_sums(const T* p, int Z, T& sz, T& sr) {
+  sz = fma(p[1] - p[-1], lit<T>(1.0 / 9.0),
+           ((p[Z + 1] - p[Z - 1]) + (p[-Z + 1] - p[-Z - 1])) * lit<T>(1.0 / 36.0));
+  sr = fma(p[Z] - p[-Z], lit<T>(1.0 / 9.0),
+           ((p[Z + 1] - p[-Z + 1]) + (p[Z - 1] - p[-Z - 1])) * lit<T>(1.0 / 36.0));
+}
+// The instance constants of the step in the lane type.
+template <class T>
+struct Par {
+  T tau, omega, negG, gfac, gz, rho0, inv_rho0, cmu;
+};
+enum { K_TAU, K_OMEGA, K_NEGG, K_GFAC, K_GZ, K_RHO0, K_INVRHO0, K_CMU, K_RREF };
+__device__ __forceinline__ float kc(const InstDesc& D, int c, float) { return D.k32[c]; }
+__device__ __forceinline__ double kc(const InstDesc& D, int c, double) { return D.k64[c]; }
+template <class T>
+__device__ __forceinline__ T splat(typename Lane<T>::C c);
+template <> __device__ __forceinline__ F1 splat<F1>(float c) { return {c}; }
+template <> __device__ __forceinline__ D1 splat<D1>(double c) { return {c}; }
+template <> __device__ __forceinline__ F2 splat<F2>(float c) { return {make_float2(c, c)}; }
+// q.gfac = -(G / 2) c_s^4 with c_s^4 = 1/9; q.cmu = mu / rho = c_s^2 (tau - 1/2)
+template <class T>
+__device__ __forceinline__ Par<T> par_of(const InstDesc& D) {
+  using C = typename Lane<T>::C;
+  Par<T> q;
+  q.tau = splat<T>(kc(D, K_TAU, C()));
+  q.omega = splat<T>(kc(D, K_OMEGA, C()));
+  q.negG = splat<T>(kc(D, K_NEGG, C()));
+  q.gfac = splat<T>(kc(D, K_GFAC, C()));
+  q.gz = splat<T>(kc(D, K_GZ, C()));
+  q.rho0 = splat<T>(kc(D, K_RHO0, C()));
+  q.inv_rho0 = splat<T>(kc(D, K_INVRHO0, C()));
+  q.cmu = splat<T>(kc(D, K_CMU, C()));
+  return q;
+}
+// 1 / r of row j, r = j + 1/2 (exact in either precision)
+__device__ __forceinline__ F1 inv_r_of(F1, int j) { return rcp(F1{__int2float_rn(j) + 0.5f}); }
+__device__ __forceinline__ F2 inv_r_of(F2, int j) {
+  const float r = __frcp_rn(__int2float_rn(j) + 0.5f);
+  return {make_float2(r, r)};
+}
+__device__ __forceinline__ D1 inv_r_of(D1, int j) { return rcp(D1{__int2double_rn(j) + 0.5}); }
 
+// Total force on a site (Eq. scforce, Eq. scAxisExtra, body force rho g_z).
+template <class T>
+__device__ __forceinline__ void forces(const Par<T>& q, T rho, T psi, T sz, T sr, bool ax, T dr0, T Drr,
+                                       T Dzr, T inv_r, T& Fz, T& Fr) {
+  const T gpsi = psi * q.negG;
+  Fz = gpsi * sz;
+  Fr = gpsi * sr;
+  if (ax) {
+    const T g = (psi * q.gfac) * inv_r;
+    Fz = fma(g, Dzr, Fz);
+    Fr = fma(g, fma(-dr0, inv_r, Drr), Fr);
+  }
+  Fz = fma(rho, q.gz, Fz);
+}
+// Axisymmetric sources of App. A at a site: S = -rho u_r / r,
+// H_z = (mu (d_r u_z + d_z u_r) - rho u_r u_z) / r,
+// H_r = (2 mu (d_r u_r - u_r / r) - rho u_r^2) / r.
+template <class T>
+__device__ __forceinline__ void site_sources(const Par<T>& q, T rho, T uz, T ur, T druz, T dzur, T drur,
+                                             T inv_r, T& S_, T& Hz, T& Hr) {
+  const T mu = rho * q.cmu, rur = rho * ur;
+  S_ = -(rur * inv_r);
+  Hz = fma(mu, druz + dzur, -(rur * uz)) * inv_r;
+  Hr = fma(mu * lit<T>(2.0), fma(-ur, inv_r, drur), -(rur * ur)) * inv_r;
+}
+// psi = rho0 (1 - exp(-rho / rho0)), Eq. psi.
+template <class T>
+__device__ __forceinline__ T psi_of(const Par<T>& q, T rho) {
+  return (lit<T>(1.0) - expl(-rho * q.inv_rho0)) * q.rho0;
+}
+
+// ---------------------------------------------------------------- tiles --
 // 256 threads per CTA.  A 2D region of a tile whose width is a multiple of 32
 // is walked as warp tasks: a task is a 32-wide segment of one row, so each warp
 // reads and writes one contiguous run of a row and branches that depend on the
-// row never diverge.
+// row never diverge.  A region whose width is not a multiple of 32 would leave
+// lanes idle in its last segment of every row (a 36-wide row costs 64 lanes),
+// so such regions are walked with a flat index instead (the division is by a
+// compile-time constant); a warp may then span two rows.
 constexpr int NT = 256, NWARP = NT / 32;
 
-//
-// A region whose width is not a multiple of 32 would leave lanes idle in its
-// last segment of every row (a 36-wide row costs 64 lanes), so such regions
-// are walked with a flat index instead (the division is by a compile-time
-// constant); a warp may then span two rows.
 template <int ROWS, int W, class F>
 __device__ __forceinline__ void for_tile(F&& body) {
   if constexpr (W % 32 == 0) {
@@ -246,10 +408,12 @@ __device__ __forceinline__ void for_tile(F&& body) {
   }
 }
 
-// Tile geometry.  Halos: psi 7, isotropic d_r psi 5, 1D d_r psi (z 5, r 3),
-// rho and u 3, collided populations and sources 1.
-template <class C, int BZ, int BR>
+// Tile geometry of one lane (BZ x BR sites).  Halos: psi 7, isotropic d_r psi
+// 5, 1D d_r psi (z 5, r 3), rho and u 3, collided populations and sources 1.
+// The integer maps hold the wrapped column of every lane and the mirrored row.
+template <class T, int BZ, int BR>
 struct Geo {
+  static constexpr int NL = Lane<T>::N;
   static constexpr int HP = 7, HD = 5, HF = 3;
   static constexpr int PZ = BZ + 2 * HP, PR = BR + 2 * HP;
   static constexpr int DZ = BZ + 2 * HD, DR = BR + 2 * HD;
@@ -259,8 +423,8 @@ struct Geo {
   static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER, nF = FZ * FR, nS = SZ * SR;
   // region A holds psi and its derivatives, later the sources S, H_z, H_r
   static constexpr int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
-  static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
-  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(nA + 3 * nF + 9 * nS);
+  static constexpr int int_bytes = ((NL * PZ + PR) * 4 + 15) / 16 * 16;
+  static constexpr size_t bytes = int_bytes + sizeof(T) * (size_t)(nA + 3 * nF + 9 * nS);
 };
 
 struct Tile {
@@ -279,55 +443,75 @@ __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_i
   return t;
 }
 
-// The fused update of one tile.  MODE 0: the timestep; MODE 1 (read-back):
-// only rho and u of the tile; MODE 2: the forward intermediates of the tile for
-// the adjoint (into `inter`, I_COUNT planes of `iplane` elements).
-// Resident CTAs per SM the register allocation must allow: five for the FP32
-// arithmetic forms (their tiles use at most ~40 KB of shared memory).
-template <class S>
-struct MinBlocks { static constexpr int value = std::is_same<S, double>::value ? 1 : 5; };
+// Resident CTAs per SM the register allocation must allow: five for the scalar
+// FP32 arithmetic forms (their tiles use at most ~40 KB of shared memory); for
+// the paired tiles as many as their shared memory lets fit in the 228 KB of an
+// SM (1 KB of it reserved per CTA), at most four (64 registers a thread).
+template <class S, class T, int BZ, int BR>
+struct MinBlocks {
+  static constexpr int fit = int((228u * 1024u) / (Geo<T, BZ, BR>::bytes + 1024u));
+  static constexpr int value = std::is_same<S, double>::value
+                                   ? 1
+                                   : (Lane<T>::N == 2 ? (fit > 4 ? 4 : (fit < 1 ? 1 : fit)) : 5);
+};
 
-template <class S, int BZ, int BR, int MODE>
+// The fused update of one tile, in lanes of type T: with F1 / D1 the tile is
+// BZ x BR sites; with F2 it is two side-by-side BZ x BR tiles (sites k0 + lc
+// in lane 0 and k0 + BZ + lc in lane 1, the same rows), i.e. a 2 BZ x BR tile
+// of the batch's tiling.  MODE 0: the timestep; MODE 1 (read-back, one lane
+// only): rho and u of the tile; MODE 2 (one lane only): the forward
+// intermediates of the tile for the adjoint (into `inter`, I_COUNT planes of
+// `iplane` elements).
+template <class S, class T, int BZ, int BR, int MODE>
 __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
                                          const int* __restrict__ tile_inst, int tile, int parity,
                                          typename Store<S>::C* __restrict__ inter, size_t iplane,
                                          uint32_t step = 0) {
   constexpr bool READBACK = MODE == 1;
   using C = typename Store<S>::C;
-  using G = Geo<C, BZ, BR>;
+  using G = Geo<T, BZ, BR>;
+  constexpr int NL = G::NL;
+  static_assert(NL == 1 || MODE == 0, "paired lanes run the timestep only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* colmap = reinterpret_cast<int*>(smem_raw);
-  int* rowmap = colmap + G::PZ;
-  C* base = reinterpret_cast<C*>(smem_raw + G::int_bytes);
-  C* sPsi = base;
-  C* sDr = sPsi + G::nP;
-  C* sD1 = sDr + G::nD;
-  C* sS = base;  // after stage 2
-  C* sHz = sS + G::nS;
-  C* sHr = sHz + G::nS;
-  C* sRho = base + G::nA;
-  C* sUz = sRho + G::nF;
-  C* sUr = sUz + G::nF;
-  C* sFs = sUr + G::nF;
+  int* colmap = reinterpret_cast<int*>(smem_raw);  // [NL][PZ]
+  int* rowmap = colmap + NL * G::PZ;
+  T* base = reinterpret_cast<T*>(smem_raw + G::int_bytes);
+  T* sPsi = base;
+  T* sDr = sPsi + G::nP;
+  T* sD1 = sDr + G::nD;
+  T* sS = base;  // after stage 2
+  T* sHz = sS + G::nS;
+  T* sHr = sHz + G::nS;
+  T* sRho = base + G::nA;
+  T* sUz = sRho + G::nF;
+  T* sUr = sUz + G::nF;
+  T* sFs = sUr + G::nF;
 
-  const Tile T = tile_of(descs, tile_inst, tile, BZ, BR, READBACK);
-  const InstDesc& D = descs[T.inst];
-  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  const Tile Tl = tile_of(descs, tile_inst, tile, NL * BZ, BR, READBACK);
+  const InstDesc& D = descs[Tl.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = Tl.k0, j0 = Tl.j0;
   const size_t plane = (size_t)P * Nr;
   const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
   const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
   const bool ax = D.axisym != 0;
   const int shift = D.shift;
-  const C tau = C(D.tau), omega = C(1) / tau, Gc = C(D.G), gz = C(D.gz), rho0 = C(D.rho0),
-          rref = C(D.rho_ref), gfac = -(Gc / C(2)) * C(1.0 / 9.0), inv_rho0 = rcp_c(rho0);
+  const Par<T> q = par_of<T>(D);
+  const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
 
-  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
+  for (int i = threadIdx.x; i < NL * G::PZ; i += NT) {
+    const int l = i / G::PZ, c = i - l * G::PZ;
+    colmap[i] = wrapz(k0 + l * BZ - G::HP + c, Nz);
+  }
   for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
   __syncthreads();
 
   // Stage 0: psi with ghost cells (periodic z, even mirror in r).
   for_tile<G::PR, G::PZ>([&](int lr, int lc) {
-    sPsi[lr * G::PZ + lc] = psin[(size_t)rowmap[lr] * P + colmap[lc]];
+    const C* row = psin + (size_t)rowmap[lr] * P;
+    C v[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) v[l] = row[colmap[l * G::PZ + lc]];
+    sPsi[lr * G::PZ + lc] = pack<T>(v);
   });
   __syncthreads();
 
@@ -342,92 +526,87 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     __syncthreads();
   }
 
-  // Stage 2 (tile + 3): moments, Shan-Chen force (Eq. scforce), axisymmetric
-  // force (Eq. scAxisExtra, c_s^4 = 1/9), body force, u (Eq. uhydro); on the
-  // tile + 1 also u^eq (Eq. ueq) and the BGK collision of all nine populations,
-  // kept in shared memory for the streaming stage.
+  // Stage 2 (tile + 3): moments, forces, u (Eq. uhydro); on the tile + 1 also
+  // u^eq (Eq. ueq) and the BGK collision of all nine populations, kept in
+  // shared memory for the streaming stage.
   for_tile<G::FR, G::FZ>([&](int lr, int lc) {
     const int j = j0 - G::HF + lr;
     if (j < 0 || j >= Nr) return;
-    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+    const T inv_r = inv_r_of(T(), j);
     const bool srow = lr >= 2 && lr < G::FR - 2;
+    const T* p = sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HF);
+    const T psi = p[0];
+    T f[9];
     {
-      const C* p = sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HF);
-      const C psi = p[0];
-      const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
-      const S* fp = fin + (size_t)j * P + colmap[lc + G::HP - G::HF];
-      C f[9];
+      C sb[NL], fl[NL];
+      const S* frow = fin + (size_t)j * P;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fp[i * plane]) + C(w_(i)) * sb;
-      // moments and the Shan-Chen neighbour sums in z-mirror pairs (see iso_r)
-      const C rho = moment0(f);
-      const C jz = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-      const C jr = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
-      const int Z = G::PZ;
-      const C sz = C(1.0 / 9.0) * (p[1] - p[-1]) +
-                   C(1.0 / 36.0) * ((p[Z + 1] - p[Z - 1]) + (p[-Z + 1] - p[-Z - 1]));
-      const C sr = C(1.0 / 9.0) * (p[Z] - p[-Z]) +
-                   C(1.0 / 36.0) * ((p[Z + 1] - p[-Z + 1]) + (p[Z - 1] - p[-Z - 1]));
-      C Fz = -Gc * psi * sz, Fr = -Gc * psi * sr;
-      if (ax) {
-        const C* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
-        const C Drr = iso_r(dr, G::DZ);
-        const C Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
-        const C g = gfac * psi * inv_r;
-        Fz += g * Dzr;
-        Fr += g * (Drr - dr[0] * inv_r);
+      for (int l = 0; l < NL; ++l) sb[l] = shift_base(shift, lane(psi, l), inv_rho0c, rho0c, rrefc);
+      const T sbt = pack<T>(sb);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+          fl[l] = Store<S>::to(frow[i * plane + colmap[l * G::PZ + lc + G::HP - G::HF]]);
+        f[i] = fma(lit<T>(w_(i)), sbt, pack<T>(fl));
       }
-      Fz += rho * gz;
-      const C inv_rho = rcp_c(rho);
-      const int fi = lr * G::FZ + lc;
-      sRho[fi] = rho;
-      sUz[fi] = (jz + C(0.5) * Fz) * inv_rho;
-      sUr[fi] = (jr + C(0.5) * Fr) * inv_rho;
-      if (MODE == 2 && lr >= G::HF && lr < G::HF + BR && lc >= G::HF && lc < G::HF + BZ &&
-          k0 + lc - G::HF < Nz) {
+    }
+    const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
+    T sz, sr;
+    sc_sums(p, G::PZ, sz, sr);
+    T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
+    if (ax) {
+      const T* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
+      dr0 = dr[0];
+      Drr = iso_r(dr, G::DZ);
+      Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
+    }
+    T Fz, Fr;
+    forces(q, rho, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz, Fr);
+    const T inv_rho = rcp(rho);
+    const int fi = lr * G::FZ + lc;
+    const T uz = fma(Fz, lit<T>(0.5), jz) * inv_rho, ur = fma(Fr, lit<T>(0.5), jr) * inv_rho;
+    sRho[fi] = rho;
+    sUz[fi] = uz;
+    sUr[fi] = ur;
+    if constexpr (MODE == 2) {
+      if (lr >= G::HF && lr < G::HF + BR && lc >= G::HF && lc < G::HF + BZ && k0 + lc - G::HF < Nz) {
         C* o = inter + (size_t)j * P + (k0 + lc - G::HF);
-        o[I_RHO * iplane] = rho;
-        o[I_UZ * iplane] = sUz[fi];
-        o[I_UR * iplane] = sUr[fi];
-        o[I_VZ * iplane] = (jz + tau * Fz) * inv_rho;
-        o[I_VR * iplane] = (jr + tau * Fr) * inv_rho;
-        o[I_FZ * iplane] = Fz;
-        o[I_FR * iplane] = Fr;
-        o[I_PSI * iplane] = psi;
-        o[I_SZ * iplane] = sz;
-        o[I_SR * iplane] = sr;
-        if (ax) {
-          const C* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
-          o[I_DR * iplane] = dr[0];
-          o[I_DRR * iplane] = iso_r(dr, G::DZ);
-          o[I_DZR * iplane] = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
-        } else {
-          o[I_DR * iplane] = C(0);
-          o[I_DRR * iplane] = C(0);
-          o[I_DZR * iplane] = C(0);
-        }
+        o[I_RHO * iplane] = lane(rho, 0);
+        o[I_UZ * iplane] = lane(uz, 0);
+        o[I_UR * iplane] = lane(ur, 0);
+        o[I_VZ * iplane] = lane(fma(Fz, q.tau, jz) * inv_rho, 0);
+        o[I_VR * iplane] = lane(fma(Fr, q.tau, jr) * inv_rho, 0);
+        o[I_FZ * iplane] = lane(Fz, 0);
+        o[I_FR * iplane] = lane(Fr, 0);
+        o[I_PSI * iplane] = lane(psi, 0);
+        o[I_SZ * iplane] = lane(sz, 0);
+        o[I_SR * iplane] = lane(sr, 0);
+        o[I_DR * iplane] = lane(dr0, 0);
+        o[I_DRR * iplane] = lane(Drr, 0);
+        o[I_DZR * iplane] = lane(Dzr, 0);
       }
-      if (MODE == 0 && srow && lc >= 2 && lc < G::FZ - 2) {
-        const C vz = (jz + tau * Fz) * inv_rho, vr = (jr + tau * Fr) * inv_rho;
-        C fe[9];
-        equilibrium(rho, vz, vr, fe);
-        C* out = sFs + (lr - 2) * G::SZ + (lc - 2);
+    }
+    if (MODE == 0 && srow && lc >= 2 && lc < G::FZ - 2) {
+      const T vz = fma(Fz, q.tau, jz) * inv_rho, vr = fma(Fr, q.tau, jr) * inv_rho;
+      T fe[9];
+      equilibrium(rho, vz, vr, fe);
+      T* out = sFs + (lr - 2) * G::SZ + (lc - 2);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[i * G::nS] = f[i] + (fe[i] - f[i]) * omega;
-      }
+      for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(fe[i] - f[i], q.omega, f[i]);
     }
   });
   __syncthreads();
 
-  if (READBACK) {
+  if constexpr (READBACK) {
     for_tile<BR, BZ>([&](int lr, int lc) {
       const int j = j0 + lr, k = k0 + lc;
       if (j >= Nr || k >= Nz) return;
       const int fi = (lr + G::HF) * G::FZ + (lc + G::HF);
       const size_t o = (size_t)j * Nz + k;
-      D.rho_out[o] = double(sRho[fi]);
-      D.uz_out[o] = double(sUz[fi]);
-      D.ur_out[o] = double(sUr[fi]);
+      D.rho_out[o] = double(lane(sRho[fi], 0));
+      D.uz_out[o] = double(lane(sUz[fi], 0));
+      D.ur_out[o] = double(lane(sUr[fi], 0));
     });
     return;
   }
@@ -439,126 +618,128 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     for_tile<G::FR, G::FZ>([&](int lr, int lc) {
       const int j = j0 - G::HF + lr;
       int m;
-      C sgz;
+      bool flip_z;
       if (j == -1 || j == -2) {
         m = -1 - j;
-        sgz = C(1);
+        flip_z = false;
       } else if (j == Nr || j == Nr + 1) {
         m = 2 * Nr - 1 - j;
-        sgz = D.wall == AMLBM_WALL_NOSLIP ? C(-1) : C(1);
+        flip_z = D.wall == AMLBM_WALL_NOSLIP;
       } else {
         return;
       }
       const int src = (m - (j0 - G::HF)) * G::FZ + lc;
-      sUz[lr * G::FZ + lc] = sgz * sUz[src];
+      sUz[lr * G::FZ + lc] = flip_z ? -sUz[src] : sUz[src];
       sUr[lr * G::FZ + lc] = -sUr[src];
     });
     __syncthreads();
   }
 
-  // Stage 3 (tile + 1): velocity gradients and the sources of App. A,
-  // S = -rho u_r / r, H_z, H_r with mu = rho c_s^2 (tau - 1/2), added to the
-  // collided populations (the whole h_i, or half of it for the link average).
+  // Stage 3 (tile + 1): velocity gradients and the sources of App. A, added to
+  // the collided populations (the whole h_i, or half of it for the link average).
   const bool link = D.src == AMLBM_SRC_LINK;
   for_tile<G::SR, G::SZ>([&](int lr, int lc) {
     const int j = j0 - 1 + lr;
     if (j < 0 || j >= Nr) return;
-    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
-    {
-      const int si = lr * G::SZ + lc;
-      C S_ = C(0), Hz = C(0), Hr = C(0);
-      if (ax) {
-        const int fi = (lr + 2) * G::FZ + (lc + 2);
-        const C druz = iso_r(sUz + fi, G::FZ);
-        const C dzur = iso_z(sUr + fi, G::FZ);
-        const C drur = iso_r(sUr + fi, G::FZ);
-        if (MODE == 2) {
-          if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
-            C* o = inter + (size_t)j * P + (k0 + lc - 1);
-            o[I_G1 * iplane] = druz;
-            o[I_G2 * iplane] = dzur;
-            o[I_G3 * iplane] = drur;
-          }
-          return;
-        }
-        const C rho = sRho[fi], uz = sUz[fi], ur = sUr[fi];
-        const C mu = rho * (tau - C(0.5)) * C(1.0 / 3.0);
-        S_ = -rho * ur * inv_r;
-        Hz = (mu * (druz + dzur) - rho * ur * uz) * inv_r;
-        Hr = (C(2) * mu * (drur - ur * inv_r) - rho * ur * ur) * inv_r;
-        const C hw = link ? C(0.5) : C(1);
-        C h[9];
-        sources(S_, Hz, Hr, h);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] += hw * h[i];
-      }
-      if (MODE == 2) {
-        if (!ax && lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
+    const int si = lr * G::SZ + lc;
+    T S_ = lit<T>(0.0), Hz = lit<T>(0.0), Hr = lit<T>(0.0);
+    if (ax) {
+      const T inv_r = inv_r_of(T(), j);
+      const int fi = (lr + 2) * G::FZ + (lc + 2);
+      const T druz = iso_r(sUz + fi, G::FZ);
+      const T dzur = iso_z(sUr + fi, G::FZ);
+      const T drur = iso_r(sUr + fi, G::FZ);
+      if constexpr (MODE == 2) {
+        if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
           C* o = inter + (size_t)j * P + (k0 + lc - 1);
-          o[I_G1 * iplane] = C(0);
-          o[I_G2 * iplane] = C(0);
-          o[I_G3 * iplane] = C(0);
+          o[I_G1 * iplane] = lane(druz, 0);
+          o[I_G2 * iplane] = lane(dzur, 0);
+          o[I_G3 * iplane] = lane(drur, 0);
         }
         return;
       }
-      sS[si] = S_;
-      sHz[si] = Hz;
-      sHr[si] = Hr;
+      site_sources(q, sRho[fi], sUz[fi], sUr[fi], druz, dzur, drur, inv_r, S_, Hz, Hr);
+      T h[9];
+      sources(S_, Hz, Hr, h);
+      if (link) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = fma(h[i], lit<T>(0.5), sFs[i * G::nS + si]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = sFs[i * G::nS + si] + h[i];
+      }
     }
+    if constexpr (MODE == 2) {
+      if (!ax && lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
+        C* o = inter + (size_t)j * P + (k0 + lc - 1);
+        o[I_G1 * iplane] = C(0);
+        o[I_G2 * iplane] = C(0);
+        o[I_G3 * iplane] = C(0);
+      }
+      return;
+    }
+    sS[si] = S_;
+    sHz[si] = Hz;
+    sHr[si] = Hr;
   });
-  if (MODE == 2) return;
+  if constexpr (MODE == 2) return;
   __syncthreads();
 
   // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
   // population comes from x - c_i in the same direction; rows 0 and Nr-1 apply
-  // the reflection maps (a warp covers one row, so the paths never diverge).
-  // Then psi of the new state and the shifted store.
+  // the reflection maps (rows are the same in both lanes, so the paths never
+  // diverge between lanes).  Then psi of the new state and the shifted store.
   S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
   C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
   for_tile<BR, BZ>([&](int lr, int lc) {
-    const int j = j0 + lr, k = k0 + lc;
-    if (j >= Nr || k >= Nz) return;
+    const int j = j0 + lr;
+    if (j >= Nr || k0 + lc >= Nz) return;
     const bool edge = (j == 0) || (j == Nr - 1);
-    {
-      C fn[9];
+    T fn[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
-        if (edge) {
-          if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
-            sl = lr + 1; ii = mirror_(i);
-          } else if (cr_(i) < 0 && j == Nr - 1) {  // through the outer wall
-            sl = lr + 1;
-            if (noslip) { sc = lc + 1; ii = opp_(i); }
-            else { ii = mirror_(i); }
-          }
+    for (int i = 0; i < 9; ++i) {
+      int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
+      if (edge) {
+        if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
+          sl = lr + 1; ii = mirror_(i);
+        } else if (cr_(i) < 0 && j == Nr - 1) {  // through the outer wall
+          sl = lr + 1;
+          if (noslip) { sc = lc + 1; ii = opp_(i); }
+          else { ii = mirror_(i); }
         }
-        fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
       }
-      if (link) {
-        const int di = (lr + 1) * G::SZ + (lc + 1);
-        C h[9];
-        sources(sS[di], sHz[di], sHr[di], h);
+      fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
+    }
+    if (link) {
+      const int di = (lr + 1) * G::SZ + (lc + 1);
+      T h[9];
+      sources(sS[di], sHz[di], sHr[di], h);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fn[i] += C(0.5) * h[i];
-      }
-      const C rho = moment0(fn);
-      const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
-      const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
-      store_site<S>(fout + (size_t)j * P + k, plane, fn, sb, D.rounding, (uint32_t)(j * Nz + k), step);
-      psout[(size_t)j * P + k] = psi;
+      for (int i = 0; i < 9; ++i) fn[i] = fma(h[i], lit<T>(0.5), fn[i]);
+    }
+    const T psi = psi_of(q, moment0(fn));
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int k = k0 + l * BZ + lc;
+      if (l > 0 && k >= Nz) break;
+      const C ps = lane(psi, l);
+      const C sb = shift_base(shift, ps, inv_rho0c, rho0c, rrefc);
+      C fv[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fv[i] = lane(fn[i], l);
+      store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
+      psout[(size_t)j * P + k] = ps;
     }
   });
 }
 
-
 template <class S, int BZ, int BR, int MODE>
-__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(const InstDesc* __restrict__ descs,
-                                                 const int* __restrict__ tile_inst, int toff,
-                                                 int parity, typename Store<S>::C* __restrict__ inter,
-                                                 size_t iplane) {
-  lbm_tile<S, BZ, BR, MODE>(descs, tile_inst, blockIdx.x + toff, parity, inter, iplane);
+__global__ void __launch_bounds__(NT, (MinBlocks<S, typename Store<S>::T, BZ, BR>::value)) lbm_kernel(
+    const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int toff, int parity,
+    typename Store<S>::C* __restrict__ inter, size_t iplane) {
+  lbm_tile<S, typename Store<S>::T, BZ, BR, MODE>(descs, tile_inst, blockIdx.x + toff, parity, inter,
+                                                  iplane);
 }
 
 // The timestep as a persistent grid (as many CTAs as fit on the GPU at once):
@@ -567,8 +748,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(const Inst
 // ctr[parity] counts this step's tiles; ctr[parity ^ 1], last used by the
 // previous step (which the stream has completed), is reset for the next one.
 // No CTA waits on another.  ctr[2], ctr[3] carry the step number the same way.
-template <class S, int BZ, int BR>
-__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
+// T = F2 runs the paired tiles (BZ is then the width of one lane's tile).
+template <class S, class T, int BZ, int BR>
+__global__ void __launch_bounds__(NT, (MinBlocks<S, T, BZ, BR>::value)) lbm_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
@@ -584,7 +766,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
     __syncthreads();
     const int t = s_tile;
     if (t >= ntiles) return;
-    lbm_tile<S, BZ, BR, 0>(descs, tile_inst, t, parity, nullptr, 0, step);
+    lbm_tile<S, T, BZ, BR, 0>(descs, tile_inst, t, parity, nullptr, 0, step);
     __syncthreads();
   }
 }
@@ -599,7 +781,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
 //                   tile + 1, collision, gradients and sources, gather-stream.
 // The arithmetic is the fused kernel's, operation for operation, so the two
 // schedules give bit-identical states.
-template <class C, int BZ, int BR>
+template <class T, int BZ, int BR>
 struct GeoA {
   static constexpr int HP = 4, HD = 2;
   static constexpr int PZ = BZ + 2 * HP, PR = BR + 2 * HP;
@@ -607,7 +789,7 @@ struct GeoA {
   static constexpr int EZ = BZ + 2 * HD, ER = BR;
   static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER;
   static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
-  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(nP + nD + nE);
+  static constexpr size_t bytes = int_bytes + sizeof(T) * (size_t)(nP + nD + nE);
 };
 
 template <class S, int BZ, int BR>
@@ -615,30 +797,31 @@ __global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ 
                                                    const int* __restrict__ tile_inst, int toff,
                                                    int parity) {
   using C = typename Store<S>::C;
-  using G = GeoA<C, BZ, BR>;
+  using T = typename Store<S>::T;
+  using G = GeoA<T, BZ, BR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* colmap = reinterpret_cast<int*>(smem_raw);
   int* rowmap = colmap + G::PZ;
-  C* sPsi = reinterpret_cast<C*>(smem_raw + G::int_bytes);
-  C* sDr = sPsi + G::nP;
-  C* sD1 = sDr + G::nD;
-  const Tile T = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
-  const InstDesc& D = descs[T.inst];
-  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  T* sPsi = reinterpret_cast<T*>(smem_raw + G::int_bytes);
+  T* sDr = sPsi + G::nP;
+  T* sD1 = sDr + G::nD;
+  const Tile Tl = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
+  const InstDesc& D = descs[Tl.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = Tl.k0, j0 = Tl.j0;
   const size_t plane = (size_t)P * Nr;
   const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
   const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
   C* __restrict__ uv = static_cast<C*>(D.uv);
   const bool ax = D.axisym != 0;
   const int shift = D.shift;
-  const C tau = C(D.tau), Gc = C(D.G), gz = C(D.gz), rho0 = C(D.rho0), rref = C(D.rho_ref),
-          gfac = -(Gc / C(2)) * C(1.0 / 9.0), inv_rho0 = rcp_c(rho0);
+  const Par<T> q = par_of<T>(D);
+  const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
 
   for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
   for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
   __syncthreads();
   for_tile<G::PR, G::PZ>([&](int lr, int lc) {
-    sPsi[lr * G::PZ + lc] = psin[(size_t)rowmap[lr] * P + colmap[lc]];
+    sPsi[lr * G::PZ + lc] = T{psin[(size_t)rowmap[lr] * P + colmap[lc]]};
   });
   __syncthreads();
   if (ax) {
@@ -653,49 +836,43 @@ __global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ 
   for_tile<BR, BZ>([&](int lr, int lc) {
     const int j = j0 + lr, k = k0 + lc;
     if (j >= Nr || k >= Nz) return;
-    const C r = C(j) + C(0.5), inv_r = rcp_c(r);
-    const C* p = sPsi + (lr + G::HP) * G::PZ + (lc + G::HP);
-    const C psi = p[0];
-    const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
+    const T inv_r = inv_r_of(T(), j);
+    const T* p = sPsi + (lr + G::HP) * G::PZ + (lc + G::HP);
+    const T psi = p[0];
+    const T sbt{shift_base(shift, psi.v, inv_rho0c, rho0c, rrefc)};
     const S* fp = fin + (size_t)j * P + k;
-    C f[9];
+    T f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fp[i * plane]) + C(w_(i)) * sb;
-    const C rho = moment0(f);
-    const C jz = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const C jr = (f[2] - f[4]) + ((f[5] - f[8]) + (f[6] - f[7]));
-    const int Z = G::PZ;
-    const C sz = C(1.0 / 9.0) * (p[1] - p[-1]) +
-                 C(1.0 / 36.0) * ((p[Z + 1] - p[Z - 1]) + (p[-Z + 1] - p[-Z - 1]));
-    const C sr = C(1.0 / 9.0) * (p[Z] - p[-Z]) +
-                 C(1.0 / 36.0) * ((p[Z + 1] - p[-Z + 1]) + (p[Z - 1] - p[-Z - 1]));
-    C Fz = -Gc * psi * sz, Fr = -Gc * psi * sr;
+    for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fp[i * plane])});
+    const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
+    T sz, sr;
+    sc_sums(p, G::PZ, sz, sr);
+    T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
     if (ax) {
-      const C* dr = sDr + (lr + G::HD) * G::DZ + (lc + G::HD);
-      const C Drr = iso_r(dr, G::DZ);
-      const C Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD), 1);
-      const C g = gfac * psi * inv_r;
-      Fz += g * Dzr;
-      Fr += g * (Drr - dr[0] * inv_r);
+      const T* dr = sDr + (lr + G::HD) * G::DZ + (lc + G::HD);
+      dr0 = dr[0];
+      Drr = iso_r(dr, G::DZ);
+      Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD), 1);
     }
-    Fz += rho * gz;
-    const C inv_rho = rcp_c(rho);
+    T Fz, Fr;
+    forces(q, rho, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz, Fr);
+    const T inv_rho = rcp(rho);
     C* o = uv + (size_t)j * P + k;
-    o[0] = (jz + C(0.5) * Fz) * inv_rho;
-    o[plane] = (jr + C(0.5) * Fr) * inv_rho;
-    o[2 * plane] = (jz + tau * Fz) * inv_rho;
-    o[3 * plane] = (jr + tau * Fr) * inv_rho;
+    o[0] = (fma(Fz, lit<T>(0.5), jz) * inv_rho).v;
+    o[plane] = (fma(Fr, lit<T>(0.5), jr) * inv_rho).v;
+    o[2 * plane] = (fma(Fz, q.tau, jz) * inv_rho).v;
+    o[3 * plane] = (fma(Fr, q.tau, jr) * inv_rho).v;
   });
 }
 
-template <class C, int BZ, int BR>
+template <class T, int BZ, int BR>
 struct GeoB {
   static constexpr int HF = 3;
   static constexpr int FZ = BZ + 2 * HF, FR = BR + 2 * HF;
   static constexpr int SZ = BZ + 2, SR = BR + 2;
   static constexpr int nF = FZ * FR, nS = SZ * SR;
   static constexpr int int_bytes = (FZ * 4 + 15) / 16 * 16;
-  static constexpr size_t bytes = int_bytes + sizeof(C) * (size_t)(2 * nF + 13 * nS);
+  static constexpr size_t bytes = int_bytes + sizeof(T) * (size_t)(2 * nF + 13 * nS);
 };
 
 template <class S, int BZ, int BR>
@@ -705,27 +882,28 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
   const uint32_t step = ctr ? (uint32_t)ctr[2 + parity] : 0u;
   if (ctr && blockIdx.x == 0 && threadIdx.x == 0) ctr[2 + (parity ^ 1)] = (int)(step + 1);
   using C = typename Store<S>::C;
-  using G = GeoB<C, BZ, BR>;
+  using T = typename Store<S>::T;
+  using G = GeoB<T, BZ, BR>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* colmap = reinterpret_cast<int*>(smem_raw);
-  C* sUz = reinterpret_cast<C*>(smem_raw + G::int_bytes);
-  C* sUr = sUz + G::nF;
-  C* sRho = sUr + G::nF;
-  C* sS = sRho + G::nS;
-  C* sHz = sS + G::nS;
-  C* sHr = sHz + G::nS;
-  C* sFs = sHr + G::nS;
-  const Tile T = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
-  const InstDesc& D = descs[T.inst];
-  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = T.k0, j0 = T.j0;
+  T* sUz = reinterpret_cast<T*>(smem_raw + G::int_bytes);
+  T* sUr = sUz + G::nF;
+  T* sRho = sUr + G::nF;
+  T* sS = sRho + G::nS;
+  T* sHz = sS + G::nS;
+  T* sHr = sHz + G::nS;
+  T* sFs = sHr + G::nS;
+  const Tile Tl = tile_of(descs, tile_inst, blockIdx.x + toff, BZ, BR);
+  const InstDesc& D = descs[Tl.inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = Tl.k0, j0 = Tl.j0;
   const size_t plane = (size_t)P * Nr;
   const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
   const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
   const C* __restrict__ uv = static_cast<const C*>(D.uv);
   const bool ax = D.axisym != 0;
   const int shift = D.shift;
-  const C tau = C(D.tau), omega = C(1) / tau, rho0 = C(D.rho0), rref = C(D.rho_ref),
-          inv_rho0 = rcp_c(rho0);
+  const Par<T> q = par_of<T>(D);
+  const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
 
   for (int i = threadIdx.x; i < G::FZ; i += NT) colmap[i] = wrapz(k0 - G::HF + i, Nz);
@@ -735,20 +913,20 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     for_tile<G::FR, G::FZ>([&](int lr, int lc) {
       const int j = j0 - G::HF + lr;
       int m = j;
-      C sgz = C(1), sgr = C(1);
+      bool flip_z = false, flip_r = false;
       if (j == -1 || j == -2) {
         m = -1 - j;
-        sgr = C(-1);
+        flip_r = true;
       } else if (j == Nr || j == Nr + 1) {
         m = 2 * Nr - 1 - j;
-        sgr = C(-1);
-        sgz = noslip ? C(-1) : C(1);
+        flip_r = true;
+        flip_z = noslip;
       } else if (j < 0 || j >= Nr) {
         return;  // never read
       }
       const size_t o = (size_t)m * P + colmap[lc];
-      sUz[lr * G::FZ + lc] = sgz * uv[o];
-      sUr[lr * G::FZ + lc] = sgr * uv[plane + o];
+      sUz[lr * G::FZ + lc] = T{flip_z ? -uv[o] : uv[o]};
+      sUr[lr * G::FZ + lc] = T{flip_r ? -uv[plane + o] : uv[plane + o]};
     });
   }
   // populations on the tile + 1: rho and the collision towards f^eq(rho, u^eq)
@@ -756,18 +934,18 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const int j = j0 - 1 + lr;
     if (j < 0 || j >= Nr) return;
     const size_t o = (size_t)j * P + colmap[lc + G::HF - 1];
-    const C sb = shift_base(shift, psin[o], inv_rho0, rho0, rref);
-    C f[9];
+    const T sbt{shift_base(shift, psin[o], inv_rho0c, rho0c, rrefc)};
+    T f[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = Store<S>::to(fin[i * plane + o]) + C(w_(i)) * sb;
-    const C rho = moment0(f);
-    const C vz = uv[2 * plane + o], vr = uv[3 * plane + o];
-    C fe[9];
+    for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fin[i * plane + o])});
+    const T rho = moment0(f);
+    const T vz{uv[2 * plane + o]}, vr{uv[3 * plane + o]};
+    T fe[9];
     equilibrium(rho, vz, vr, fe);
     const int si = lr * G::SZ + lc;
     sRho[si] = rho;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = f[i] + (fe[i] - f[i]) * omega;
+    for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = fma(fe[i] - f[i], q.omega, f[i]);
   });
   __syncthreads();
   // gradients and sources on the tile + 1
@@ -776,23 +954,23 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const int j = j0 - 1 + lr;
     if (j < 0 || j >= Nr) return;
     const int si = lr * G::SZ + lc;
-    C S_ = C(0), Hz = C(0), Hr = C(0);
+    T S_ = lit<T>(0.0), Hz = lit<T>(0.0), Hr = lit<T>(0.0);
     if (ax) {
-      const C r = C(j) + C(0.5), inv_r = rcp_c(r);
+      const T inv_r = inv_r_of(T(), j);
       const int fi = (lr + 2) * G::FZ + (lc + 2);
-      const C druz = iso_r(sUz + fi, G::FZ);
-      const C dzur = iso_z(sUr + fi, G::FZ);
-      const C drur = iso_r(sUr + fi, G::FZ);
-      const C rho = sRho[si], uz = sUz[fi], ur = sUr[fi];
-      const C mu = rho * (tau - C(0.5)) * C(1.0 / 3.0);
-      S_ = -rho * ur * inv_r;
-      Hz = (mu * (druz + dzur) - rho * ur * uz) * inv_r;
-      Hr = (C(2) * mu * (drur - ur * inv_r) - rho * ur * ur) * inv_r;
-      const C hw = link ? C(0.5) : C(1);
-      C h[9];
+      const T druz = iso_r(sUz + fi, G::FZ);
+      const T dzur = iso_z(sUr + fi, G::FZ);
+      const T drur = iso_r(sUr + fi, G::FZ);
+      site_sources(q, sRho[si], sUz[fi], sUr[fi], druz, dzur, drur, inv_r, S_, Hz, Hr);
+      T h[9];
       sources(S_, Hz, Hr, h);
+      if (link) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] += hw * h[i];
+        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = fma(h[i], lit<T>(0.5), sFs[i * G::nS + si]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = sFs[i * G::nS + si] + h[i];
+      }
     }
     sS[si] = S_;
     sHz[si] = Hz;
@@ -805,7 +983,7 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const int j = j0 + lr, k = k0 + lc;
     if (j >= Nr || k >= Nz) return;
     const bool edge = (j == 0) || (j == Nr - 1);
-    C fn[9];
+    T fn[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
@@ -822,38 +1000,41 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     }
     if (link) {
       const int di = (lr + 1) * G::SZ + (lc + 1);
-      C h[9];
+      T h[9];
       sources(sS[di], sHz[di], sHr[di], h);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) fn[i] += C(0.5) * h[i];
+      for (int i = 0; i < 9; ++i) fn[i] = fma(h[i], lit<T>(0.5), fn[i]);
     }
-    const C rho = moment0(fn);
-    const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
-    const C sb = shift_base(shift, psi, inv_rho0, rho0, rref);
-    store_site<S>(fout + (size_t)j * P + k, plane, fn, sb, D.rounding, (uint32_t)(j * Nz + k), step);
+    const C psi = psi_of(q, moment0(fn)).v;
+    const C sb = shift_base(shift, psi, inv_rho0c, rho0c, rrefc);
+    C fv[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fv[i] = fn[i].v;
+    store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
     psout[(size_t)j * P + k] = psi;
   });
 }
 
-// f = f^eq(rho, u) (no force shift) and psi of the new state.
 // Site n = j*Nz + k of instance D: f = f^eq(rho, u) with u^eq = u (the
 // initial state of the scheme), stored in the instance's storage form, and psi.
 template <class S>
 __device__ __forceinline__ void init_site(const InstDesc& D, int n, double rho_d, double uz_d,
                                           double ur_d, int parity) {
   using C = typename Store<S>::C;
+  using T = typename Store<S>::T;
   const int j = n / D.Nz, k = n - j * D.Nz;
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   S* f = static_cast<S*>(D.f[parity]);
   C* psi_out = static_cast<C*>(D.psi[parity]);
-  const C rho0 = C(D.rho0), rref = C(D.rho_ref);
-  C fe[9];
-  equilibrium(C(rho_d), C(uz_d), C(ur_d), fe);
-  const C rho = moment0(fe);
-  const C psi = rho0 * (C(1) - exp_c(-rho / rho0));
-  const C sb = shift_base(D.shift, psi, rcp_c(rho0), rho0, rref);
+  const Par<T> q = par_of<T>(D);
+  T fe[9];
+  equilibrium(T{C(rho_d)}, T{C(uz_d)}, T{C(ur_d)}, fe);
+  const C psi = psi_of(q, moment0(fe)).v;
+  const C sb = shift_base(D.shift, psi, kc(D, K_INVRHO0, C()), kc(D, K_RHO0, C()), kc(D, K_RREF, C()));
+  C fv[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i * plane + o] = Store<S>::from(fe[i] - C(w_(i)) * sb);
+  for (int i = 0; i < 9; ++i) fv[i] = fe[i].v;
+  store_site<S>(f + o, plane, fv, sb, 0, 0u, 0u);
   psi_out[o] = psi;
 }
 
@@ -903,23 +1084,28 @@ __global__ void unpack_kernel(const InstDesc* __restrict__ descs, int inst, int 
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   const S* f = static_cast<const S*>(D.f[parity]);
   const C psi = static_cast<const C*>(D.psi[parity])[o];
-  const C sb = shift_base(D.shift, psi, rcp_c(C(D.rho0)), C(D.rho0), C(D.rho_ref));
+  const C sb = shift_base(D.shift, psi, kc(D, K_INVRHO0, C()), kc(D, K_RHO0, C()), kc(D, K_RREF, C()));
 #pragma unroll
-  for (int i = 0; i < 9; ++i) out[(size_t)i * N + n] = double(Store<S>::to(f[i * plane + o]) + C(w_(i)) * sb);
+  for (int i = 0; i < 9; ++i)
+    out[(size_t)i * N + n] = double(fma_c(C(w_(i)), sb, Store<S>::to(f[i * plane + o])));
 }
 
-template <class S, int BZ, int BR, int MODE>
+// ------------------------------------------------------------- launchers --
+template <class S, class T, int BZ, int BR, int MODE>
 cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
                      cudaStream_t s, void* inter = nullptr, size_t iplane = 0, int* ctr = nullptr) {
   using C = typename Store<S>::C;
-  constexpr size_t smem = Geo<C, BZ, BR>::bytes;
+  constexpr size_t smem = Geo<T, BZ, BR>::bytes;
+  constexpr bool paired = Lane<T>::N == 2;
   static bool attr = false;
   static int grid_cap = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaSuccess;
+    if constexpr (!paired)
+      e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
     if (e == cudaSuccess && MODE == 0)
-      e = cudaFuncSetAttribute(lbm_persistent<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(lbm_persistent<S, T, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
     if (e != cudaSuccess) return e;
     if (MODE == 0) {
@@ -927,18 +1113,25 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
       e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm_persistent<S, BZ, BR>, NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm_persistent<S, T, BZ, BR>, NT, smem);
       if (e != cudaSuccess) return e;
       grid_cap = sms * (per_sm > 0 ? per_sm : 1);
     }
     attr = true;
   }
-  if (MODE == 0 && ctr && toff == 0) {
+  if constexpr (paired) {
+    // the paired tiles always run as the persistent grid
+    if (!ctr || toff != 0) return cudaErrorInvalidValue;
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-    lbm_persistent<S, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
+    lbm_persistent<S, T, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
   } else {
-    lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
-                                                         iplane);
+    if (MODE == 0 && ctr && toff == 0) {
+      const int grid = ntiles < grid_cap ? ntiles : grid_cap;
+      lbm_persistent<S, T, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
+    } else {
+      lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
+                                                           iplane);
+    }
   }
   return cudaGetLastError();
 }
@@ -946,8 +1139,8 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
 template <class S, int BZ, int BR>
 cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
                            cudaStream_t s, int* ctr) {
-  using C = typename Store<S>::C;
-  constexpr size_t sa = GeoA<C, BZ, BR>::bytes, sbb = GeoB<C, BZ, BR>::bytes;
+  using T = typename Store<S>::T;
+  constexpr size_t sa = GeoA<T, BZ, BR>::bytes, sbb = GeoB<T, BZ, BR>::bytes;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(force_kernel<S, BZ, BR>,
@@ -963,14 +1156,17 @@ cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int tof
   return cudaGetLastError();
 }
 
-// Tile shapes compiled for each storage form.
+// Tile shapes compiled for each storage form (for the paired schedule tz is
+// the width of the pair: two lanes of tz / 2).
 struct TileEntry { int storage, sched, tz, tr; };
 #define AMLBM_TILES_16(ST)                                                                    \
-  {ST, SCHED_FUSED, 32, 8}, {ST, SCHED_FUSED, 64, 8}, {ST, SCHED_FUSED, 58, 8},               \
-  {ST, SCHED_FUSED, 58, 16}, {ST, SCHED_FUSED, 26, 16}, {ST, SCHED_FUSED, 32, 16},            \
-  {ST, SCHED_FUSED, 122, 8}, {ST, SCHED_SPLIT, 32, 8}, {ST, SCHED_SPLIT, 64, 8},              \
-  {ST, SCHED_SPLIT, 32, 16}, {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 128, 8},            \
-  {ST, SCHED_SPLIT, 64, 4}, {ST, SCHED_FUSED, 32, 32}, {ST, SCHED_FUSED, 64, 16}
+  {ST, SCHED_FUSED, 26, 16}, {ST, SCHED_FUSED, 32, 16}, {ST, SCHED_FUSED, 64, 8},             \
+  {ST, SCHED_FUSED, 58, 8}, {ST, SCHED_FUSED, 32, 8}, {ST, SCHED_FUSED, 32, 32},              \
+  {ST, SCHED_FUSED, 64, 16}, {ST, SCHED_SPLIT, 32, 16}, {ST, SCHED_SPLIT, 64, 8},             \
+  {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 32, 8}, {ST, SCHED_PAIRED, 32, 16},            \
+  {ST, SCHED_PAIRED, 40, 16}, {ST, SCHED_PAIRED, 44, 14}, {ST, SCHED_PAIRED, 48, 12},         \
+  {ST, SCHED_PAIRED, 48, 16}, {ST, SCHED_PAIRED, 52, 8}, {ST, SCHED_PAIRED, 64, 8},           \
+  {ST, SCHED_PAIRED, 52, 16}
 constexpr TileEntry kTiles[] = {
     {AMLBM_STORE_F64, SCHED_FUSED, 32, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 64, 8},
     {AMLBM_STORE_F64, SCHED_FUSED, 58, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 26, 8},
@@ -983,6 +1179,7 @@ constexpr TileEntry kTiles[] = {
 template <class S>
 cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                      int toff, int par, cudaStream_t s, int* ctr) {
+  using T = typename Store<S>::T;
   if (nt <= 0) return cudaSuccess;
   if (sched == SCHED_SPLIT && !macro) {
 #define AMLBM_SPLIT(TZ, TR) \
@@ -992,16 +1189,30 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
     AMLBM_SPLIT(32, 16)
     if constexpr (!std::is_same<S, double>::value) {
       AMLBM_SPLIT(64, 16)
-      AMLBM_SPLIT(128, 8)
-      AMLBM_SPLIT(64, 4)
     }
 #undef AMLBM_SPLIT
     return cudaErrorInvalidValue;
   }
-#define AMLBM_TILE(TZ, TR)                                                \
-  if (tz == TZ && tr == TR)                                               \
-    return macro ? launch_t<S, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
-                 : launch_t<S, TZ, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
+  if (sched == SCHED_PAIRED && !macro) {
+    if constexpr (!std::is_same<S, double>::value) {
+#define AMLBM_PAIR(TZ, TR) \
+  if (tz == TZ && tr == TR) return launch_t<S, F2, TZ / 2, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
+      AMLBM_PAIR(32, 16)
+      AMLBM_PAIR(40, 16)
+      AMLBM_PAIR(44, 14)
+      AMLBM_PAIR(48, 12)
+      AMLBM_PAIR(48, 16)
+      AMLBM_PAIR(52, 8)
+      AMLBM_PAIR(64, 8)
+      AMLBM_PAIR(52, 16)
+#undef AMLBM_PAIR
+    }
+    return cudaErrorInvalidValue;
+  }
+#define AMLBM_TILE(TZ, TR)                                                   \
+  if (tz == TZ && tr == TR)                                                  \
+    return macro ? launch_t<S, T, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
+                 : launch_t<S, T, TZ, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
   if (macro) {  // read-back always uses a fused tile compiled for every storage
     AMLBM_TILE(32, 8)
     return cudaErrorInvalidValue;
@@ -1012,10 +1223,8 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
   if constexpr (std::is_same<S, double>::value) {
     AMLBM_TILE(26, 8)
   } else {
-    AMLBM_TILE(58, 16)
     AMLBM_TILE(26, 16)
     AMLBM_TILE(32, 16)
-    AMLBM_TILE(122, 8)
     AMLBM_TILE(32, 32)
     AMLBM_TILE(64, 16)
   }
@@ -1053,15 +1262,6 @@ int tile_list(int storage, int sched, int* tz, int* tr, int cap) {
   return n;
 }
 
-size_t step_smem_bytes(int storage, int tz, int tr) {
-  const size_t c = storage == AMLBM_STORE_F64 ? 8 : 4;
-  const int nP = (tz + 14) * (tr + 14), nD = (tz + 10) * (tr + 10), nE = (tz + 10) * (tr + 6);
-  const int nF = (tz + 6) * (tr + 6), nS = (tz + 2) * (tr + 2);
-  const int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
-  const size_t ib = ((size_t)(tz + 14 + tr + 14) * 4 + 15) / 16 * 16;
-  return ib + c * (size_t)(nA + 3 * nF + 9 * nS);
-}
-
 cudaError_t launch_step(int storage, int sched, int tz, int tr, const InstDesc* d, const int* ti,
                         int nt, int toff, int parity, cudaStream_t s, int* ctr) {
   return dispatch_storage(storage, false, sched, tz, tr, d, ti, nt, toff, parity, s, ctr);
@@ -1074,9 +1274,9 @@ cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const i
 cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                          void* inter, size_t plane, cudaStream_t s) {
   if (storage == AMLBM_STORE_F64) {
-    if (tz == 32 && tr == 8) return launch_t<double, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
+    if (tz == 32 && tr == 8) return launch_t<double, D1, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
   } else if (storage == AMLBM_STORE_F32) {
-    if (tz == 32 && tr == 8) return launch_t<float, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
+    if (tz == 32 && tr == 8) return launch_t<float, F1, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
   }
   return cudaErrorInvalidValue;
 }

@@ -90,11 +90,14 @@ def test_fp64_thread_full_size():
 
 # Max relative error in rho after 1000 steps of the static-drop workload, per
 # storage form and shift (measured values are printed; the bounds below are the
-# ones each form meets with margin).
+# ones each form meets with margin).  The 16-bit errors are random walks whose
+# maximum over the sites varies with the drop's placement: over four placements
+# BF16 measured 1.0e-2 .. 6.2e-2 rounded to nearest and 4.3e-3 .. 1.8e-2 with
+# stochastic rounding, FP16 7e-4 .. 3.4e-3 either way.
 PRECISION_CASES = [
     ("f32", "none", "nearest", 1e-4), ("f32", "local", "nearest", 1e-4),
-    ("f16", "local", "nearest", 2e-3), ("bf16", "local", "nearest", 1.5e-1),
-    ("f16", "local", "stochastic", 5e-3), ("bf16", "local", "stochastic", 1e-2),
+    ("f16", "local", "nearest", 5e-3), ("bf16", "local", "nearest", 1.5e-1),
+    ("f16", "local", "stochastic", 5e-3), ("bf16", "local", "stochastic", 3e-2),
     ("f16", "global", "nearest", 1.0), ("bf16", "global", "nearest", 1.0),
 ]
 
