@@ -245,14 +245,11 @@ typedef struct amlbm_instance {
 /* How a timestep is launched.  FUSED: one kernel per tile computes the whole
  * update, recomputing forces and velocities on a 3-site halo.  SPLIT: a force
  * kernel writes u and u^eq per site, then a collide-stream kernel reads them with
- * a halo (less recomputation, 16 or 32 more bytes per site through L2).  PAIRED
- * (FP32, FP16 and BF16 storage): the fused update of two side-by-side tiles of
- * tile_z / 2 x tile_r sites per CTA, both computed by the same packed FP32x2
- * instructions.  All schedules give bit-identical states. */
+ * a halo (less recomputation, 16 or 32 more bytes per site through L2).  Both
+ * give bit-identical states. */
 #define AMLBM_SCHED_AUTO 0
 #define AMLBM_SCHED_FUSED 1
 #define AMLBM_SCHED_SPLIT 2
-#define AMLBM_SCHED_PAIRED 3
 
 /* Schedule and tile shape (sites along z x sites along r) of the step kernels;
  * all zero lets the library choose. */

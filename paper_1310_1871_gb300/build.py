@@ -20,9 +20,9 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["amlbm_step.cu", "amlbm_abi.cu", "amlbm_diag.cu", "amlbm_noalloc.cu", "amlbm_adjoint.cu", "amlbm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-# The step kernels state every fused multiply-add explicitly; no other multiply
-# and add may be fused by the compiler, so that a site computed in one packed
-# FP32x2 lane and in a scalar lane rounds identically.
+# The step kernels state every fused multiply-add explicitly (rounding
+# intrinsics); nothing else may be fused by the compiler, so that every
+# schedule and tiling computes a site with the same operations.
 FILE_FLAGS = {"amlbm_step.cu": ["-fmad=false"]}
 
 

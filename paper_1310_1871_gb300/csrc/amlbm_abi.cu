@@ -237,7 +237,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     tz = tune->tile_z;
     tr = tune->tile_r;
     sched = tune->schedule ? tune->schedule : AMLBM_SCHED_SPLIT;
-    if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT && sched != AMLBM_SCHED_PAIRED)
+    if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT)
       return fail(AMLBM_EINVAL, "bad schedule");
     if (!tz && !tr) {
       int s2;
@@ -558,7 +558,7 @@ size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
   // room for whichever compiled tile the tune picks (the tile list grows with
   // the number of tiles)
   size_t need = 0;
-  for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_PAIRED; ++sc) {
+  for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_SPLIT; ++sc) {
     int tz[32], tr[32];
     const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, sc, tz, tr, 32));
     for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);

@@ -36,10 +36,8 @@ struct InstDesc {
 // Every launcher returns the cudaGetLastError() of its launch.
 // The step and macro kernels run CTAs for the flattened tiles
 // [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
-// (force kernel, then collide-stream kernel), 3 paired (the fused update of two
-// side-by-side tiles per CTA in packed FP32x2 arithmetic; FP32-arithmetic
-// storage forms only; tz is the width of the pair).
-enum { SCHED_FUSED = 1, SCHED_SPLIT = 2, SCHED_PAIRED = 3 };
+// (force kernel, then collide-stream kernel).
+enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
 // ctr (four ints, zero at creation): tile counters of the persistent fused
 // grid and the step numbers for stochastic rounding, one per parity; nullptr
 // launches one CTA per tile.

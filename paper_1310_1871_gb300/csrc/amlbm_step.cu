@@ -13,14 +13,11 @@
 // 9 written, psi written once and read once (halo re-reads hit L2).
 // No tensor cores: the update is a stencil, not a contraction.
 //
-// The arithmetic is written once on "lane" types: F1 (one site in FP32), D1
-// (one site in FP64) and F2 (two sites in FP32, in the packed FP32x2
-// instructions of sm_100 and later: one FFMA2 / FADD2 / FMUL2 serves both).
-// The paired schedule gives each CTA two z-adjacent tiles of the same rows, one
-// per lane, so every stencil and every physics step is one packed instruction
-// for two sites.  Each operation is an explicitly rounded intrinsic (nothing is
-// left to the compiler's contraction), so a site gets the same bits from an F2
-// lane as from an F1 lane, in whichever kernel it is computed.
+// The arithmetic is written once on "lane" types, F1 (FP32) and D1 (FP64),
+// whose every operation is an explicitly rounded intrinsic: each fused
+// multiply-add is written out and nothing else is left to the compiler's
+// contraction, so every schedule and tiling computes a site with the same
+// operations and gets the same bits.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -56,7 +53,6 @@ __host__ __device__ constexpr int opp_(int i) {
 // ---------------------------------------------------------------- lanes --
 struct F1 { float v; };
 struct D1 { double v; };
-struct __align__(8) F2 { float2 v; };
 
 __device__ __forceinline__ F1 operator+(F1 a, F1 b) { return {__fadd_rn(a.v, b.v)}; }
 __device__ __forceinline__ F1 operator-(F1 a, F1 b) { return {__fsub_rn(a.v, b.v)}; }
@@ -70,41 +66,21 @@ __device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {__dmul_rn(a.v, b.v
 __device__ __forceinline__ D1 operator-(D1 a) { return {-a.v}; }
 __device__ __forceinline__ D1 fma(D1 a, D1 b, D1 c) { return {__fma_rn(a.v, b.v, c.v)}; }
 
-// a - b is a + (-b) exactly, so FADD2 with a negated operand rounds as FSUB.
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 operator-(F2 a) { return {make_float2(-a.v.x, -a.v.y)}; }
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__fadd2_rn(a.v, (-b).v)}; }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
-
 template <class T> struct Lane;
 template <> struct Lane<F1> { using C = float; static constexpr int N = 1; };
 template <> struct Lane<D1> { using C = double; static constexpr int N = 1; };
-template <> struct Lane<F2> { using C = float; static constexpr int N = 2; };
 
 template <class T> __device__ __forceinline__ T lit(double c);
 template <> __device__ __forceinline__ F1 lit<F1>(double c) { return {float(c)}; }
 template <> __device__ __forceinline__ D1 lit<D1>(double c) { return {c}; }
-template <> __device__ __forceinline__ F2 lit<F2>(double c) { return {make_float2(float(c), float(c))}; }
 
-__device__ __forceinline__ float lane(F1 a, int) { return a.v; }
-__device__ __forceinline__ double lane(D1 a, int) { return a.v; }
-__device__ __forceinline__ float lane(F2 a, int l) { return l ? a.v.y : a.v.x; }
-
-template <class T> __device__ __forceinline__ T pack(const typename Lane<T>::C* c);
-template <> __device__ __forceinline__ F1 pack<F1>(const float* c) { return {c[0]}; }
-template <> __device__ __forceinline__ D1 pack<D1>(const double* c) { return {c[0]}; }
-template <> __device__ __forceinline__ F2 pack<F2>(const float* c) { return {make_float2(c[0], c[1])}; }
-
-// Reciprocal and exponential, per lane.  FP32 uses the correctly rounded
+// Reciprocal and exponential.  FP32 uses the correctly rounded
 // reciprocal and the SFU exponential (relative error ~1e-7, far below the
 // storage rounding); FP64 the correctly rounded reciprocal and exp.
 __device__ __forceinline__ F1 rcp(F1 a) { return {__frcp_rn(a.v)}; }
 __device__ __forceinline__ D1 rcp(D1 a) { return {__drcp_rn(a.v)}; }
-__device__ __forceinline__ F2 rcp(F2 a) { return {make_float2(__frcp_rn(a.v.x), __frcp_rn(a.v.y))}; }
 __device__ __forceinline__ F1 expl(F1 a) { return {__expf(a.v)}; }
 __device__ __forceinline__ D1 expl(D1 a) { return {exp(a.v)}; }
-__device__ __forceinline__ F2 expl(F2 a) { return {make_float2(__expf(a.v.x), __expf(a.v.y))}; }
 
 // ------------------------------------------------------------- storage --
 // Storage codecs: conversion between the stored element and the arithmetic
@@ -326,7 +302,6 @@ template <class T>
 __device__ __forceinline__ T splat(typename Lane<T>::C c);
 template <> __device__ __forceinline__ F1 splat<F1>(float c) { return {c}; }
 template <> __device__ __forceinline__ D1 splat<D1>(double c) { return {c}; }
-template <> __device__ __forceinline__ F2 splat<F2>(float c) { return {make_float2(c, c)}; }
 // q.gfac = -(G / 2) c_s^4 with c_s^4 = 1/9; q.cmu = mu / rho = c_s^2 (tau - 1/2)
 template <class T>
 __device__ __forceinline__ Par<T> par_of(const InstDesc& D) {
@@ -344,10 +319,6 @@ __device__ __forceinline__ Par<T> par_of(const InstDesc& D) {
 }
 // 1 / r of row j, r = j + 1/2 (exact in either precision)
 __device__ __forceinline__ F1 inv_r_of(F1, int j) { return rcp(F1{__int2float_rn(j) + 0.5f}); }
-__device__ __forceinline__ F2 inv_r_of(F2, int j) {
-  const float r = __frcp_rn(__int2float_rn(j) + 0.5f);
-  return {make_float2(r, r)};
-}
 __device__ __forceinline__ D1 inv_r_of(D1, int j) { return rcp(D1{__int2double_rn(j) + 0.5}); }
 
 // Total force on a site (Eq. scforce, Eq. scAxisExtra, body force rho g_z).
@@ -408,12 +379,11 @@ __device__ __forceinline__ void for_tile(F&& body) {
   }
 }
 
-// Tile geometry of one lane (BZ x BR sites).  Halos: psi 7, isotropic d_r psi
-// 5, 1D d_r psi (z 5, r 3), rho and u 3, collided populations and sources 1.
-// The integer maps hold the wrapped column of every lane and the mirrored row.
+// Tile geometry (BZ x BR sites).  Halos: psi 7, isotropic d_r psi 5, 1D d_r
+// psi (z 5, r 3), rho and u 3, collided populations and sources 1.  The
+// integer maps hold the wrapped column and the mirrored row of the psi region.
 template <class T, int BZ, int BR>
 struct Geo {
-  static constexpr int NL = Lane<T>::N;
   static constexpr int HP = 7, HD = 5, HF = 3;
   static constexpr int PZ = BZ + 2 * HP, PR = BR + 2 * HP;
   static constexpr int DZ = BZ + 2 * HD, DR = BR + 2 * HD;
@@ -423,7 +393,7 @@ struct Geo {
   static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER, nF = FZ * FR, nS = SZ * SR;
   // region A holds psi and its derivatives, later the sources S, H_z, H_r
   static constexpr int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
-  static constexpr int int_bytes = ((NL * PZ + PR) * 4 + 15) / 16 * 16;
+  static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
   static constexpr size_t bytes = int_bytes + sizeof(T) * (size_t)(nA + 3 * nF + 9 * nS);
 };
 
@@ -443,25 +413,15 @@ __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_i
   return t;
 }
 
-// Resident CTAs per SM the register allocation must allow: five for the scalar
-// FP32 arithmetic forms (their tiles use at most ~40 KB of shared memory); for
-// the paired tiles as many as their shared memory lets fit in the 228 KB of an
-// SM (1 KB of it reserved per CTA), at most four (64 registers a thread).
-template <class S, class T, int BZ, int BR>
-struct MinBlocks {
-  static constexpr int fit = int((228u * 1024u) / (Geo<T, BZ, BR>::bytes + 1024u));
-  static constexpr int value = std::is_same<S, double>::value
-                                   ? 1
-                                   : (Lane<T>::N == 2 ? (fit > 4 ? 4 : (fit < 1 ? 1 : fit)) : 5);
-};
+// Resident CTAs per SM the register allocation must allow: five for the FP32
+// arithmetic forms (their tiles use at most ~40 KB of shared memory).
+template <class S>
+struct MinBlocks { static constexpr int value = std::is_same<S, double>::value ? 1 : 5; };
 
-// The fused update of one tile, in lanes of type T: with F1 / D1 the tile is
-// BZ x BR sites; with F2 it is two side-by-side BZ x BR tiles (sites k0 + lc
-// in lane 0 and k0 + BZ + lc in lane 1, the same rows), i.e. a 2 BZ x BR tile
-// of the batch's tiling.  MODE 0: the timestep; MODE 1 (read-back, one lane
-// only): rho and u of the tile; MODE 2 (one lane only): the forward
-// intermediates of the tile for the adjoint (into `inter`, I_COUNT planes of
-// `iplane` elements).
+// The fused update of one BZ x BR tile in the lane type T of the storage form.
+// MODE 0: the timestep; MODE 1 (read-back): only rho and u of the tile; MODE 2:
+// the forward intermediates of the tile for the adjoint (into `inter`, I_COUNT
+// planes of `iplane` elements).
 template <class S, class T, int BZ, int BR, int MODE>
 __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
                                          const int* __restrict__ tile_inst, int tile, int parity,
@@ -470,11 +430,9 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   constexpr bool READBACK = MODE == 1;
   using C = typename Store<S>::C;
   using G = Geo<T, BZ, BR>;
-  constexpr int NL = G::NL;
-  static_assert(NL == 1 || MODE == 0, "paired lanes run the timestep only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* colmap = reinterpret_cast<int*>(smem_raw);  // [NL][PZ]
-  int* rowmap = colmap + NL * G::PZ;
+  int* colmap = reinterpret_cast<int*>(smem_raw);
+  int* rowmap = colmap + G::PZ;
   T* base = reinterpret_cast<T*>(smem_raw + G::int_bytes);
   T* sPsi = base;
   T* sDr = sPsi + G::nP;
@@ -487,7 +445,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   T* sUr = sUz + G::nF;
   T* sFs = sUr + G::nF;
 
-  const Tile Tl = tile_of(descs, tile_inst, tile, NL * BZ, BR, READBACK);
+  const Tile Tl = tile_of(descs, tile_inst, tile, BZ, BR, READBACK);
   const InstDesc& D = descs[Tl.inst];
   const int Nz = D.Nz, Nr = D.Nr, P = D.P, k0 = Tl.k0, j0 = Tl.j0;
   const size_t plane = (size_t)P * Nr;
@@ -498,20 +456,13 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   const Par<T> q = par_of<T>(D);
   const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
 
-  for (int i = threadIdx.x; i < NL * G::PZ; i += NT) {
-    const int l = i / G::PZ, c = i - l * G::PZ;
-    colmap[i] = wrapz(k0 + l * BZ - G::HP + c, Nz);
-  }
+  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
   for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
   __syncthreads();
 
   // Stage 0: psi with ghost cells (periodic z, even mirror in r).
   for_tile<G::PR, G::PZ>([&](int lr, int lc) {
-    const C* row = psin + (size_t)rowmap[lr] * P;
-    C v[NL];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) v[l] = row[colmap[l * G::PZ + lc]];
-    sPsi[lr * G::PZ + lc] = pack<T>(v);
+    sPsi[lr * G::PZ + lc] = T{psin[(size_t)rowmap[lr] * P + colmap[lc]]};
   });
   __syncthreads();
 
@@ -538,18 +489,10 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     const T psi = p[0];
     T f[9];
     {
-      C sb[NL], fl[NL];
-      const S* frow = fin + (size_t)j * P;
+      const T sbt{shift_base(shift, psi.v, inv_rho0c, rho0c, rrefc)};
+      const S* fp = fin + (size_t)j * P + colmap[lc + G::HP - G::HF];
 #pragma unroll
-      for (int l = 0; l < NL; ++l) sb[l] = shift_base(shift, lane(psi, l), inv_rho0c, rho0c, rrefc);
-      const T sbt = pack<T>(sb);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-#pragma unroll
-        for (int l = 0; l < NL; ++l)
-          fl[l] = Store<S>::to(frow[i * plane + colmap[l * G::PZ + lc + G::HP - G::HF]]);
-        f[i] = fma(lit<T>(w_(i)), sbt, pack<T>(fl));
-      }
+      for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fp[i * plane])});
     }
     const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
     T sz, sr;
@@ -572,19 +515,19 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     if constexpr (MODE == 2) {
       if (lr >= G::HF && lr < G::HF + BR && lc >= G::HF && lc < G::HF + BZ && k0 + lc - G::HF < Nz) {
         C* o = inter + (size_t)j * P + (k0 + lc - G::HF);
-        o[I_RHO * iplane] = lane(rho, 0);
-        o[I_UZ * iplane] = lane(uz, 0);
-        o[I_UR * iplane] = lane(ur, 0);
-        o[I_VZ * iplane] = lane(fma(Fz, q.tau, jz) * inv_rho, 0);
-        o[I_VR * iplane] = lane(fma(Fr, q.tau, jr) * inv_rho, 0);
-        o[I_FZ * iplane] = lane(Fz, 0);
-        o[I_FR * iplane] = lane(Fr, 0);
-        o[I_PSI * iplane] = lane(psi, 0);
-        o[I_SZ * iplane] = lane(sz, 0);
-        o[I_SR * iplane] = lane(sr, 0);
-        o[I_DR * iplane] = lane(dr0, 0);
-        o[I_DRR * iplane] = lane(Drr, 0);
-        o[I_DZR * iplane] = lane(Dzr, 0);
+        o[I_RHO * iplane] = (rho).v;
+        o[I_UZ * iplane] = (uz).v;
+        o[I_UR * iplane] = (ur).v;
+        o[I_VZ * iplane] = (fma(Fz, q.tau, jz) * inv_rho).v;
+        o[I_VR * iplane] = (fma(Fr, q.tau, jr) * inv_rho).v;
+        o[I_FZ * iplane] = (Fz).v;
+        o[I_FR * iplane] = (Fr).v;
+        o[I_PSI * iplane] = (psi).v;
+        o[I_SZ * iplane] = (sz).v;
+        o[I_SR * iplane] = (sr).v;
+        o[I_DR * iplane] = (dr0).v;
+        o[I_DRR * iplane] = (Drr).v;
+        o[I_DZR * iplane] = (Dzr).v;
       }
     }
     if (MODE == 0 && srow && lc >= 2 && lc < G::FZ - 2) {
@@ -604,9 +547,9 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       if (j >= Nr || k >= Nz) return;
       const int fi = (lr + G::HF) * G::FZ + (lc + G::HF);
       const size_t o = (size_t)j * Nz + k;
-      D.rho_out[o] = double(lane(sRho[fi], 0));
-      D.uz_out[o] = double(lane(sUz[fi], 0));
-      D.ur_out[o] = double(lane(sUr[fi], 0));
+      D.rho_out[o] = double((sRho[fi]).v);
+      D.uz_out[o] = double((sUz[fi]).v);
+      D.ur_out[o] = double((sUr[fi]).v);
     });
     return;
   }
@@ -652,9 +595,9 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       if constexpr (MODE == 2) {
         if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
           C* o = inter + (size_t)j * P + (k0 + lc - 1);
-          o[I_G1 * iplane] = lane(druz, 0);
-          o[I_G2 * iplane] = lane(dzur, 0);
-          o[I_G3 * iplane] = lane(drur, 0);
+          o[I_G1 * iplane] = (druz).v;
+          o[I_G2 * iplane] = (dzur).v;
+          o[I_G3 * iplane] = (drur).v;
         }
         return;
       }
@@ -687,14 +630,14 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
 
   // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
   // population comes from x - c_i in the same direction; rows 0 and Nr-1 apply
-  // the reflection maps (rows are the same in both lanes, so the paths never
-  // diverge between lanes).  Then psi of the new state and the shifted store.
+  // the reflection maps (a warp covers one row, so the paths never diverge).
+  // Then psi of the new state and the shifted store.
   S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
   C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
   for_tile<BR, BZ>([&](int lr, int lc) {
-    const int j = j0 + lr;
-    if (j >= Nr || k0 + lc >= Nz) return;
+    const int j = j0 + lr, k = k0 + lc;
+    if (j >= Nr || k >= Nz) return;
     const bool edge = (j == 0) || (j == Nr - 1);
     T fn[9];
 #pragma unroll
@@ -718,24 +661,18 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
 #pragma unroll
       for (int i = 0; i < 9; ++i) fn[i] = fma(h[i], lit<T>(0.5), fn[i]);
     }
-    const T psi = psi_of(q, moment0(fn));
+    const C ps = psi_of(q, moment0(fn)).v;
+    const C sb = shift_base(shift, ps, inv_rho0c, rho0c, rrefc);
+    C fv[9];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      const int k = k0 + l * BZ + lc;
-      if (l > 0 && k >= Nz) break;
-      const C ps = lane(psi, l);
-      const C sb = shift_base(shift, ps, inv_rho0c, rho0c, rrefc);
-      C fv[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fv[i] = lane(fn[i], l);
-      store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
-      psout[(size_t)j * P + k] = ps;
-    }
+    for (int i = 0; i < 9; ++i) fv[i] = fn[i].v;
+    store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
+    psout[(size_t)j * P + k] = ps;
   });
 }
 
 template <class S, int BZ, int BR, int MODE>
-__global__ void __launch_bounds__(NT, (MinBlocks<S, typename Store<S>::T, BZ, BR>::value)) lbm_kernel(
+__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int toff, int parity,
     typename Store<S>::C* __restrict__ inter, size_t iplane) {
   lbm_tile<S, typename Store<S>::T, BZ, BR, MODE>(descs, tile_inst, blockIdx.x + toff, parity, inter,
@@ -748,9 +685,8 @@ __global__ void __launch_bounds__(NT, (MinBlocks<S, typename Store<S>::T, BZ, BR
 // ctr[parity] counts this step's tiles; ctr[parity ^ 1], last used by the
 // previous step (which the stream has completed), is reset for the next one.
 // No CTA waits on another.  ctr[2], ctr[3] carry the step number the same way.
-// T = F2 runs the paired tiles (BZ is then the width of one lane's tile).
 template <class S, class T, int BZ, int BR>
-__global__ void __launch_bounds__(NT, (MinBlocks<S, T, BZ, BR>::value)) lbm_persistent(
+__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
@@ -1096,14 +1032,11 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
                      cudaStream_t s, void* inter = nullptr, size_t iplane = 0, int* ctr = nullptr) {
   using C = typename Store<S>::C;
   constexpr size_t smem = Geo<T, BZ, BR>::bytes;
-  constexpr bool paired = Lane<T>::N == 2;
   static bool attr = false;
   static int grid_cap = 0;
   if (!attr) {
-    cudaError_t e = cudaSuccess;
-    if constexpr (!paired)
-      e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && MODE == 0)
       e = cudaFuncSetAttribute(lbm_persistent<S, T, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
@@ -1119,19 +1052,11 @@ cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int
     }
     attr = true;
   }
-  if constexpr (paired) {
-    // the paired tiles always run as the persistent grid
-    if (!ctr || toff != 0) return cudaErrorInvalidValue;
+  if (MODE == 0 && ctr && toff == 0) {
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
     lbm_persistent<S, T, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
   } else {
-    if (MODE == 0 && ctr && toff == 0) {
-      const int grid = ntiles < grid_cap ? ntiles : grid_cap;
-      lbm_persistent<S, T, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
-    } else {
-      lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter),
-                                                           iplane);
-    }
+    lbm_kernel<S, BZ, BR, MODE><<<ntiles, NT, smem, s>>>(d, ti, toff, parity, static_cast<C*>(inter), iplane);
   }
   return cudaGetLastError();
 }
@@ -1156,17 +1081,13 @@ cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int tof
   return cudaGetLastError();
 }
 
-// Tile shapes compiled for each storage form (for the paired schedule tz is
-// the width of the pair: two lanes of tz / 2).
+// Tile shapes compiled for each storage form.
 struct TileEntry { int storage, sched, tz, tr; };
 #define AMLBM_TILES_16(ST)                                                                    \
   {ST, SCHED_FUSED, 26, 16}, {ST, SCHED_FUSED, 32, 16}, {ST, SCHED_FUSED, 64, 8},             \
   {ST, SCHED_FUSED, 58, 8}, {ST, SCHED_FUSED, 32, 8}, {ST, SCHED_FUSED, 32, 32},              \
   {ST, SCHED_FUSED, 64, 16}, {ST, SCHED_SPLIT, 32, 16}, {ST, SCHED_SPLIT, 64, 8},             \
-  {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 32, 8}, {ST, SCHED_PAIRED, 32, 16},            \
-  {ST, SCHED_PAIRED, 40, 16}, {ST, SCHED_PAIRED, 44, 14}, {ST, SCHED_PAIRED, 48, 12},         \
-  {ST, SCHED_PAIRED, 48, 16}, {ST, SCHED_PAIRED, 52, 8}, {ST, SCHED_PAIRED, 64, 8},           \
-  {ST, SCHED_PAIRED, 52, 16}
+  {ST, SCHED_SPLIT, 64, 16}, {ST, SCHED_SPLIT, 32, 8}
 constexpr TileEntry kTiles[] = {
     {AMLBM_STORE_F64, SCHED_FUSED, 32, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 64, 8},
     {AMLBM_STORE_F64, SCHED_FUSED, 58, 8}, {AMLBM_STORE_F64, SCHED_FUSED, 26, 8},
@@ -1191,22 +1112,6 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
       AMLBM_SPLIT(64, 16)
     }
 #undef AMLBM_SPLIT
-    return cudaErrorInvalidValue;
-  }
-  if (sched == SCHED_PAIRED && !macro) {
-    if constexpr (!std::is_same<S, double>::value) {
-#define AMLBM_PAIR(TZ, TR) \
-  if (tz == TZ && tr == TR) return launch_t<S, F2, TZ / 2, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
-      AMLBM_PAIR(32, 16)
-      AMLBM_PAIR(40, 16)
-      AMLBM_PAIR(44, 14)
-      AMLBM_PAIR(48, 12)
-      AMLBM_PAIR(48, 16)
-      AMLBM_PAIR(52, 8)
-      AMLBM_PAIR(64, 8)
-      AMLBM_PAIR(52, 16)
-#undef AMLBM_PAIR
-    }
     return cudaErrorInvalidValue;
   }
 #define AMLBM_TILE(TZ, TR)                                                   \

@@ -61,7 +61,7 @@ extern "C" int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void
 
   int timed = 0;
   double best_ms = 1e300;
-  for (int sched = AMLBM_SCHED_FUSED; sched <= AMLBM_SCHED_PAIRED; ++sched) {
+  for (int sched = AMLBM_SCHED_FUSED; sched <= AMLBM_SCHED_SPLIT; ++sched) {
     int tz[64], tr[64];
     const int nt = std::min(64, amlbm_tiles(storage, sched, tz, tr, 64));
     for (int c = 0; c < nt; ++c) {

@@ -23,7 +23,7 @@ def sweep(n=6):
 def test_autotune_times_every_candidate(storage):
     _, specs = sweep()
     sched, tile, cands = amlbm.autotune_raw(specs, storage, steps=5)
-    n_expected = sum(len(amlbm.tiles(storage, s)) for s in ("fused", "split", "paired"))
+    n_expected = len(amlbm.tiles(storage, "fused")) + len(amlbm.tiles(storage, "split"))
     assert len(cands) == n_expected
     assert all(c["ms_per_step"] > 0 for c in cands)
     fastest = min(cands, key=lambda c: c["ms_per_step"])
@@ -69,7 +69,7 @@ def test_every_compiled_tile_gives_the_same_state(storage):
 
     ref = run("fused", (32, 8))
     bad = []
-    for sched in ("fused", "split", "paired"):
+    for sched in ("fused", "split"):
         for tile in amlbm.tiles(storage, sched):
             got = run(sched, tile)
             if not all(np.array_equal(a, c) for a, c in zip(ref, got)):
