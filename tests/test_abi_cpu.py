@@ -63,7 +63,8 @@ def test_bad_flags_and_tiles_rejected(lib):
 
 def test_tile_lists_and_workspace_sizes(lib):
     assert (32, 8) in amlbm.tiles("f64") and (128, 8) not in amlbm.tiles("f64")
-    assert (122, 8) in amlbm.tiles("bf16") and (26, 16) in amlbm.tiles("f32")
+    assert (58, 8) in amlbm.tiles("bf16") and (26, 16) in amlbm.tiles("f32")
+    assert (26, 16) not in amlbm.tiles("f64") and (64, 16) in amlbm.tiles("bf16", "split")
     small = lib.amlbm_workspace_bytes(64, 32, 0)
     big = lib.amlbm_workspace_bytes(256, 128, 0)
     half = lib.amlbm_workspace_bytes(256, 128, 3)
