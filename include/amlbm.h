@@ -202,7 +202,8 @@ int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm
  * phi = (rho - rho_v)/(rho_l - rho_v). */
 typedef struct amlbm_adjoint_problem {
   int T;           /* timesteps (>= 1) */
-  int ckpt_every;  /* steps between stored states (>= 1); memory ~ (T/ckpt + ckpt) states */
+  int ckpt_every;  /* steps between stored states (>= 1); device memory ~ T/ckpt_every
+                      states + ckpt_every states and their intermediates (26 planes each) */
   int objective;   /* AMLBM_OBJ_* */
   int l0;          /* Legendre degree of amps[0] */
   int n_amps;      /* 0..32 */
@@ -215,10 +216,11 @@ typedef struct amlbm_adjoint_problem {
 /* Device bytes amlbm_adjoint needs for this context and problem (0 if invalid). */
 size_t amlbm_adjoint_workspace_bytes(amlbm_ctx* ctx, const amlbm_adjoint_problem* p);
 
-/* Hand-written discrete adjoint of the run above (SURVEY-named form (3); the paper
- * differentiates nothing): J and dJ/dG, dJ/dtau, dJ/d(amps) (n_amps values).
+/* Hand-written discrete adjoint of the run above (the paper differentiates
+ * nothing): J and dJ/dG, dJ/dtau, dJ/d(amps) (n_amps values).
  * The forward run stores the state every ckpt_every steps; the backward sweep
- * recomputes each segment and applies the transposed step (inverse streaming,
+ * recomputes each segment (keeping every state of it and the forward
+ * intermediates of each) and applies the transposed step (inverse streaming,
  * adjoint collision and sources, transposed gradient and force stencils with the
  * mirror ghosts folded back) from the last step to the first.  Parameter
  * gradients accumulate in FP64.  Needs FP64 or FP32 storage without shift and the

@@ -3,15 +3,17 @@
 // Legendre shape amplitudes to the initial drop, the objectives, and the
 // checkpointed driver behind amlbm_adjoint / amlbm_objective.
 //
-// One adjoint step (lambda^{n+1} -> lambda^n, state f^n) runs as:
-//   inter  : forward intermediates of f^n (lbm_kernel MODE 2)
+// The forward intermediates of every state of a checkpoint segment are written
+// while the segment is recomputed (lbm_kernel MODE 3: the step and the
+// intermediates of the state it starts from in one pass).  One adjoint step
+// (lambda^{n+1} -> lambda^n, state f^n) then runs as:
 //   post   : mu = transpose of the streaming map (a gather), then the adjoint of
 //            the BGK collision and of the sources S, H_z, H_r  -> rho, u, u^eq,
 //            velocity-gradient adjoints, tau part
-//   vel    : transposed gradient stencils with the u ghosts folded back, then the
-//            adjoint of u = (j + F/2)/rho and u^eq = (j + tau F)/rho
-//   force  : adjoint of F_SC (Eq. scforce) and F^gamma (Eq. scAxisExtra) at the
-//            site (local psi factor, d_zr, d_rr, d_r parts), G part
+//   vel    : transposed gradient stencils with the u ghosts folded back, the
+//            adjoint of u = (j + F/2)/rho and u^eq = (j + tau F)/rho, and at the
+//            same site the adjoint of F_SC (Eq. scforce) and F^gamma (Eq.
+//            scAxisExtra) (local psi factor, d_zr, d_rr, d_r parts), G part
 //   deriv  : transposed 1D d_z (of d_zr) and isotropic d_r (of d_rr)
 //   final  : transposed Shan-Chen neighbour sum, 1D d_r and isotropic d_r on psi,
 //            psi ghosts folded onto their mirrors, d psi/d rho, and
@@ -49,16 +51,20 @@ __host__ __device__ constexpr int aopp(int i) {
        : i == 5 ? 7 : i == 7 ? 5 : i == 6 ? 8 : 6;
 }
 
+// Periodic wrap of a column that lies a few sites outside [0, Nz) (no
+// division: stencil offsets are at most 4, so one or two corrections suffice
+// unless Nz is smaller than that).
 __device__ __forceinline__ int wz(int k, int Nz) {
-  k %= Nz;
-  return k < 0 ? k + Nz : k;
+  while (k < 0) k += Nz;
+  while (k >= Nz) k -= Nz;
+  return k;
 }
 
 template <class C>
 struct Adj {
   int Nz, Nr, P, wall, axisym;
   size_t plane;
-  C tau, omega, G, rho0, gz;
+  C tau, omega, G, rho0, gz, inv_rho0;
   const C* lam_in;
   C* lam_out;
   const C* f;      // state f^n, 9 planes
@@ -131,12 +137,13 @@ __global__ void adj_post(Adj<C> A) {
   const C rho = I[I_RHO * A.plane], vz = I[I_VZ * A.plane], vr = I[I_VR * A.plane];
   const C uz = I[I_UZ * A.plane], ur = I[I_UR * A.plane];
   C rb = C(0), vzb = C(0), vrb = C(0), tb = C(0);
+  const C irho = C(1) / rho;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     const C fe = feq_std(q, rho, vz, vr);
     const C cv = C(acz(q)) * vz + C(acr(q)) * vr;
     const C m = A.omega * mu[q];
-    rb += m * fe / rho;
+    rb += m * fe * irho;
     const C com = m * C(aw(q)) * rho;
     vzb += com * (C(3) * C(acz(q)) + C(9) * cv * C(acz(q)) - C(3) * vz);
     vrb += com * (C(3) * C(acr(q)) + C(9) * cv * C(acr(q)) - C(3) * vr);
@@ -153,7 +160,8 @@ __global__ void adj_post(Adj<C> A) {
     }
     const C r = C(j) + C(0.5), ir = C(1) / r;
     const C g1 = I[I_G1 * A.plane], g2 = I[I_G2 * A.plane], g3 = I[I_G3 * A.plane];
-    const C muv = rho * (A.tau - C(0.5)) / C(3);
+    const C cmu = (A.tau - C(0.5)) * C(1.0 / 3.0);
+    const C muv = rho * cmu;
     // S = -rho u_r / r
     rb += -Sb * ur * ir;
     urb += -Sb * rho * ir;
@@ -170,8 +178,8 @@ __global__ void adj_post(Adj<C> A) {
     urb += Hrb * (-C(2) * muv * ir - C(2) * rho * ur) * ir;
     rb += -Hrb * ur * ur * ir;
     // mu = rho (tau - 1/2) / 3
-    rb += mvb * (A.tau - C(0.5)) / C(3);
-    tb += mvb * rho / C(3);
+    rb += mvb * cmu;
+    tb += mvb * rho * C(1.0 / 3.0);
   }
   A.rhob[o] = rb;
   A.uzb[o] = uzb;
@@ -184,7 +192,8 @@ __global__ void adj_post(Adj<C> A) {
   A.accT[o] += double(tb);
 }
 
-// ---- vel: transposed gradient stencils (u ghosts folded), adjoint of u and u^eq
+// ---- vel: transposed gradient stencils (u ghosts folded), adjoint of u and u^eq;
+// then (same site, no neighbours) the local adjoint of F_SC and F^gamma
 template <class C>
 __global__ void adj_vel(Adj<C> A) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -220,42 +229,33 @@ __global__ void adj_vel(Adj<C> A) {
   A.Fzb[o] = Fzb;
   A.Frb[o] = Frb;
   A.rhob[o] += -(uzb * uz + urb * ur + vzb * vz + vrb * vr) * ir + Fzb * A.gz;
-  A.accT[o] += double((vzb * Fz + vrb * Fr) * ir);
-}
-
-// ---- force: local adjoint of F_SC and F^gamma
-template <class C>
-__global__ void adj_force(Adj<C> A) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= A.Nz * A.Nr) return;
-  const int j = n / A.Nz, k = n - j * A.Nz;
-  const size_t o = (size_t)j * A.P + k;
-  const C* I = A.inter + o;
-  const C psi = I[I_PSI * A.plane], sz = I[I_SZ * A.plane], sr = I[I_SR * A.plane];
-  const C Fzb = A.Fzb[o], Frb = A.Frb[o];
+  double tacc = double((vzb * Fz + vrb * Fr) * ir);
   // F_SC = -G psi s
+  const C psi = I[I_PSI * A.plane], sz = I[I_SZ * A.plane], sr = I[I_SR * A.plane];
   C pb = -A.G * (Fzb * sz + Frb * sr);
   double gb = double(-psi * (Fzb * sz + Frb * sr));
   A.qz[o] = -A.G * psi * Fzb;
   A.qr[o] = -A.G * psi * Frb;
   C dzrb = C(0), drrb = C(0), drdb = C(0);
   if (A.axisym) {
-    const C r = C(j) + C(0.5), ir = C(1) / r;
+    const C irr = C(1) / (C(j) + C(0.5));
     const C Dr = I[I_DR * A.plane], Drr = I[I_DRR * A.plane], Dzr = I[I_DZR * A.plane];
-    const C gf = -A.G / C(18);
-    const C t = Fzb * Dzr * ir + Frb * (Drr * ir - Dr * ir * ir);
+    const C gf = -A.G * C(1.0 / 18.0);
+    const C t = Fzb * Dzr * irr + Frb * (Drr * irr - Dr * irr * irr);
     pb += gf * t;
-    gb += double(-psi * t / C(18));
-    dzrb = gf * psi * Fzb * ir;
-    drrb = gf * psi * Frb * ir;
-    drdb = -gf * psi * Frb * ir * ir;
+    gb += double(-psi * t * C(1.0 / 18.0));
+    dzrb = gf * psi * Fzb * irr;
+    drrb = gf * psi * Frb * irr;
+    drdb = -gf * psi * Frb * irr * irr;
   }
   A.psib[o] = pb;
   A.dzrb[o] = dzrb;
   A.drrb[o] = drrb;
   A.drdb[o] = drdb;
   A.accG[o] += gb;
+  A.accT[o] += tacc;
 }
+
 
 // ---- deriv: transposed 1D d_z (into the 1D d_r field) and isotropic d_r (into
 // the padded d_r psi field, rows -2 .. Nr+1)
@@ -307,7 +307,7 @@ __global__ void adj_final(Adj<C> A) {
   const int gw = 2 * A.Nr - 1 - j;
   if (gw <= A.Nr + 3) pb += psi_pad_adj(k, gw, A);
   const C rho = A.inter[I_RHO * A.plane + o];
-  const C rb = A.rhob[o] + pb * exp(-rho / A.rho0);
+  const C rb = A.rhob[o] + pb * exp(-rho * A.inv_rho0);
   const C jzb = A.jzb[o], jrb = A.jrb[o];
 #pragma unroll
   for (int q = 0; q < 9; ++q)
@@ -461,9 +461,9 @@ AdjLayout adj_layout(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem& p) {
   size_t o = 0;
   auto take = [&](size_t b) { const size_t a = o; o = al(o + b); return a; };
   L.ckpt = take((size_t)L.nck * L.state_elems * cb);
-  L.seg = take((size_t)L.nseg * L.state_elems * cb);
+  L.seg = take((size_t)(L.nseg + 1) * L.state_elems * cb);  // the segment's states
   L.lam = take(2 * 9 * plane * cb);
-  L.inter = take((size_t)amlbm::I_COUNT * plane * cb);
+  L.inter = take((size_t)L.nseg * amlbm::I_COUNT * plane * cb);  // their intermediates
   L.mu = take(9 * plane * cb);
   L.arr = take((size_t)kAdjArrays * plane * cb);
   L.drp = take((size_t)(ci.Nr + 4) * ci.host.P * cb);
@@ -585,15 +585,18 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
                                         lam[0]);
       ADJ_CK(cudaGetLastError());
     }
-    // descriptors of the segment slots for the intermediates kernel (tile 32 x 8)
+    // descriptors of the segment slots (tile 32 x 8): descriptor q steps slot q
+    // into slot q + 1
     {
       std::vector<InstDesc> d(L.nseg, ci.host);
       for (int q = 0; q < L.nseg; ++q) {
         d[q].tiles_z = (Nz + 31) / 32;
         d[q].tiles_r = (Nr + 7) / 8;
         d[q].tile_base = 0;
-        d[q].f[0] = seg + (size_t)q * L.state_elems;
-        d[q].psi[0] = seg + (size_t)q * L.state_elems + 9 * plane;
+        for (int h = 0; h < 2; ++h) {
+          d[q].f[h] = seg + (size_t)(q + h) * L.state_elems;
+          d[q].psi[h] = seg + (size_t)(q + h) * L.state_elems + 9 * plane;
+        }
       }
       std::vector<int> tiles(L.ntiles, 0);
       ADJ_CK(cudaMemcpyAsync(base + L.descs, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
@@ -607,7 +610,7 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
       A.plane = plane;
       A.tau = C(ci.host.tau); A.omega = C(1) / A.tau; A.G = C(ci.host.G); A.rho0 = C(ci.host.rho0);
       A.gz = C(ci.host.gz);
-      A.inter = reinterpret_cast<C*>(base + L.inter);
+      A.inv_rho0 = C(1.0 / ci.host.rho0);
       A.mu = reinterpret_cast<C*>(base + L.mu);
       C* arr = reinterpret_cast<C*>(base + L.arr);
       C** fields[kAdjArrays] = {&A.rhob, &A.uzb, &A.urb, &A.vzb, &A.vrb, &A.g1b, &A.g2b, &A.g3b, &A.jzb,
@@ -620,33 +623,26 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
       const InstDesc* d_seg = reinterpret_cast<const InstDesc*>(base + L.descs);
       const int* d_tiles = reinterpret_cast<const int*>(base + L.tiles);
       const int nbp = (Nz * (Nr + 4) + 255) / 256;
+      C* inter_seg = reinterpret_cast<C*>(base + L.inter);
+      const size_t iseg = (size_t)I_COUNT * plane;
       int cur = 0;
       for (int m = L.nck - 1; m >= 0; --m) {
         const int n0 = m * p->ckpt_every, n1 = std::min(p->T, n0 + p->ckpt_every);
-        // recompute the segment's states from its checkpoint
+        // recompute the segment's states from its checkpoint, with the
+        // intermediates of each (the last step's new state is not needed)
         ADJ_CK(cudaMemcpyAsync(seg, ckpt + (size_t)m * L.state_elems, SB, cudaMemcpyDeviceToDevice, s));
-        if (n1 - n0 > 1) {
-          amlbm_device_state(ctx, &fcur, &pcur, &pitch);
-          ADJ_CK(cudaMemcpyAsync(fcur, seg, FB, cudaMemcpyDeviceToDevice, s));
-          ADJ_CK(cudaMemcpyAsync(pcur, seg + 9 * plane, PB, cudaMemcpyDeviceToDevice, s));
-          for (int q = 1; q < n1 - n0; ++q) {
-            if ((rc = amlbm_step(ctx, 1))) goto done;
-            amlbm_device_state(ctx, &fcur, &pcur, &pitch);
-            C* dst = seg + (size_t)q * L.state_elems;
-            ADJ_CK(cudaMemcpyAsync(dst, fcur, FB, cudaMemcpyDeviceToDevice, s));
-            ADJ_CK(cudaMemcpyAsync(dst + 9 * plane, pcur, PB, cudaMemcpyDeviceToDevice, s));
-          }
-        }
+        for (int q = 0; q < n1 - n0; ++q)
+          ADJ_CK(launch_step_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles, inter_seg + q * iseg,
+                                   plane, s));
         // transposed steps from the last of the segment to the first
         for (int n = n1 - 1; n >= n0; --n) {
           const int q = n - n0;
-          ADJ_CK(launch_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles, const_cast<C*>(A.inter), plane, s));
+          A.inter = inter_seg + q * iseg;
           A.f = seg + (size_t)q * L.state_elems;
           A.lam_in = lam[cur];
           A.lam_out = lam[cur ^ 1];
           adj_post<C><<<nb, 256, 0, s>>>(A);
           adj_vel<C><<<nb, 256, 0, s>>>(A);
-          adj_force<C><<<nb, 256, 0, s>>>(A);
           adj_deriv<C><<<nbp, 256, 0, s>>>(A);
           adj_final<C><<<nb, 256, 0, s>>>(A);
           ADJ_CK(cudaGetLastError());

@@ -63,6 +63,12 @@ enum InterField {
 // f[0] / psi[0] hold that state, into inter (I_COUNT planes of plane elements).
 cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
                          int ntiles, void* inter, size_t plane, cudaStream_t s);
+// The timestep of instance 0 of d_desc from f[0] / psi[0] into f[1] / psi[1]
+// (FP64 / FP32 storage, no shift) together with the intermediates of the state
+// it starts from, as launch_inter writes them.
+cudaError_t launch_step_inter(int storage, int tz, int tr, const InstDesc* d_desc,
+                              const int* d_tile_inst, int ntiles, void* inter, size_t plane,
+                              cudaStream_t s);
 // Diagnostics (amlbm_diag.cu) of the state whose rho / u the read-back kernel
 // has written: partial sums into `partials` (nblk x 8 doubles) and the Nz column
 // radii into `cols`, then a single-block pass into out[16].
