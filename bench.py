@@ -248,6 +248,7 @@ def run_gpu(args):
         # parity form; FP32 the unshifted single-precision form)
         compare = {}
         adjoint = None
+        scaled = None
         if rank == 0 and not args.no_compare:
             for st in ("f64", "f32"):
                 bb, _ = build_batch(st, rank, stream=stream)
@@ -258,6 +259,7 @@ def run_gpu(args):
             compare[STORAGE] = {"mlups": round(mlups / world, 1), "schedule": sched, "tile": list(tile)}
             compare["bf16_over_f64"] = round(compare[STORAGE]["mlups"] / compare["f64"]["mlups"], 2)
             adjoint = adjoint_cost(torch)
+            scaled = scaled_cases(torch, tile, sched)
 
     traffic, tkernel = profiled_traffic(os.path.join(ROOT, "paper_1310_1871_gb300", "csrc", "amlbm_step.cu"))
     kname = (f"lbm_persistent<__nv_bfloat16, {tile[0]}, {tile[1]}>" if sched == "fused"
@@ -287,6 +289,7 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "compare_mlups": compare or None,
             "adjoint": adjoint if (rank == 0 and not args.no_compare) else None,
+            "scaled_hbm_cases": scaled if (rank == 0 and not args.no_compare) else None,
             "wall_s_timed_loop": round(wall, 3),
         }
         print(json.dumps(line), flush=True)
@@ -317,6 +320,55 @@ def adjoint_cost(torch, T=2000):
         ta = time.perf_counter() - t0
         out[st] = {"forward_s": round(tf, 4), "adjoint_s": round(ta, 4), "ratio": round(ta / tf, 2)}
         lat.close()
+    return out
+
+
+def scaled_cases(torch, tile, sched, steps=10):
+    """The HBM-sized cases: the oscillating-drop physics (G = -5, tau = 1, P2
+    perturbation 5 %) scaled 32x to an 8192 x 4096 lattice (33.5 M sites, R = 1280),
+    and the sweep's recipe with 1024 instances (seeds 1234 + k).  BF16 storage.
+    Each state is far larger than L2, so back-to-back steps read it from HBM;
+    CUDA events around `steps` timesteps after 3 warm-up steps."""
+    from paper_1310_1871_gb300 import amlbm
+    hbm, kind = peaks()
+    out = {}
+
+    def timed(step_fn, sites):
+        for _ in range(3):
+            step_fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            step_fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        gbs = BYTES_PER_LU[STORAGE] * sites / (ms * 1e-3) / 1e9
+        return {"sites": int(sites), "ms_per_step": round(ms, 4), "mlups": round(sites / (ms * 1e-3) / 1e6, 1),
+                "achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4)}
+
+    Nz, Nr, R = 8192, 4096, 1280.0
+    lat = amlbm.Lattice(Nz, Nr, tau=1.0, G=-5.0, storage=STORAGE)
+    z = torch.arange(Nz, dtype=torch.float64, device="cuda")[None, :] - Nz / 2
+    r = torch.arange(Nr, dtype=torch.float64, device="cuda")[:, None] + 0.5
+    d = torch.sqrt(z * z + r * r)
+    ct = z / d
+    rs = R * (1.0 + 0.05 * 0.5 * (3 * ct * ct - 1))
+    rho = I.RHO_V_G5 + 0.5 * (I.RHO_L_G5 - I.RHO_V_G5) * (1 - torch.tanh((d - rs) / 2.0))
+    lat.init_fields_device(rho.contiguous())
+    del z, r, d, ct, rs, rho
+    out["lattice_8192x4096"] = timed(lambda: lat.step(1), Nz * Nr)
+    lat.close()
+
+    inst = I.batch_sweep(1024)
+    specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
+    b = amlbm.Batch(specs, storage=STORAGE, tile=tuple(tile), schedule=sched)
+    cols = [np.concatenate([np.ravel(x.make_fields()[q]) for x in inst]) for q in range(3)]
+    b.init_all(*cols)
+    out["batch_1024"] = dict(timed(lambda: b.step(1), b.sites), tile=list(b.tile), schedule=b.schedule)
+    b.close()
+    out["peak"] = f"{hbm} GB/s ({kind} HBM copy bandwidth)"
     return out
 
 
