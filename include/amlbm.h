@@ -67,18 +67,23 @@ extern "C" {
 #define AMLBM_STORE_F16 2  /* IEEE half of (f_i - W_i s) 2^10 (s: see AMLBM_SHIFT_*) */
 #define AMLBM_STORE_BF16 3 /* bfloat16 of f_i - W_i s */
 
-/* What the FP32 and 16-bit forms store: f_i - W_i s.  FP64 storage is never shifted. */
+/* What the FP32 and 16-bit forms store: f_i - W_i s (or f_i - f^eq_i, EQUILIBRIUM).
+ * FP64 storage is never shifted. */
 #define AMLBM_SHIFT_DEFAULT 0 /* NONE for FP32, LOCAL for FP16 / BF16 */
 #define AMLBM_SHIFT_NONE 1    /* s = 0 */
 #define AMLBM_SHIFT_GLOBAL 2  /* s = rho_ref, one constant per lattice */
 #define AMLBM_SHIFT_LOCAL 3   /* s = -rho0 ln(1 - psi/rho0) of the site's stored psi: the
                                  site's own density recovered from psi, no extra bytes */
+#define AMLBM_SHIFT_EQUILIBRIUM 4 /* store f_i - f^eq_i(s, v) with s as LOCAL and v the bare
+                                     velocity sum_i c_i f_i / rho of the stored state, kept in
+                                     two FP32 planes beside psi (8 more bytes per site): the
+                                     16-bit value then carries only the non-equilibrium part */
 
 /* Rounding of the 16-bit stores.  Stochastic rounding draws its bits from a hash
  * of (site, population, step number), so a run is reproducible and unbiased in
  * expectation; round-to-nearest repeats the same error at every step of a
  * slowly varying state, and those errors add up. */
-#define AMLBM_ROUND_DEFAULT 0 /* stochastic for BF16, to nearest otherwise */
+#define AMLBM_ROUND_DEFAULT 0 /* stochastic for BF16 with the W_i s shifts, else to nearest */
 #define AMLBM_ROUND_NEAREST 1
 #define AMLBM_ROUND_STOCHASTIC 2
 
@@ -157,7 +162,9 @@ int amlbm_read_fields(amlbm_ctx* ctx, double* rho, double* uz, double* ur, doubl
  * Synchronises. */
 int amlbm_diagnostics(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* out);
 
-/* Copy the full state (populations, psi, step count) to / from a host buffer.
+/* Copy the full state (populations, psi, the stored velocity of the equilibrium
+ * shift, the step count and the position of the stochastic-rounding stream) to /
+ * from a host buffer, so that a restarted run continues bit for bit.
  * amlbm_save_state with buf == NULL stores the needed size in *len. */
 int amlbm_save_state(amlbm_ctx* ctx, void* buf, size_t* len);
 int amlbm_load_state(amlbm_ctx* ctx, const void* buf, size_t len);

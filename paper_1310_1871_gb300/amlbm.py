@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -5
 WALL = {"freeslip": 0, "noslip": 1}
 SRC = {"local": 0, "link": 1}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
-SHIFT = {"default": 0, "none": 1, "global": 2, "local": 3}
+SHIFT = {"default": 0, "none": 1, "global": 2, "local": 3, "equilibrium": 4}
 ROUNDING = {"default": 0, "nearest": 1, "stochastic": 2}
 DIAG_FIELDS = ["mass2d", "mass3d", "momz3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out",
                "dp", "bad", "sumS", "steps"]

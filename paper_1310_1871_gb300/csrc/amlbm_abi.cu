@@ -74,16 +74,20 @@ void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched,
   *tr = 8;
 }
 
-// Shift code the kernels use: 0 none, 1 global rho_ref, 2 local (from psi).
+// Shift code the kernels use: 0 none, 1 global rho_ref, 2 local (from psi),
+// 3 equilibrium (local s and the stored velocity).
 int resolve_shift(const amlbm_bc& bc) {
   if (bc.storage == AMLBM_STORE_F64) return 0;
   switch (bc.shift) {
     case AMLBM_SHIFT_NONE: return 0;
     case AMLBM_SHIFT_GLOBAL: return 1;
     case AMLBM_SHIFT_LOCAL: return 2;
+    case AMLBM_SHIFT_EQUILIBRIUM: return 3;
     default: return bc.storage == AMLBM_STORE_F32 ? 0 : 2;
   }
 }
+// Planes of the compute type per psi copy: psi, and v_z, v_r for the equilibrium shift.
+int psi_planes(int shift_code) { return shift_code == 3 ? 3 : 1; }
 
 int validate(const amlbm_instance& I, int idx) {
   const std::string w = "instance " + std::to_string(idx) + ": ";
@@ -101,7 +105,7 @@ int validate(const amlbm_instance& I, int idx) {
     return fail(AMLBM_EINVAL, w + "bad src_mode");
   if (I.bc.storage < AMLBM_STORE_F64 || I.bc.storage > AMLBM_STORE_BF16)
     return fail(AMLBM_EINVAL, w + "bad storage");
-  if (I.bc.shift < AMLBM_SHIFT_DEFAULT || I.bc.shift > AMLBM_SHIFT_LOCAL)
+  if (I.bc.shift < AMLBM_SHIFT_DEFAULT || I.bc.shift > AMLBM_SHIFT_EQUILIBRIUM)
     return fail(AMLBM_EINVAL, w + "bad shift");
   if (I.bc.storage == AMLBM_STORE_F64 && I.bc.shift > AMLBM_SHIFT_NONE)
     return fail(AMLBM_EINVAL, w + "FP64 storage is not shifted");
@@ -152,8 +156,9 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
     const size_t plane = (size_t)pitch_of(I.Nz) * I.Nr;
     L.f0.push_back(take(9 * plane * elem_bytes(storage)));
     L.f1.push_back(take(9 * plane * elem_bytes(storage)));
-    L.p0.push_back(take(plane * compute_bytes(storage)));
-    L.p1.push_back(take(plane * compute_bytes(storage)));
+    const size_t pp = plane * compute_bytes(storage) * psi_planes(resolve_shift(I.bc));
+    L.p0.push_back(take(pp));
+    L.p1.push_back(take(pp));
     L.uv.push_back(take(4 * plane * compute_bytes(storage)));
     L.rho.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
     L.uz.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
@@ -294,10 +299,13 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.axisym = I.bc.axisym;
     d.src = I.bc.src_mode;
     d.shift = resolve_shift(I.bc);
-    // 1 = stochastic rounding of the 16-bit stores (measured: BF16 gains an order
-    // of magnitude in accuracy from it, FP16 does not)
-    d.rounding = storage == AMLBM_STORE_BF16 ? (I.bc.rounding != AMLBM_ROUND_NEAREST)
-               : storage == AMLBM_STORE_F16 ? (I.bc.rounding == AMLBM_ROUND_STOCHASTIC) : 0;
+    // 1 = stochastic rounding of the 16-bit stores.  Default: stochastic for BF16
+    // with the W_i s shifts (measured: an order of magnitude more accurate there),
+    // to nearest for FP16 and for the equilibrium shift (no gain measured)
+    const bool sr_default = storage == AMLBM_STORE_BF16 && d.shift != 3;
+    d.rounding = (storage != AMLBM_STORE_F16 && storage != AMLBM_STORE_BF16) ? 0
+               : I.bc.rounding == AMLBM_ROUND_STOCHASTIC ? 1
+               : I.bc.rounding == AMLBM_ROUND_NEAREST ? 0 : (sr_default ? 1 : 0);
     d.tiles_z = (I.Nz + tz - 1) / tz;
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
@@ -644,6 +652,9 @@ static amlbm_instance one(int Nz, int Nr, double tau, double G, double rho0, con
 size_t amlbm_workspace_bytes(int Nz, int Nr, int storage) {
   amlbm_bc bc = default_bc();
   bc.storage = storage;
+  // room for every shift mode of this storage (the equilibrium shift keeps the
+  // velocity beside psi)
+  if (storage != AMLBM_STORE_F64) bc.shift = AMLBM_SHIFT_EQUILIBRIUM;
   amlbm_instance I = one(Nz, Nr, 1.0, -5.0, 1.0, &bc);
   return amlbm_batch_workspace_bytes(1, &I);
 }
@@ -691,7 +702,8 @@ int amlbm_diagnostics(amlbm_ctx* c, const amlbm_diag_params* dp, amlbm_diag* out
 namespace {
 struct StateHeader {
   char magic[8];
-  int Nz, Nr, storage, pad;
+  int Nz, Nr, storage;
+  int rstep;  // step number of the stochastic-rounding stream at the saved state
   long long steps;
   size_t fbytes, pbytes;
 };
@@ -702,7 +714,8 @@ int amlbm_save_state(amlbm_ctx* c, void* buf, size_t* len) {
   amlbm_batch* b = c->b;
   const InstDesc& d = b->desc[0];
   const size_t plane = (size_t)d.P * d.Nr;
-  const size_t fb = 9 * plane * elem_bytes(b->storage), pb = plane * compute_bytes(b->storage);
+  const size_t fb = 9 * plane * elem_bytes(b->storage),
+               pb = plane * compute_bytes(b->storage) * psi_planes(d.shift);
   const size_t need = sizeof(StateHeader) + fb + pb;
   if (!buf) { *len = need; return AMLBM_OK; }
   if (*len < need) return fail(AMLBM_EINVAL, "buffer too small: need " + std::to_string(need));
@@ -710,6 +723,8 @@ int amlbm_save_state(amlbm_ctx* c, void* buf, size_t* len) {
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "AMLBMST1", 8);
   h.Nz = d.Nz; h.Nr = d.Nr; h.storage = b->storage; h.steps = b->steps[0]; h.fbytes = fb; h.pbytes = pb;
+  AMLBM_CK(cudaMemcpyAsync(&h.rstep, b->d_ctr + 2 + b->parity, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof(h));
   AMLBM_CK(cudaMemcpyAsync(p + sizeof(h), d.f[b->parity], fb, cudaMemcpyDeviceToHost, b->stream));
@@ -727,13 +742,15 @@ int amlbm_load_state(amlbm_ctx* c, const void* buf, size_t len) {
   if (len < sizeof(h)) return fail(AMLBM_EINVAL, "buffer too small");
   std::memcpy(&h, buf, sizeof(h));
   const size_t plane = (size_t)d.P * d.Nr;
-  const size_t fb = 9 * plane * elem_bytes(b->storage), pb = plane * compute_bytes(b->storage);
+  const size_t fb = 9 * plane * elem_bytes(b->storage),
+               pb = plane * compute_bytes(b->storage) * psi_planes(d.shift);
   if (std::memcmp(h.magic, "AMLBMST1", 8) || h.Nz != d.Nz || h.Nr != d.Nr || h.storage != b->storage ||
       h.fbytes != fb || h.pbytes != pb || len < sizeof(h) + fb + pb)
     return fail(AMLBM_EINVAL, "state does not match this context");
   const char* p = static_cast<const char*>(buf);
   AMLBM_CK(cudaMemcpyAsync(d.f[b->parity], p + sizeof(h), fb, cudaMemcpyHostToDevice, b->stream));
   AMLBM_CK(cudaMemcpyAsync(d.psi[b->parity], p + sizeof(h) + fb, pb, cudaMemcpyHostToDevice, b->stream));
+  AMLBM_CK(cudaMemcpyAsync(b->d_ctr + 2 + b->parity, &h.rstep, sizeof(int), cudaMemcpyHostToDevice, b->stream));
   AMLBM_CK(cudaStreamSynchronize(b->stream));
   b->steps[0] = h.steps;
   return AMLBM_OK;

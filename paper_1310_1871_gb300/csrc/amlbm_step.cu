@@ -168,6 +168,24 @@ __device__ __forceinline__ void store_site(S* o, size_t plane, const typename St
   }
 }
 
+// Store q_i = fn[i] - base[i] (the equilibrium shift), rounding as store_site.
+template <class S>
+__device__ __forceinline__ void store_site_base(S* o, size_t plane, const typename Store<S>::C* fn,
+                                                const typename Store<S>::C* base, int rounding,
+                                                uint32_t site, uint32_t step) {
+  if (sizeof(S) == 2 && rounding) {
+    uint32_t x = mix32(site ^ mix32(step + 0x9E3779B9u));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      x = lcg_next(x);
+      o[i * plane] = Store<S>::from_sr(fn[i] - base[i], x);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i * plane] = Store<S>::from(fn[i] - base[i]);
+  }
+}
+
 // Shift s of a site from its stored psi: 0 (none), rho_ref (global), or the
 // density recovered from psi, -rho0 ln(1 - psi/rho0) (local).  Writer and
 // reader evaluate it from the same stored psi with the same non-contracted
@@ -179,7 +197,7 @@ __device__ __forceinline__ double shift_base(int mode, double psi, double inv_rh
 }
 __device__ __forceinline__ float shift_base(int mode, float psi, float inv_rho0, float rho0,
                                             float rref) {
-  if (mode == 2) {
+  if (mode >= 2) {
     const float q = __fsub_rn(1.0f, __fmul_rn(psi, inv_rho0));
     return __fmul_rn(-rho0, __logf(q));
   }
@@ -352,6 +370,56 @@ __device__ __forceinline__ T psi_of(const Par<T>& q, T rho) {
   return (lit<T>(1.0) - expl(-rho * q.inv_rho0)) * q.rho0;
 }
 
+// Decode the nine populations of a site from their stored values q[i * plane]:
+// f_i = q_i + W_i s (shift modes 0-2, one fused multiply-add) or, in the
+// equilibrium mode (3), f_i = q_i + f^eq_i(s, v) with the velocity v stored in
+// the two planes that follow psi (pv points at the site's psi).
+template <class S, class T>
+__device__ __forceinline__ void decode_site(int mode, const S* q, size_t plane, typename Store<S>::C psi,
+                                            const typename Store<S>::C* pv, typename Store<S>::C inv_rho0,
+                                            typename Store<S>::C rho0, typename Store<S>::C rref, T* f) {
+  const T sbt{shift_base(mode, psi, inv_rho0, rho0, rref)};
+  if (mode == 3) {
+    T fe[9];
+    equilibrium(sbt, T{pv[plane]}, T{pv[2 * plane]}, fe);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = T{Store<S>::to(q[i * plane])} + fe[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(q[i * plane])});
+  }
+}
+
+// Store the new populations fn of a site and its psi (at *pso); in the
+// equilibrium mode also the bare velocity v = sum_i c_i fn_i / rho of the new
+// state (after psi) and q_i = fn_i - f^eq_i(s, v).
+template <class S, class T>
+__device__ __forceinline__ void encode_site(int mode, S* o, typename Store<S>::C* pso, size_t plane,
+                                            const T* fn, T rho, typename Store<S>::C psi,
+                                            typename Store<S>::C inv_rho0, typename Store<S>::C rho0,
+                                            typename Store<S>::C rref, int rounding, uint32_t site,
+                                            uint32_t step) {
+  using C = typename Store<S>::C;
+  const C sb = shift_base(mode, psi, inv_rho0, rho0, rref);
+  C fv[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fv[i] = fn[i].v;
+  if (mode == 3) {
+    const T ir = rcp(rho), vz = moment_z(fn) * ir, vr = moment_r(fn) * ir;
+    T fe[9];
+    equilibrium(T{sb}, vz, vr, fe);
+    C base[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) base[i] = fe[i].v;
+    store_site_base<S>(o, plane, fv, base, rounding, site, step);
+    pso[plane] = vz.v;
+    pso[2 * plane] = vr.v;
+  } else {
+    store_site<S>(o, plane, fv, sb, rounding, site, step);
+  }
+  pso[0] = psi;
+}
+
 // ---------------------------------------------------------------- tiles --
 // 256 threads per CTA.  A 2D region of a tile whose width is a multiple of 32
 // is walked as warp tasks: a task is a 32-wide segment of one row, so each warp
@@ -490,10 +558,8 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     const T psi = p[0];
     T f[9];
     {
-      const T sbt{shift_base(shift, psi.v, inv_rho0c, rho0c, rrefc)};
-      const S* fp = fin + (size_t)j * P + colmap[lc + G::HP - G::HF];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fp[i * plane])});
+      const size_t so = (size_t)j * P + colmap[lc + G::HP - G::HF];
+      decode_site<S>(shift, fin + so, plane, psi.v, psin + so, inv_rho0c, rho0c, rrefc, f);
     }
     const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
     T sz, sr;
@@ -662,13 +728,9 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
 #pragma unroll
       for (int i = 0; i < 9; ++i) fn[i] = fma(h[i], lit<T>(0.5), fn[i]);
     }
-    const C ps = psi_of(q, moment0(fn)).v;
-    const C sb = shift_base(shift, ps, inv_rho0c, rho0c, rrefc);
-    C fv[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fv[i] = fn[i].v;
-    store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
-    psout[(size_t)j * P + k] = ps;
+    const T rho = moment0(fn);
+    encode_site<S>(shift, fout + (size_t)j * P + k, psout + (size_t)j * P + k, plane, fn, rho,
+                   psi_of(q, rho).v, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k), step);
   });
 }
 
@@ -776,11 +838,9 @@ __global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ 
     const T inv_r = inv_r_of(T(), j);
     const T* p = sPsi + (lr + G::HP) * G::PZ + (lc + G::HP);
     const T psi = p[0];
-    const T sbt{shift_base(shift, psi.v, inv_rho0c, rho0c, rrefc)};
-    const S* fp = fin + (size_t)j * P + k;
     T f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fp[i * plane])});
+    decode_site<S>(shift, fin + (size_t)j * P + k, plane, psi.v, psin + (size_t)j * P + k, inv_rho0c, rho0c,
+                   rrefc, f);
     const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
     T sz, sr;
     sc_sums(p, G::PZ, sz, sr);
@@ -871,10 +931,8 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const int j = j0 - 1 + lr;
     if (j < 0 || j >= Nr) return;
     const size_t o = (size_t)j * P + colmap[lc + G::HF - 1];
-    const T sbt{shift_base(shift, psin[o], inv_rho0c, rho0c, rrefc)};
     T f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = fma(lit<T>(w_(i)), sbt, T{Store<S>::to(fin[i * plane + o])});
+    decode_site<S>(shift, fin + o, plane, psin[o], psin + o, inv_rho0c, rho0c, rrefc, f);
     const T rho = moment0(f);
     const T vz{uv[2 * plane + o]}, vr{uv[3 * plane + o]};
     T fe[9];
@@ -942,13 +1000,9 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
 #pragma unroll
       for (int i = 0; i < 9; ++i) fn[i] = fma(h[i], lit<T>(0.5), fn[i]);
     }
-    const C psi = psi_of(q, moment0(fn)).v;
-    const C sb = shift_base(shift, psi, inv_rho0c, rho0c, rrefc);
-    C fv[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fv[i] = fn[i].v;
-    store_site<S>(fout + (size_t)j * P + k, plane, fv, sb, D.rounding, (uint32_t)(j * Nz + k), step);
-    psout[(size_t)j * P + k] = psi;
+    const T rho = moment0(fn);
+    encode_site<S>(shift, fout + (size_t)j * P + k, psout + (size_t)j * P + k, plane, fn, rho,
+                   psi_of(q, rho).v, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k), step);
   });
 }
 
@@ -966,13 +1020,9 @@ __device__ __forceinline__ void init_site(const InstDesc& D, int n, double rho_d
   const Par<T> q = par_of<T>(D);
   T fe[9];
   equilibrium(T{C(rho_d)}, T{C(uz_d)}, T{C(ur_d)}, fe);
-  const C psi = psi_of(q, moment0(fe)).v;
-  const C sb = shift_base(D.shift, psi, kc(D, K_INVRHO0, C()), kc(D, K_RHO0, C()), kc(D, K_RREF, C()));
-  C fv[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fv[i] = fe[i].v;
-  store_site<S>(f + o, plane, fv, sb, 0, 0u, 0u);
-  psi_out[o] = psi;
+  const T rho = moment0(fe);
+  encode_site<S>(D.shift, f + o, psi_out + o, plane, fe, rho, psi_of(q, rho).v, kc(D, K_INVRHO0, C()),
+                 kc(D, K_RHO0, C()), kc(D, K_RREF, C()), 0, 0u, 0u);
 }
 
 template <class S>
@@ -1020,11 +1070,13 @@ __global__ void unpack_kernel(const InstDesc* __restrict__ descs, int inst, int 
   const int j = n / D.Nz, k = n - j * D.Nz;
   const size_t plane = (size_t)D.P * D.Nr, o = (size_t)j * D.P + k;
   const S* f = static_cast<const S*>(D.f[parity]);
-  const C psi = static_cast<const C*>(D.psi[parity])[o];
-  const C sb = shift_base(D.shift, psi, kc(D, K_INVRHO0, C()), kc(D, K_RHO0, C()), kc(D, K_RREF, C()));
+  const C* ps = static_cast<const C*>(D.psi[parity]) + o;
+  using T = typename Store<S>::T;
+  T fv[9];
+  decode_site<S>(D.shift, f + o, plane, ps[0], ps, kc(D, K_INVRHO0, C()), kc(D, K_RHO0, C()),
+                 kc(D, K_RREF, C()), fv);
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    out[(size_t)i * N + n] = double(fma_c(C(w_(i)), sb, Store<S>::to(f[i * plane + o])));
+  for (int i = 0; i < 9; ++i) out[(size_t)i * N + n] = double(fv[i].v);
 }
 
 // ------------------------------------------------------------- launchers --

@@ -72,6 +72,16 @@ def test_tile_lists_and_workspace_sizes(lib):
     # populations (two copies) dominate: 2 x 9 x pitch x Nr x 8 bytes for FP64
     assert big >= 2 * 9 * 256 * 128 * 8
     assert lib.amlbm_workspace_bytes(0, 128, 0) == 0
+    # the equilibrium shift keeps two velocity planes beside each psi copy
+    inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(256, 128, 1.0, -5.0, 1.0,
+                                                amlbm.make_bc(storage="bf16", shift="local")))
+    loc = lib.amlbm_batch_workspace_bytes(1, inst)
+    inst[0].bc.shift = amlbm.SHIFT["equilibrium"]
+    eq = lib.amlbm_batch_workspace_bytes(1, inst)
+    assert eq - loc == 2 * 2 * 256 * 128 * 4
+    assert half >= eq  # a context's workspace fits every shift mode
+    inst[0].bc.shift = 5
+    assert lib.amlbm_batch_workspace_bytes(1, inst) == 0
 
 
 def test_workspace_too_small_rejected(lib):

@@ -99,6 +99,11 @@ PRECISION_CASES = [
     ("f16", "local", "nearest", 5e-3), ("bf16", "local", "nearest", 1.5e-1),
     ("f16", "local", "stochastic", 5e-3), ("bf16", "local", "stochastic", 3e-2),
     ("f16", "global", "nearest", 1.0), ("bf16", "global", "nearest", 1.0),
+    # equilibrium shift (the 16-bit value holds f_i - f^eq_i): over the four placements
+    # FP16 measured 1.1e-5 .. 1.1e-4 (nearest), BF16 2.2e-4 .. 1.5e-3 (nearest) and
+    # 2.0e-4 .. 2.0e-3 (stochastic)
+    ("f16", "equilibrium", "nearest", 2.5e-4), ("bf16", "equilibrium", "nearest", 4e-3),
+    ("bf16", "equilibrium", "stochastic", 5e-3), ("f32", "equilibrium", "nearest", 1e-4),
 ]
 
 
@@ -115,10 +120,12 @@ def test_reduced_precision_forms(storage, shift, rounding, bound):
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("case", [dict(), dict(wall="noslip", gz=1e-4), dict(src="link"), dict(axisym=False),
-                                  dict(rounding="stochastic")])
+                                  dict(rounding="stochastic"), dict(shift="equilibrium")])
 def test_split_schedule_equals_fused_bitwise(storage, case):
     """The two-kernel schedule performs the fused kernel's arithmetic operation for
     operation: states after 120 steps are bit-identical (ragged 70 x 21 lattice)."""
+    if storage == "f64" and case.get("shift"):
+        pytest.skip("FP64 storage is never shifted")
     spec = amlbm.InstanceSpec(70, 21, 0.8, -5.0, **case)
     fl = I.drop(70, 21, 30.0, 9.0, amps=(0.08,))
     out = []
@@ -203,9 +210,12 @@ def test_diagnostics_flag_unstable_state():
     lat.close()
 
 
-def test_save_load_state_roundtrip():
+@pytest.mark.parametrize("storage,shift", [("f32", "default"), ("bf16", "equilibrium")])
+def test_save_load_state_roundtrip(storage, shift):
+    """The saved state (populations, psi and, for the equilibrium shift, the stored
+    velocity) restarts the run bit for bit."""
     fl = I.drop(40, 20, 20.0, 7.0, amps=(0.05,))
-    lat = amlbm.Lattice(40, 20, tau=0.9, G=-5.0, storage="f32")
+    lat = amlbm.Lattice(40, 20, tau=0.9, G=-5.0, storage=storage, shift=shift)
     lat.init_fields(*fl)
     lat.step(30)
     state = lat.save_state()
