@@ -249,6 +249,7 @@ def run_gpu(args):
         compare = {}
         adjoint = None
         scaled = None
+        precision = None
         if rank == 0 and not args.no_compare:
             for st in ("f64", "f32"):
                 bb, _ = build_batch(st, rank, stream=stream)
@@ -260,6 +261,7 @@ def run_gpu(args):
             compare["bf16_over_f64"] = round(compare[STORAGE]["mlups"] / compare["f64"]["mlups"], 2)
             adjoint = adjoint_cost(torch)
             scaled = scaled_cases(torch, tile, sched)
+            precision = precision_vs_f64(torch)
 
     traffic, tkernel = profiled_traffic(os.path.join(ROOT, "paper_1310_1871_gb300", "csrc", "amlbm_step.cu"))
     kname = (f"lbm_persistent<__nv_bfloat16, {tile[0]}, {tile[1]}>" if sched == "fused"
@@ -290,6 +292,7 @@ def run_gpu(args):
             "compare_mlups": compare or None,
             "adjoint": adjoint if (rank == 0 and not args.no_compare) else None,
             "scaled_hbm_cases": scaled if (rank == 0 and not args.no_compare) else None,
+            "precision_vs_f64": precision if (rank == 0 and not args.no_compare) else None,
             "wall_s_timed_loop": round(wall, 3),
         }
         print(json.dumps(line), flush=True)
@@ -320,6 +323,44 @@ def adjoint_cost(torch, T=2000):
         ta = time.perf_counter() - t0
         out[st] = {"forward_s": round(tf, 4), "adjoint_s": round(ta, 4), "ratio": round(ta / tf, 2)}
         lat.close()
+    return out
+
+
+def precision_vs_f64(torch, steps=1000):
+    """Per-instance max relative rho error of the reduced-precision forms against
+    the FP64 form after `steps` timesteps of the 64-drop sweep, and their
+    throughput on the same sweep (back-to-back steps, autotuned launch).
+    Instances whose FP64 run itself goes non-finite (the unstable corner of the
+    parameter ranges) are left out and counted."""
+    from paper_1310_1871_gb300 import amlbm
+    inst = I.batch_sweep(64)
+    cols = [np.concatenate([np.ravel(x.make_fields()[q]) for x in inst]) for q in range(3)]
+
+    def run(storage, shift):
+        specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G, shift=shift) for x in inst]
+        b = amlbm.Batch(specs, storage=storage, tile="auto")
+        b.init_all(*cols)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.step(steps)
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / steps
+        rho = [b.read(k)[0] for k in range(len(inst))]
+        b.close()
+        return rho, b.sites / (ms * 1e-3) / 1e6
+    ref, ref_mlups = run("f64", "default")
+    ok = [k for k in range(len(inst)) if np.isfinite(ref[k]).all()]
+    out = {"steps": steps, "instances_compared": len(ok), "unstable_in_f64": len(inst) - len(ok),
+           "f64_mlups": round(ref_mlups, 1)}
+    for storage, shift in (("f32", "default"), ("bf16", "default"), ("bf16", "equilibrium"),
+                           ("f16", "default"), ("f16", "equilibrium")):
+        rho, mlups = run(storage, shift)
+        err = [float(np.abs(rho[k] / ref[k] - 1).max()) for k in ok]
+        out[f"{storage}/{shift}"] = {"max_rel_rho_err": float(f"{max(err):.3e}"),
+                                     "median_rel_rho_err": float(f"{float(np.median(err)):.3e}"),
+                                     "mlups": round(mlups, 1), "over_f64": round(mlups / ref_mlups, 2)}
     return out
 
 
