@@ -447,20 +447,19 @@ __device__ __forceinline__ void for_tile(F&& body) {
   }
 }
 
-// Tile geometry (BZ x BR sites).  Halos: psi 7, isotropic d_r psi 5, 1D d_r
-// psi (z 5, r 3), rho and u 3, collided populations and sources 1.  The
-// integer maps hold the wrapped column and the mirrored row of the psi region.
+// Tile geometry (BZ x BR sites).  Halos: psi 7, isotropic d_r psi 5, rho and u
+// 3, collided populations and sources 1.  The integer maps hold the wrapped
+// column and the mirrored row of the psi region.
 template <class T, int BZ, int BR>
 struct Geo {
   static constexpr int HP = 7, HD = 5, HF = 3;
   static constexpr int PZ = BZ + 2 * HP, PR = BR + 2 * HP;
   static constexpr int DZ = BZ + 2 * HD, DR = BR + 2 * HD;
-  static constexpr int EZ = BZ + 2 * HD, ER = BR + 2 * HF;
   static constexpr int FZ = BZ + 2 * HF, FR = BR + 2 * HF;
   static constexpr int SZ = BZ + 2, SR = BR + 2;
-  static constexpr int nP = PZ * PR, nD = DZ * DR, nE = EZ * ER, nF = FZ * FR, nS = SZ * SR;
-  // region A holds psi and its derivatives, later the sources S, H_z, H_r
-  static constexpr int nA = (nP + nD + nE) > 3 * nS ? (nP + nD + nE) : 3 * nS;
+  static constexpr int nP = PZ * PR, nD = DZ * DR, nF = FZ * FR, nS = SZ * SR;
+  // region A holds psi and d_r psi, later the sources S, H_z, H_r
+  static constexpr int nA = (nP + nD) > 3 * nS ? (nP + nD) : 3 * nS;
   static constexpr int int_bytes = ((PZ + PR) * 4 + 15) / 16 * 16;
   static constexpr size_t bytes = int_bytes + sizeof(T) * (size_t)(nA + 3 * nF + 9 * nS);
 };
@@ -481,10 +480,16 @@ __device__ __forceinline__ Tile tile_of(const InstDesc* descs, const int* tile_i
   return t;
 }
 
-// Resident CTAs per SM the register allocation must allow: five for the FP32
-// arithmetic forms (their tiles use at most ~40 KB of shared memory).
-template <class S>
-struct MinBlocks { static constexpr int value = std::is_same<S, double>::value ? 1 : 5; };
+// Resident CTAs per SM the register allocation must allow: for the FP32
+// arithmetic forms as many as the tile's shared memory lets fit in the 228 KB of
+// an SM (1 KB of it reserved per CTA), at most five (48 registers a thread:
+// at six the 40-register budget spills and the step is slower).
+template <class S, class T, int BZ, int BR>
+struct MinBlocks {
+  static constexpr int fit = int((228u * 1024u) / (Geo<T, BZ, BR>::bytes + 1024u));
+  static constexpr int value =
+      std::is_same<S, double>::value ? 1 : (fit > 5 ? 5 : (fit < 1 ? 1 : fit));
+};
 
 // The fused update of one BZ x BR tile in the lane type T of the storage form.
 // MODE 0: the timestep; MODE 1 (read-back): only rho and u of the tile; MODE 2:
@@ -505,7 +510,6 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   T* base = reinterpret_cast<T*>(smem_raw + G::int_bytes);
   T* sPsi = base;
   T* sDr = sPsi + G::nP;
-  T* sD1 = sDr + G::nD;
   T* sS = base;  // after stage 2
   T* sHz = sS + G::nS;
   T* sHr = sHz + G::nS;
@@ -535,13 +539,10 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   });
   __syncthreads();
 
-  // Stage 1: isotropic d_r psi (tile + 5) and 1D d_r psi (z: tile + 5, r: tile + 3).
+  // Stage 1: isotropic d_r psi (tile + 5).
   if (ax) {
     for_tile<G::DR, G::DZ>([&](int lr, int lc) {
       sDr[lr * G::DZ + lc] = iso_r(sPsi + (lr + G::HP - G::HD) * G::PZ + (lc + G::HP - G::HD), G::PZ);
-    });
-    for_tile<G::ER, G::EZ>([&](int lr, int lc) {
-      sD1[lr * G::EZ + lc] = d1(sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HD), G::PZ);
     });
     __syncthreads();
   }
@@ -569,7 +570,11 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       const T* dr = sDr + (lr + G::HD - G::HF) * G::DZ + (lc + G::HD - G::HF);
       dr0 = dr[0];
       Drr = iso_r(dr, G::DZ);
-      Dzr = d1(sD1 + lr * G::EZ + (lc + G::HD - G::HF), 1);
+      // d_zr psi = 1D d_z of the 1D d_r psi of the four z-neighbours (Sec. II.D)
+      T e[5];
+#pragma unroll
+      for (int m = -2; m <= 2; ++m) e[m + 2] = m ? d1(p + m, G::PZ) : lit<T>(0.0);
+      Dzr = d1(e + 2, 1);
     }
     T Fz, Fr;
     forces(q, rho, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz, Fr);
@@ -735,7 +740,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
 }
 
 template <class S, int BZ, int BR, int MODE>
-__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(
+__global__ void __launch_bounds__(NT, (MinBlocks<S, typename Store<S>::T, BZ, BR>::value)) lbm_kernel(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int toff, int parity,
     typename Store<S>::C* __restrict__ inter, size_t iplane) {
   lbm_tile<S, typename Store<S>::T, BZ, BR, MODE>(descs, tile_inst, blockIdx.x + toff, parity, inter,
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_kernel(
 // previous step (which the stream has completed), is reset for the next one.
 // No CTA waits on another.  ctr[2], ctr[3] carry the step number the same way.
 template <class S, class T, int BZ, int BR>
-__global__ void __launch_bounds__(NT, MinBlocks<S>::value) lbm_persistent(
+__global__ void __launch_bounds__(NT, (MinBlocks<S, T, BZ, BR>::value)) lbm_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
