@@ -111,12 +111,72 @@ __device__ __forceinline__ C feq_std(int i, C rho, C vz, C vr) {
   return C(aw(i)) * rho * (C(1) + C(3) * cv + C(4.5) * cv * cv - C(1.5) * (vz * vz + vr * vr));
 }
 
+// ---- shared-memory windows of the tiled transposed kernels
+// A block of ATZ x ATR threads handles the ATZ x ATR sites (k0 + tx, j0 + ty).  A
+// window holds a [Nr][P] field on rows j0 - HR .. j0 + ATR - 1 + HR and columns
+// k0 - 2 .. k0 + ATZ + 1 (wrapped in z), with the value the global accessors give
+// outside the stored rows (zero), so the transposed stencils read it exactly as
+// they would read global memory.  Blocks away from the axis and the wall load only
+// the rows their own sites' stencils reach (radius 2).
+constexpr int ATZ = 32, ATR = 8, ANT = ATZ * ATR;
+
+template <class C, int HR>
+struct Win {
+  static constexpr int W = ATZ + 4, H = ATR + 2 * HR;
+  C v[H * W];
+};
+
+template <bool PAD, class C, int HR>
+__device__ __forceinline__ void load_win(Win<C, HR>& w, const C* g, int k0, int j0, bool near_edge,
+                                         const Adj<C>& A) {
+  constexpr int W = Win<C, HR>::W;
+  const int r_lo = near_edge ? 0 : HR - 2, r_hi = near_edge ? Win<C, HR>::H : HR + ATR + 2;
+  for (int i = r_lo * W + threadIdx.x; i < r_hi * W; i += ANT) {
+    const int rr = i / W, cc = i - rr * W;
+    const int y = j0 - HR + rr, k = k0 - 2 + cc;
+    w.v[i] = PAD ? atpad(g, k, y, A) : at(g, k, y, A);
+  }
+}
+
+template <class C, int HR>
+__device__ __forceinline__ C wat(const Win<C, HR>& w, int k, int y, int k0, int j0) {
+  return w.v[(y - j0 + HR) * Win<C, HR>::W + (k - k0 + 2)];
+}
+
+// iso_t on a window (same terms in the same order as iso_t)
+template <int AX, class C, int HR>
+__device__ __forceinline__ C iso_tw(const Win<C, HR>& g, int k, int j, int k0, int j0) {
+  C s = C(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int c = AX ? acr(i) : acz(i);
+    if (c == 0) continue;
+    const C a = wat(g, k - acz(i), j - acr(i), k0, j0);
+    const C b = wat(g, k - 2 * acz(i), j - 2 * acr(i), k0, j0);
+    s += C(c) * (C(8) * a - b);
+  }
+  return s * C(1.0 / 36.0);
+}
+
 // ---- post: inverse streaming, collision and source adjoints (per real site)
 template <class C>
-__global__ void adj_post(Adj<C> A) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= A.Nz * A.Nr) return;
-  const int j = n / A.Nz, k = n - j * A.Nz;
+__global__ void __launch_bounds__(ANT) adj_post(Adj<C> A) {
+  // lambda^{n+1} on the tile + 1 (9 planes), the rows and columns every arrival
+  // site of the tile's populations lies in
+  constexpr int W = ATZ + 2, H = ATR + 2;
+  __shared__ C wl[9][H * W];
+  const int k0 = blockIdx.x * ATZ, j0 = blockIdx.y * ATR;
+  for (int i = threadIdx.x; i < H * W; i += ANT) {
+    const int rr = i / W, cc = i - rr * W;
+    const int y = j0 - 1 + rr, x = k0 - 1 + cc;
+    const bool in = y >= 0 && y < A.Nr;
+    const size_t g = in ? (size_t)y * A.P + wz(x, A.Nz) : 0;
+#pragma unroll
+    for (int d = 0; d < 9; ++d) wl[d][i] = in ? A.lam_in[d * A.plane + g] : C(0);
+  }
+  __syncthreads();
+  const int k = k0 + (int)threadIdx.x % ATZ, j = j0 + (int)threadIdx.x / ATZ;
+  if (k >= A.Nz || j >= A.Nr) return;
   const size_t o = (size_t)j * A.P + k;
   const bool noslip = A.wall == AMLBM_WALL_NOSLIP;
   C mu[9];
@@ -130,7 +190,7 @@ __global__ void adj_post(Adj<C> A) {
       if (noslip) { yk = k; yj = A.Nr - 1; d = aopp(q); }
       else { yj = A.Nr - 1; d = amirror(q); }
     }
-    mu[q] = A.lam_in[d * A.plane + (size_t)yj * A.P + wz(yk, A.Nz)];
+    mu[q] = wl[d][(yj - j0 + 1) * W + (yk - k0 + 1)];
     A.mu[q * A.plane + o] = mu[q];
   }
   const C* I = A.inter + o;
@@ -195,27 +255,36 @@ __global__ void adj_post(Adj<C> A) {
 // ---- vel: transposed gradient stencils (u ghosts folded), adjoint of u and u^eq;
 // then (same site, no neighbours) the local adjoint of F_SC and F^gamma
 template <class C>
-__global__ void adj_vel(Adj<C> A) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= A.Nz * A.Nr) return;
-  const int j = n / A.Nz, k = n - j * A.Nz;
+__global__ void __launch_bounds__(ANT) adj_vel(Adj<C> A) {
+  constexpr int HR = 5;  // ghost rows -2, -1 and Nr, Nr + 1 reach two rows further
+  __shared__ Win<C, HR> w1, w2, w3;
+  const int k0 = blockIdx.x * ATZ, j0 = blockIdx.y * ATR;
+  const int k = k0 + (int)threadIdx.x % ATZ, j = j0 + (int)threadIdx.x / ATZ;
+  if (A.axisym) {
+    const bool near_edge = j0 < 2 || j0 + ATR > A.Nr - 2;
+    load_win<false>(w1, A.g1b, k0, j0, near_edge, A);
+    load_win<false>(w2, A.g2b, k0, j0, near_edge, A);
+    load_win<false>(w3, A.g3b, k0, j0, near_edge, A);
+    __syncthreads();
+  }
+  if (k >= A.Nz || j >= A.Nr) return;
   const size_t o = (size_t)j * A.P + k;
   C uzb = A.uzb[o], urb = A.urb[o];
   if (A.axisym) {
     const C szw = A.wall == AMLBM_WALL_NOSLIP ? C(-1) : C(1);
-    uzb += iso_t<1, false>(A.g1b, k, j, A);
-    urb += iso_t<0, false>(A.g2b, k, j, A) + iso_t<1, false>(A.g3b, k, j, A);
+    uzb += iso_tw<1>(w1, k, j, k0, j0);
+    urb += iso_tw<0>(w2, k, j, k0, j0) + iso_tw<1>(w3, k, j, k0, j0);
     // ghost rows (depth 2) that mirror this row: u_z even / u_r odd at the axis;
     // at the wall u_r odd and u_z even (free-slip) or odd (no-slip)
     const int ga = -1 - j;
     if (ga >= -2) {
-      uzb += iso_t<1, false>(A.g1b, k, ga, A);
-      urb -= iso_t<0, false>(A.g2b, k, ga, A) + iso_t<1, false>(A.g3b, k, ga, A);
+      uzb += iso_tw<1>(w1, k, ga, k0, j0);
+      urb -= iso_tw<0>(w2, k, ga, k0, j0) + iso_tw<1>(w3, k, ga, k0, j0);
     }
     const int gw = 2 * A.Nr - 1 - j;
     if (gw <= A.Nr + 1) {
-      uzb += szw * iso_t<1, false>(A.g1b, k, gw, A);
-      urb -= iso_t<0, false>(A.g2b, k, gw, A) + iso_t<1, false>(A.g3b, k, gw, A);
+      uzb += szw * iso_tw<1>(w1, k, gw, k0, j0);
+      urb -= iso_tw<0>(w2, k, gw, k0, j0) + iso_tw<1>(w3, k, gw, k0, j0);
     }
   }
   const C* I = A.inter + o;
@@ -258,54 +327,77 @@ __global__ void adj_vel(Adj<C> A) {
 
 
 // ---- deriv: transposed 1D d_z (into the 1D d_r field) and isotropic d_r (into
-// the padded d_r psi field, rows -2 .. Nr+1)
+// the padded d_r psi field, rows -2 .. Nr+1); tiles of the padded rows
 template <class C>
-__global__ void adj_deriv(Adj<C> A) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= A.Nz * (A.Nr + 4)) return;
-  const int jp = n / A.Nz - 2, k = n - (jp + 2) * A.Nz;
+__global__ void __launch_bounds__(ANT) adj_deriv(Adj<C> A) {
+  __shared__ Win<C, 2> wr;             // d_rr psi adjoint, padded rows jp0 - 2 .. jp0 + ATR + 1
+  __shared__ C wd[ATR * (ATZ + 4)];    // d_zr psi adjoint, rows jp0 .. jp0 + ATR - 1
+  const int k0 = blockIdx.x * ATZ, jp0 = -2 + (int)blockIdx.y * ATR;
+  load_win<false>(wr, A.drrb, k0, jp0, true, A);
+  for (int i = threadIdx.x; i < ATR * (ATZ + 4); i += ANT) {
+    const int rr = i / (ATZ + 4), cc = i - rr * (ATZ + 4);
+    const int y = jp0 + rr;
+    wd[i] = (y >= 0 && y < A.Nr) ? A.dzrb[(size_t)y * A.P + wz(k0 - 2 + cc, A.Nz)] : C(0);
+  }
+  __syncthreads();
+  const int tx = (int)threadIdx.x % ATZ, ty = (int)threadIdx.x / ATZ;
+  const int k = k0 + tx, jp = jp0 + ty;
+  if (k >= A.Nz || jp > A.Nr + 1) return;
   if (jp >= 0 && jp < A.Nr) {
-    const C* d = A.dzrb + (size_t)jp * A.P;
-    const C e = (C(8) * (d[wz(k - 1, A.Nz)] - d[wz(k + 1, A.Nz)]) -
-                 (d[wz(k - 2, A.Nz)] - d[wz(k + 2, A.Nz)])) * C(1.0 / 12.0);
+    const C* d = wd + ty * (ATZ + 4) + tx + 2;  // column k
+    const C e = (C(8) * (d[-1] - d[1]) - (d[-2] - d[2])) * C(1.0 / 12.0);
     A.eb[(size_t)jp * A.P + k] = e;
   }
-  C v = iso_t<1, false>(A.drrb, k, jp, A);
+  C v = iso_tw<1>(wr, k, jp, k0, jp0);
   if (jp >= 0 && jp < A.Nr) v += A.drdb[(size_t)jp * A.P + k];
   A.drpb[(size_t)(jp + 2) * A.P + k] = v;
 }
 
 // psi adjoint at the (possibly ghost) position (k, y): transposed Shan-Chen
-// neighbour sum, 1D d_r and isotropic d_r.
-template <class C>
-__device__ __forceinline__ C psi_pad_adj(int k, int y, const Adj<C>& A) {
+// neighbour sum, 1D d_r and isotropic d_r, from the windows of q_z, q_r, the 1D
+// d_r adjoint e and the padded d_r psi adjoint.
+template <class C, int HR>
+__device__ __forceinline__ C psi_pad_adj(int k, int y, int k0, int j0, const Win<C, HR>& qz,
+                                         const Win<C, HR>& qr, const Win<C, HR>& eb,
+                                         const Win<C, HR>& dp, bool axisym) {
   C s = C(0);
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     const C w = C(aw(i));
-    if (acz(i)) s += w * C(acz(i)) * at(A.qz, k - acz(i), y - acr(i), A);
-    if (acr(i)) s += w * C(acr(i)) * at(A.qr, k - acz(i), y - acr(i), A);
+    if (acz(i)) s += w * C(acz(i)) * wat(qz, k - acz(i), y - acr(i), k0, j0);
+    if (acr(i)) s += w * C(acr(i)) * wat(qr, k - acz(i), y - acr(i), k0, j0);
   }
-  if (A.axisym) {
-    s += (C(8) * (at(A.eb, k, y - 1, A) - at(A.eb, k, y + 1, A)) -
-          (at(A.eb, k, y - 2, A) - at(A.eb, k, y + 2, A))) * C(1.0 / 12.0);
-    s += iso_t<1, true>(A.drpb, k, y, A);
+  if (axisym) {
+    s += (C(8) * (wat(eb, k, y - 1, k0, j0) - wat(eb, k, y + 1, k0, j0)) -
+          (wat(eb, k, y - 2, k0, j0) - wat(eb, k, y + 2, k0, j0))) * C(1.0 / 12.0);
+    s += iso_tw<1>(dp, k, y, k0, j0);
   }
   return s;
 }
 
 // ---- final: psi ghosts folded (even mirrors, depth 4), d psi / d rho, lambda^n
 template <class C>
-__global__ void adj_final(Adj<C> A) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= A.Nz * A.Nr) return;
-  const int j = n / A.Nz, k = n - j * A.Nz;
+__global__ void __launch_bounds__(ANT) adj_final(Adj<C> A) {
+  constexpr int HR = 9;  // ghost rows down to -4 and up to Nr + 3, read at distance 2
+  __shared__ Win<C, HR> wqz, wqr, web, wdp;
+  const int k0 = blockIdx.x * ATZ, j0 = blockIdx.y * ATR;
+  const int k = k0 + (int)threadIdx.x % ATZ, j = j0 + (int)threadIdx.x / ATZ;
+  const bool near_edge = j0 < 4 || j0 + ATR > A.Nr - 4;
+  load_win<false>(wqz, A.qz, k0, j0, near_edge, A);
+  load_win<false>(wqr, A.qr, k0, j0, near_edge, A);
+  if (A.axisym) {
+    load_win<false>(web, A.eb, k0, j0, near_edge, A);
+    load_win<true>(wdp, A.drpb, k0, j0, near_edge, A);
+  }
+  __syncthreads();
+  if (k >= A.Nz || j >= A.Nr) return;
   const size_t o = (size_t)j * A.P + k;
-  C pb = A.psib[o] + psi_pad_adj(k, j, A);
+  const bool ax = A.axisym != 0;
+  C pb = A.psib[o] + psi_pad_adj(k, j, k0, j0, wqz, wqr, web, wdp, ax);
   const int ga = -1 - j;
-  if (ga >= -4) pb += psi_pad_adj(k, ga, A);
+  if (ga >= -4) pb += psi_pad_adj(k, ga, k0, j0, wqz, wqr, web, wdp, ax);
   const int gw = 2 * A.Nr - 1 - j;
-  if (gw <= A.Nr + 3) pb += psi_pad_adj(k, gw, A);
+  if (gw <= A.Nr + 3) pb += psi_pad_adj(k, gw, k0, j0, wqz, wqr, web, wdp, ax);
   const C rho = A.inter[I_RHO * A.plane + o];
   const C rb = A.rhob[o] + pb * exp(-rho * A.inv_rho0);
   const C jzb = A.jzb[o], jrb = A.jrb[o];
@@ -622,33 +714,97 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
       A.accT = A.accG + plane;
       const InstDesc* d_seg = reinterpret_cast<const InstDesc*>(base + L.descs);
       const int* d_tiles = reinterpret_cast<const int*>(base + L.tiles);
-      const int nbp = (Nz * (Nr + 4) + 255) / 256;
+      const dim3 tgrid((Nz + ATZ - 1) / ATZ, (Nr + ATR - 1) / ATR);
+      const dim3 dgrid((Nz + ATZ - 1) / ATZ, (Nr + 4 + ATR - 1) / ATR);  // padded rows -2 .. Nr + 1
       C* inter_seg = reinterpret_cast<C*>(base + L.inter);
       const size_t iseg = (size_t)I_COUNT * plane;
-      int cur = 0;
-      for (int m = L.nck - 1; m >= 0; --m) {
-        const int n0 = m * p->ckpt_every, n1 = std::min(p->T, n0 + p->ckpt_every);
-        // recompute the segment's states from its checkpoint, with the
-        // intermediates of each (the last step's new state is not needed)
-        ADJ_CK(cudaMemcpyAsync(seg, ckpt + (size_t)m * L.state_elems, SB, cudaMemcpyDeviceToDevice, s));
-        for (int q = 0; q < n1 - n0; ++q)
-          ADJ_CK(launch_step_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles, inter_seg + q * iseg,
-                                   plane, s));
-        // transposed steps from the last of the segment to the first
-        for (int n = n1 - 1; n >= n0; --n) {
-          const int q = n - n0;
-          A.inter = inter_seg + q * iseg;
-          A.f = seg + (size_t)q * L.state_elems;
-          A.lam_in = lam[cur];
-          A.lam_out = lam[cur ^ 1];
-          adj_post<C><<<nb, 256, 0, s>>>(A);
-          adj_vel<C><<<nb, 256, 0, s>>>(A);
-          adj_deriv<C><<<nbp, 256, 0, s>>>(A);
-          adj_final<C><<<nb, 256, 0, s>>>(A);
-          ADJ_CK(cudaGetLastError());
-          cur ^= 1;
+      // One segment of `len` steps on stream `st`, starting with lambda in lam[c0]:
+      // the recompute (step + intermediates of every state), then the transposed
+      // steps from the last to the first.
+      auto segment = [&](int len, int c0, cudaStream_t st) -> cudaError_t {
+        Adj<C> B = A;
+        int c = c0;
+        for (int q = 0; q < len; ++q) {
+          const cudaError_t e = launch_step_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles,
+                                                  inter_seg + q * iseg, plane, st);
+          if (e != cudaSuccess) return e;
         }
+        for (int q = len - 1; q >= 0; --q) {
+          B.inter = inter_seg + q * iseg;
+          B.f = seg + (size_t)q * L.state_elems;
+          B.lam_in = lam[c];
+          B.lam_out = lam[c ^ 1];
+          adj_post<C><<<tgrid, ANT, 0, st>>>(B);
+          adj_vel<C><<<tgrid, ANT, 0, st>>>(B);
+          adj_deriv<C><<<dgrid, ANT, 0, st>>>(B);
+          adj_final<C><<<tgrid, ANT, 0, st>>>(B);
+          c ^= 1;
+        }
+        return cudaGetLastError();
+      };
+      // Every full segment issues the same launches with the same arguments (for a
+      // given starting lambda buffer), so after the first segment has run directly
+      // (kernel attributes set) one captured graph per starting buffer replays
+      // them on a private stream ordered after the checkpoint copy on s.  Any
+      // failure of the graph machinery falls back to direct launches.
+      cudaStream_t gs = nullptr;
+      cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+      cudaGraphExec_t gx[2] = {nullptr, nullptr};
+      bool use_graph = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess &&
+                       cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) == cudaSuccess &&
+                       cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) == cudaSuccess;
+      // errors inside the loop leave it (rc set) so that the graph resources below
+      // are always released
+#define SEG_CK(call)                                                                          \
+  {                                                                                           \
+    const cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                                  \
+      rc = amlbm::set_error(AMLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      break;                                                                                  \
+    }                                                                                         \
+  }
+      int cur = 0, direct_done = 0;
+      for (int m = L.nck - 1; m >= 0 && rc == AMLBM_OK; --m) {
+        const int n0 = m * p->ckpt_every, n1 = std::min(p->T, n0 + p->ckpt_every), len = n1 - n0;
+        SEG_CK(cudaMemcpyAsync(seg, ckpt + (size_t)m * L.state_elems, SB, cudaMemcpyDeviceToDevice, s));
+        bool ran = false;
+        if (use_graph && direct_done > 0 && len == p->ckpt_every) {
+          if (!gx[cur]) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+            const cudaError_t e1 = e == cudaSuccess ? segment(len, cur, gs) : e;
+            if (e == cudaSuccess) e = cudaStreamEndCapture(gs, &g);
+            if (e == cudaSuccess && e1 == cudaSuccess) e = cudaGraphInstantiate(&gx[cur], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess || e1 != cudaSuccess) {
+              use_graph = false;
+              gx[cur] = nullptr;
+              cudaGetLastError();  // the direct path below reports real errors
+            }
+          }
+          if (use_graph) {
+            SEG_CK(cudaEventRecord(ev_in, s));
+            SEG_CK(cudaStreamWaitEvent(gs, ev_in, 0));
+            SEG_CK(cudaGraphLaunch(gx[cur], gs));
+            SEG_CK(cudaEventRecord(ev_out, gs));
+            SEG_CK(cudaStreamWaitEvent(s, ev_out, 0));
+            ran = true;
+          }
+        }
+        if (!ran) {
+          SEG_CK(segment(len, cur, s));
+          ++direct_done;
+        }
+        if (len & 1) cur ^= 1;
       }
+      if (gs) cudaStreamSynchronize(gs);
+      for (auto& g : gx)
+        if (g) cudaGraphExecDestroy(g);
+      if (ev_in) cudaEventDestroy(ev_in);
+      if (ev_out) cudaEventDestroy(ev_out);
+      if (gs) cudaStreamDestroy(gs);
+#undef SEG_CK
+      if (rc) goto done;
       // parameter gradients (FP64, fixed order)
       sum2_kernel<<<L.nred, RED_NT, 0, s>>>(A.accG, A.accT, Nz, Nr, P, redbuf);
       ADJ_CK(cudaGetLastError());
