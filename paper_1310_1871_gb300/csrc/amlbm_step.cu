@@ -24,6 +24,7 @@
 
 #include <stdint.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "amlbm.h"
@@ -1085,31 +1086,49 @@ __global__ void unpack_kernel(const InstDesc* __restrict__ descs, int inst, int 
 }
 
 // ------------------------------------------------------------- launchers --
+// One-time set-up of a kernel family on each device (function attributes are
+// per device), safe when several host threads launch at once.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+  std::once_flag once[kMaxDevices];
+  cudaError_t err[kMaxDevices] = {};
+  int grid_cap[kMaxDevices] = {};
+};
+
+template <class F>
+cudaError_t once_per_device(DeviceOnce& st, F&& init, int* grid_cap = nullptr) {
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::call_once(st.once[dev], [&] { st.err[dev] = init(dev, &st.grid_cap[dev]); });
+  if (grid_cap) *grid_cap = st.grid_cap[dev];
+  return st.err[dev];
+}
+
 template <class S, class T, int BZ, int BR, int MODE>
 cudaError_t launch_t(const InstDesc* d, const int* ti, int ntiles, int toff, int parity,
                      cudaStream_t s, void* inter = nullptr, size_t iplane = 0, int* ctr = nullptr) {
   using C = typename Store<S>::C;
   constexpr size_t smem = Geo<T, BZ, BR>::bytes;
-  static bool attr = false;
-  static int grid_cap = 0;
-  if (!attr) {
+  static DeviceOnce st;
+  int grid_cap = 0;
+  const cudaError_t ie = once_per_device(st, [](int dev, int* cap) {
     cudaError_t e = cudaFuncSetAttribute(lbm_kernel<S, BZ, BR, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && MODE == 0)
       e = cudaFuncSetAttribute(lbm_persistent<S, T, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
-    if (e != cudaSuccess) return e;
-    if (MODE == 0) {
-      int dev = 0, sms = 0, per_sm = 0;
-      e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && MODE == 0) {
+      int sms = 0, per_sm = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm_persistent<S, T, BZ, BR>, NT, smem);
-      if (e != cudaSuccess) return e;
-      grid_cap = sms * (per_sm > 0 ? per_sm : 1);
+      *cap = sms * (per_sm > 0 ? per_sm : 1);
     }
-    attr = true;
-  }
+    return e;
+  }, &grid_cap);
+  if (ie != cudaSuccess) return ie;
   if (MODE == 0 && ctr && toff == 0) {
     const int grid = ntiles < grid_cap ? ntiles : grid_cap;
     lbm_persistent<S, T, BZ, BR><<<grid, NT, smem, s>>>(d, ti, ntiles, parity, ctr);
@@ -1124,16 +1143,16 @@ cudaError_t launch_split_t(const InstDesc* d, const int* ti, int ntiles, int tof
                            cudaStream_t s, int* ctr) {
   using T = typename Store<S>::T;
   constexpr size_t sa = GeoA<T, BZ, BR>::bytes, sbb = GeoB<T, BZ, BR>::bytes;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceOnce st;
+  const cudaError_t ie = once_per_device(st, [](int, int*) {
     cudaError_t e = cudaFuncSetAttribute(force_kernel<S, BZ, BR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(stream_kernel<S, BZ, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sbb);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    return e;
+  });
+  if (ie != cudaSuccess) return ie;
   force_kernel<S, BZ, BR><<<ntiles, NT, sa, s>>>(d, ti, toff, parity);
   stream_kernel<S, BZ, BR><<<ntiles, NT, sbb, s>>>(d, ti, toff, parity, ctr);
   return cudaGetLastError();
