@@ -227,18 +227,18 @@ def run_gpu(args):
         cols = [np.concatenate([np.ravel(x.make_fields()[q]) for x in inst]) for q in range(3)]
         pinned = [torch.from_numpy(c).pin_memory() for c in cols]
         host = [t.numpy() for t in pinned]
-        params = [dict(zc=x.zc, R=x.R, rho_l=x.rho_l, rho_v=x.rho_v) for x in inst]
+        params = np.array([[x.zc, x.R, x.rho_l, x.rho_v] for x in inst], dtype=np.float64)
         h2d = sum(a.nbytes for a in host)
         d2h = 64 * 16 * 8
         b.init_all(*host)
         b.step(1)
-        b.diagnostics_all(params, check=False)
+        b.diagnostics_all(params, check=False, as_array=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             b.init_all(*host)
             b.step(1)
-            b.diagnostics_all(params, check=False)
+            b.diagnostics_all(params, check=False, as_array=True)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         e2e_val = job_mlups(sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3, world)

@@ -327,21 +327,34 @@ class Batch:
         rho, uz, ur = self._flat(rho), self._flat(uz), self._flat(ur)
         _check(self.lib, self.lib.amlbm_batch_init_all(self.h, _dptr(rho), _dptr(uz), _dptr(ur)))
 
-    def diagnostics_all(self, params=None, check=True):
-        """Diagnostics of every instance in one pass (amlbm_batch_diagnostics_all);
-        params: one dict per instance with zc, R, rho_l, rho_v (None: defaults)."""
+    def diagnostics_all(self, params=None, check=True, as_array=False):
+        """Diagnostics of every instance in one pass (amlbm_batch_diagnostics_all).
+
+        params: None (defaults), one dict per instance with zc, R, rho_l, rho_v, or a
+        float64 array of shape (n, 4) in that column order.  Returns one dict per
+        instance, or with as_array=True an (n, 16) float64 array whose first columns
+        follow DIAG_FIELDS (no per-instance Python objects, for tight loops)."""
         n = len(self.specs)
         dp = None
         if params is not None:
-            dp = (DiagParams * n)()
-            for k, (s, q) in enumerate(zip(self.specs, params)):
-                zc = q.get("zc")
-                dp[k] = DiagParams(s.Nz / 2 if zc is None else float(zc), float(q.get("R", 1.0)),
-                                   float(q.get("rho_l", 2.0)), float(q.get("rho_v", 0.1)))
+            if isinstance(params, np.ndarray):
+                a = np.ascontiguousarray(params, dtype=np.float64)
+                if a.shape != (n, 4):
+                    raise ValueError(f"params array must have shape ({n}, 4)")
+                self._dp_keep = a
+                dp = (DiagParams * n).from_buffer(a)
+            else:
+                dp = (DiagParams * n)()
+                for k, (s, q) in enumerate(zip(self.specs, params)):
+                    zc = q.get("zc")
+                    dp[k] = DiagParams(s.Nz / 2 if zc is None else float(zc), float(q.get("R", 1.0)),
+                                       float(q.get("rho_l", 2.0)), float(q.get("rho_v", 0.1)))
         out = (Diag * n)()
         rc = self.lib.amlbm_batch_diagnostics_all(self.h, dp, out)
         if rc not in (OK, EUNSTABLE) or (check and rc != OK):
             _check(self.lib, rc)
+        if as_array:
+            return np.frombuffer(out, dtype=np.float64).reshape(n, -1).copy()
         return [_diag_dict(d) for d in out]
 
     def close(self):

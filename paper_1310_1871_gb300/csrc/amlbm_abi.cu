@@ -186,6 +186,10 @@ struct amlbm_batch {
   int parity = 0;
   long long sites = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // pinned host staging of the whole-batch diagnostics (jobs, then 16 doubles per
+  // instance), allocated on first use; the jobs last uploaded
+  char* pin = nullptr;
+  std::vector<amlbm::DiagJob> last_jobs;
 };
 
 struct amlbm_ctx {
@@ -499,7 +503,22 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
     col += d.Nz;
   }
   amlbm::DiagJob* d_jobs = reinterpret_cast<amlbm::DiagJob*>(b->arena + b->L.diag_jobs);
-  AMLBM_CK(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(jobs[0]), cudaMemcpyHostToDevice, b->stream));
+  const size_t jbytes = jobs.size() * sizeof(jobs[0]), rbytes = (size_t)16 * b->n * sizeof(double);
+  if (!b->pin && cudaMallocHost(reinterpret_cast<void**>(&b->pin), jbytes + rbytes) != cudaSuccess) {
+    b->pin = nullptr;  // pageable copies below
+    cudaGetLastError();
+  }
+  // a time-stepping loop asks for the same parameters every time: upload once
+  if (b->last_jobs.size() != jobs.size() || std::memcmp(b->last_jobs.data(), jobs.data(), jbytes) != 0) {
+    const void* src = jobs.data();
+    if (b->pin) {
+      std::memcpy(b->pin, jobs.data(), jbytes);
+      src = b->pin;
+    }
+    AMLBM_CK(cudaMemcpyAsync(d_jobs, src, jbytes, cudaMemcpyHostToDevice, b->stream));
+    if (!b->pin) AMLBM_CK(cudaStreamSynchronize(b->stream));  // the pageable source goes out of scope
+    b->last_jobs = jobs;
+  }
   cudaError_t e = amlbm::launch_macro(b->storage, 32, 8, b->d_desc, b->d_rb_tiles, b->L.rb_ntiles, 0,
                                       b->parity, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
@@ -508,8 +527,13 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
   double* res = reinterpret_cast<double*>(b->arena + b->L.diag_out);
   e = amlbm::launch_diag_all(b->storage, b->d_desc, d_jobs, b->n, blk, b->parity, part, cols, res, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("diag kernels: ") + cudaGetErrorString(e));
-  std::vector<double> h((size_t)16 * b->n);
-  AMLBM_CK(cudaMemcpyAsync(h.data(), res, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  std::vector<double> hv;
+  double* h = b->pin ? reinterpret_cast<double*>(b->pin + jbytes) : nullptr;
+  if (!h) {
+    hv.resize((size_t)16 * b->n);
+    h = hv.data();
+  }
+  AMLBM_CK(cudaMemcpyAsync(h, res, rbytes, cudaMemcpyDeviceToHost, b->stream));
   AMLBM_CK(cudaStreamSynchronize(b->stream));
   int first_bad = -1;
   for (int k = 0; k < b->n; ++k) {
@@ -636,6 +660,7 @@ void amlbm_batch_destroy(amlbm_batch* b) {
   else cudaDeviceSynchronize();
   for (auto& g : b->graph)
     if (g) cudaGraphExecDestroy(g);
+  if (b->pin) cudaFreeHost(b->pin);
   if (b->owns && b->arena) cudaFree(b->arena);
   delete b;
 }

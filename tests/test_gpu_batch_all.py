@@ -113,3 +113,26 @@ def test_diagnostics_all_against_oracle():
     for key in ("mass2d", "mass3d", "Eke", "umax", "a2", "A", "neck", "p_in", "p_out", "dp"):
         assert abs(d[key] - e[key]) <= 1e-10 * abs(e[key]), (key, d[key], e[key])
     b.close()
+
+
+def test_diagnostics_all_array_forms_and_repeated_calls():
+    """Parameters as an (n, 4) array and results as an (n, 16) array give the dict
+    results; repeated calls with unchanged and with changed parameters agree with the
+    per-instance call (the parameters are uploaded only when they change)."""
+    b, fields = make("bf16")
+    for k, fl in enumerate(fields):
+        b.init_fields(k, *fl)
+    b.step(30)
+    arr = np.array([[Nz / 2, Nr / 2.5, 1.93, 0.16] for Nz, Nr, _, _, _ in SPECS])
+    dicts = b.diagnostics_all([dict(zc=a[0], R=a[1], rho_l=a[2], rho_v=a[3]) for a in arr])
+    for _ in range(2):
+        res = b.diagnostics_all(arr, as_array=True)
+        for k, d in enumerate(dicts):
+            assert [res[k, m] for m in range(len(amlbm.DIAG_FIELDS))] == [d[f] for f in amlbm.DIAG_FIELDS]
+    arr2 = arr.copy()
+    arr2[:, 1] *= 1.5
+    res2 = b.diagnostics_all(arr2, as_array=True)
+    for k in range(len(SPECS)):
+        one = b.diagnostics(k, zc=arr2[k, 0], R=arr2[k, 1], rho_l=1.93, rho_v=0.16)
+        assert [res2[k, m] for m in range(len(amlbm.DIAG_FIELDS))] == [one[f] for f in amlbm.DIAG_FIELDS]
+    b.close()
