@@ -1,0 +1,73 @@
+"""The benchmark's own launch configuration and sizes.
+
+- The 64-drop sweep in the configuration `bench.py` times (BF16 storage with the local
+  shift and stochastic rounding, FP32 arithmetic, the fused persistent launch with the
+  autotuner's 26 x 16 tile): three sampled instances against the FP64 oracle.
+- The largest case the benchmark runs (the 8192 x 4096 drop, 33.5 M sites), where the
+  oracle is too slow: properties that hold at any size, in FP64 - the exact z-mirror
+  symmetry of a centred drop, the discrete mass budget sum rho(t+1) - sum rho(t) =
+  sum S(t), and agreement of two tilings bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1310_1871_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1310_1871_gb300 import amlbm  # noqa: E402
+
+
+@pytest.mark.parametrize("storage,bound", [("bf16", 2e-2), ("f32", 1e-4)])
+def test_sweep_in_bench_configuration_against_oracle(storage, bound):
+    inst = I.batch_sweep(64)
+    specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
+    b = amlbm.Batch(specs, storage=storage, tile=(26, 16), schedule="fused")
+    b.init_all(*[[x.make_fields()[q] for x in inst] for q in range(3)])
+    steps = 200
+    b.step(steps)
+    sizes = [x.Nz * x.Nr for x in inst]
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes)), 1):
+        x = inst[k]
+        o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+        ref = o.fields(o.run(o.init(*x.make_fields()), steps))["rho"]
+        rho = b.read(k)[0]
+        err = np.abs(rho / ref - 1).max()
+        print(f"{storage} instance {k} ({x.Nz}x{x.Nr}): max rel rho err {err:.2e} after {steps} steps")
+        assert err < bound, (k, err)
+    b.close()
+
+
+def test_largest_case_properties_fp64():
+    Nz, Nr, R = 8192, 4096, 1280.0
+    z = torch.arange(Nz, dtype=torch.float64, device="cuda")[None, :] - (Nz / 2 - 0.5)
+    r = torch.arange(Nr, dtype=torch.float64, device="cuda")[:, None] + 0.5
+    d = torch.sqrt(z * z + r * r)
+    ct = z / d
+    rs = R * (1.0 + 0.05 * 0.5 * (3 * ct * ct - 1))
+    rho = (I.RHO_V_G5 + 0.5 * (I.RHO_L_G5 - I.RHO_V_G5) * (1 - torch.tanh((d - rs) / 2.0))).contiguous()
+    del z, r, d, ct, rs
+    # the field is mirror-symmetric about z = Nz/2 - 1/2 (column k <-> Nz - 1 - k)
+    assert torch.equal(rho, torch.flip(rho, dims=[1]))
+    out = []
+    for tile, sched in (((26, 8), "fused"), ((32, 16), "split")):
+        b = amlbm.Batch([amlbm.InstanceSpec(Nz, Nr, 1.0, -5.0)], storage="f64", tile=tile, schedule=sched)
+        b.init_fields(0, rho.cpu().numpy())
+        d0 = b.diagnostics(0, zc=Nz / 2, R=R, rho_l=I.RHO_L_G5, rho_v=I.RHO_V_G5)
+        b.step(1)
+        d1 = b.diagnostics(0, zc=Nz / 2, R=R, rho_l=I.RHO_L_G5, rho_v=I.RHO_V_G5)
+        b.step(4)
+        rho5 = b.read(0)[0]
+        out.append(rho5)
+        b.close()
+        # discrete mass budget of the first step: the sources add sum S to sum rho
+        budget = (d1["mass2d"] - d0["mass2d"]) - d0["sumS"]
+        assert abs(budget) < 1e-9 * d0["mass2d"], budget
+        # exact mirror symmetry after 5 steps
+        assert np.array_equal(rho5, rho5[:, ::-1])
+    assert np.array_equal(out[0], out[1])
