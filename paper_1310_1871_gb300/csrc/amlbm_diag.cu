@@ -64,31 +64,37 @@ __device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr
   return double(Nr);
 }
 
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
+
 // Block blk of the nblk blocks of job J: partial sums over the sites
 // blk*NT + tid + m*nblk*NT into partials[(J.blk0 + blk) * NSUM + q], and the
 // radii of the columns blk*WARPS + warp + m*nblk*WARPS into cols[J.col0 + k].
+// The per-site terms are formed in the arithmetic type C of the storage form
+// (its values are no more precise than that) and accumulated in FP64; FP64 runs
+// at a small fraction of the FP32 rate on GB300, so there is no division or
+// square root per site (|u|^2 is max-reduced, its root taken once at the end).
+template <class C>
 __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, double* partials,
                               double* cols) {
   const int Nz = D.Nz, Nr = D.Nr, N = Nz * Nr;
-  const double two_pi = 2.0 * 3.14159265358979323846;
-  // FP64 runs at a small fraction of the FP32 rate on GB300: no division or square
-  // root per site (|u|^2 is max-reduced, its root taken once at the end)
-  const double inv_dl = 1.0 / (J.rho_l - J.rho_v);
+  const C two_pi = C(2.0 * 3.14159265358979323846);
+  const C inv_dl = C(1.0 / (J.rho_l - J.rho_v)), rho_v = C(J.rho_v), zc = C(J.zc);
   double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int n = blk * DIAG_NT + threadIdx.x; n < N; n += J.nblk * DIAG_NT) {
     const int j = n / Nz, k = n - j * Nz;
-    const double r = j + 0.5, rho = D.rho_out[n], uz = D.uz_out[n], ur = D.ur_out[n];
-    const double u2 = uz * uz + ur * ur, w = two_pi * r * rho;
-    acc[0] += rho;
-    acc[1] += w;
-    acc[2] += w * uz;
-    acc[3] += 0.5 * w * u2;
-    const double dz = k - J.zc;
-    acc[4] += two_pi * r * ((rho - J.rho_v) * inv_dl) * (dz * dz - 0.5 * r * r);
-    acc[5] += -rho * ur * __drcp_rn(r);
-    const bool bad = !(rho > 0) || !isfinite(rho) || !isfinite(u2);
+    const C r = C(j) + C(0.5), rho = C(D.rho_out[n]), uz = C(D.uz_out[n]), ur = C(D.ur_out[n]);
+    const C u2 = uz * uz + ur * ur, w = two_pi * r * rho;
+    acc[0] += double(rho);
+    acc[1] += double(w);
+    acc[2] += double(w * uz);
+    acc[3] += double(C(0.5) * w * u2);
+    const C dz = C(k) - zc;
+    acc[4] += double(two_pi * r * ((rho - rho_v) * inv_dl) * (dz * dz - C(0.5) * r * r));
+    acc[5] += double(-rho * ur * rcp_t(r));
+    const bool bad = !(rho > C(0)) || !isfinite(rho) || !isfinite(u2);
     acc[6] += bad ? 1.0 : 0.0;
-    acc[7] = fmax(acc[7], bad ? 0.0 : u2);
+    acc[7] = fmax(acc[7], bad ? 0.0 : double(u2));
   }
   __shared__ double red[DIAG_WARPS][NSUM];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -175,9 +181,10 @@ __device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, con
   }
 }
 
+template <class C>
 __global__ void __launch_bounds__(DIAG_NT) diag_partial_one(const InstDesc* __restrict__ descs, DiagJob J,
                                                             double* partials, double* cols) {
-  partial_block(descs[J.inst], J, blockIdx.x, partials, cols);
+  partial_block<C>(descs[J.inst], J, blockIdx.x, partials, cols);
 }
 
 template <class C>
@@ -189,6 +196,7 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_one(const InstDesc* __rest
 
 // Every job of a batch: block b belongs to the job whose block range
 // [blk0, blk0 + nblk) holds b (jobs sorted by blk0).
+template <class C>
 __global__ void __launch_bounds__(DIAG_NT) diag_partial_all(const InstDesc* __restrict__ descs,
                                                             const DiagJob* __restrict__ jobs, int njobs,
                                                             double* partials, double* cols) {
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(DIAG_NT) diag_partial_all(const InstDesc* __re
     else hi = mid - 1;
   }
   const DiagJob J = jobs[lo];
-  partial_block(descs[J.inst], J, blockIdx.x - J.blk0, partials, cols);
+  partial_block<C>(descs[J.inst], J, blockIdx.x - J.blk0, partials, cols);
 }
 
 template <class C>
@@ -236,11 +244,13 @@ cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr
   J.blk0 = 0;
   J.nblk = nblk;
   J.col0 = 0;
-  diag_partial_one<<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
-  if (storage == AMLBM_STORE_F64)
+  if (storage == AMLBM_STORE_F64) {
+    diag_partial_one<double><<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
     diag_final_one<double><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
-  else
+  } else {
+    diag_partial_one<float><<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
     diag_final_one<float><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
+  }
   return cudaGetLastError();
 }
 
@@ -248,11 +258,13 @@ cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_job
                             int total_blocks, int parity, double* partials, double* cols, double* out,
                             cudaStream_t s) {
   if (njobs < 1 || total_blocks < 1) return cudaErrorInvalidValue;
-  diag_partial_all<<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
-  if (storage == AMLBM_STORE_F64)
+  if (storage == AMLBM_STORE_F64) {
+    diag_partial_all<double><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
     diag_final_all<double><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
-  else
+  } else {
+    diag_partial_all<float><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
     diag_final_all<float><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
+  }
   return cudaGetLastError();
 }
 
