@@ -216,6 +216,10 @@ def run_gpu(args):
             dist.barrier()
         mlups = job_mlups(sites, args.steps, total_ms, world)
         avg_ms = total_ms / args.steps
+        # the same timed steps in five consecutive runs: median and spread of their MLUPS
+        runs = [sites * len(c) / (sum(c) * 1e-3) / 1e6 for c in np.array_split(np.array(times), 5) if len(c)]
+        five = {"median_mlups": round(float(np.median(runs)), 1), "min_mlups": round(min(runs), 1),
+                "max_mlups": round(max(runs), 1)}
         hbm, kind = peaks()
         achieved = BYTES_PER_LU[STORAGE] * sites / (avg_ms * 1e-3) / 1e9
 
@@ -294,13 +298,14 @@ def run_gpu(args):
             "scaled_hbm_cases": scaled if (rank == 0 and not args.no_compare) else None,
             "precision_vs_f64": precision if (rank == 0 and not args.no_compare) else None,
             "wall_s_timed_loop": round(wall, 3),
+            "five_runs_per_gpu": five,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def adjoint_cost(torch, T=2000):
+def adjoint_cost(torch, T=10000):
     """Cost of the discrete adjoint on the differentiable drop (512 x 128, R = 48, 16
     Legendre amplitudes, a2^2 objective, checkpoints every 100 steps), FP32 and FP64:
     wall time of amlbm_adjoint (forward with checkpoints + recomputation + reverse
