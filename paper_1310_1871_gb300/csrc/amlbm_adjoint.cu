@@ -89,22 +89,6 @@ __device__ __forceinline__ C atpad(const C* a, int k, int j, const Adj<C>& A) {
   return a[(size_t)(j + 2) * A.P + wz(k, A.Nz)];
 }
 
-// Transpose of the isotropic derivative along r (AX = 1) or z (AX = 0) at the
-// (possibly ghost) position (k, j):  sum_i c_i,AX (8 g(y - c_i) - g(y - 2 c_i)) / 36.
-template <int AX, bool PAD, class C>
-__device__ __forceinline__ C iso_t(const C* g, int k, int j, const Adj<C>& A) {
-  C s = C(0);
-#pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    const int c = AX ? acr(i) : acz(i);
-    if (c == 0) continue;
-    const C a = PAD ? atpad(g, k - acz(i), j - acr(i), A) : at(g, k - acz(i), j - acr(i), A);
-    const C b = PAD ? atpad(g, k - 2 * acz(i), j - 2 * acr(i), A) : at(g, k - 2 * acz(i), j - 2 * acr(i), A);
-    s += C(c) * (C(8) * a - b);
-  }
-  return s * C(1.0 / 36.0);
-}
-
 template <class C>
 __device__ __forceinline__ C feq_std(int i, C rho, C vz, C vr) {
   const C cv = C(acz(i)) * vz + C(acr(i)) * vr;
@@ -143,7 +127,9 @@ __device__ __forceinline__ C wat(const Win<C, HR>& w, int k, int y, int k0, int 
   return w.v[(y - j0 + HR) * Win<C, HR>::W + (k - k0 + 2)];
 }
 
-// iso_t on a window (same terms in the same order as iso_t)
+// Transpose of the isotropic derivative along r (AX = 1) or z (AX = 0) at the
+// (possibly ghost) position (k, j), on a window:
+//   sum_i c_i,AX (8 g(y - c_i) - g(y - 2 c_i)) / 36.
 template <int AX, class C, int HR>
 __device__ __forceinline__ C iso_tw(const Win<C, HR>& g, int k, int j, int k0, int j0) {
   C s = C(0);

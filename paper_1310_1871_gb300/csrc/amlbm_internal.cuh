@@ -59,13 +59,9 @@ enum InterField {
   I_RHO, I_UZ, I_UR, I_VZ, I_VR, I_FZ, I_FR, I_PSI, I_SZ, I_SR, I_DR, I_DRR, I_DZR,
   I_G1, I_G2, I_G3, I_COUNT
 };
-// Writes the intermediates of the state (f, psi) of instance 0 of d_desc, whose
-// f[0] / psi[0] hold that state, into inter (I_COUNT planes of plane elements).
-cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
-                         int ntiles, void* inter, size_t plane, cudaStream_t s);
 // The timestep of instance 0 of d_desc from f[0] / psi[0] into f[1] / psi[1]
 // (FP64 / FP32 storage, no shift) together with the intermediates of the state
-// it starts from, as launch_inter writes them.
+// it starts from (I_COUNT planes of `plane` elements of the compute type).
 cudaError_t launch_step_inter(int storage, int tz, int tr, const InstDesc* d_desc,
                               const int* d_tile_inst, int ntiles, void* inter, size_t plane,
                               cudaStream_t s);

@@ -493,10 +493,9 @@ struct MinBlocks {
 };
 
 // The fused update of one BZ x BR tile in the lane type T of the storage form.
-// MODE 0: the timestep; MODE 1 (read-back): only rho and u of the tile; MODE 2:
-// the forward intermediates of the tile for the adjoint (into `inter`, I_COUNT
-// planes of `iplane` elements); MODE 3: the timestep and the intermediates of
-// the state it starts from.
+// MODE 0: the timestep; MODE 1 (read-back): only rho and u of the tile; MODE 3:
+// the timestep and the forward intermediates of the state it starts from, for
+// the adjoint (into `inter`, I_COUNT planes of `iplane` elements).
 template <class S, class T, int BZ, int BR, int MODE>
 __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
                                          const int* __restrict__ tile_inst, int tile, int parity,
@@ -585,7 +584,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     sRho[fi] = rho;
     sUz[fi] = uz;
     sUr[fi] = ur;
-    if constexpr (MODE == 2 || MODE == 3) {
+    if constexpr (MODE == 3) {
       if (lr >= G::HF && lr < G::HF + BR && lc >= G::HF && lc < G::HF + BZ && k0 + lc - G::HF < Nz) {
         C* o = inter + (size_t)j * P + (k0 + lc - G::HF);
         o[I_RHO * iplane] = (rho).v;
@@ -665,7 +664,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       const T druz = iso_r(sUz + fi, G::FZ);
       const T dzur = iso_z(sUr + fi, G::FZ);
       const T drur = iso_r(sUr + fi, G::FZ);
-      if constexpr (MODE == 2 || MODE == 3) {
+      if constexpr (MODE == 3) {
         if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
           C* o = inter + (size_t)j * P + (k0 + lc - 1);
           o[I_G1 * iplane] = (druz).v;
@@ -673,7 +672,6 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
           o[I_G3 * iplane] = (drur).v;
         }
       }
-      if constexpr (MODE == 2) return;
       site_sources(q, sRho[fi], sUz[fi], sUr[fi], druz, dzur, drur, inv_r, S_, Hz, Hr);
       T h[9];
       sources(S_, Hz, Hr, h);
@@ -685,7 +683,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
         for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = sFs[i * G::nS + si] + h[i];
       }
     }
-    if constexpr (MODE == 2 || MODE == 3) {
+    if constexpr (MODE == 3) {
       if (!ax && lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
         C* o = inter + (size_t)j * P + (k0 + lc - 1);
         o[I_G1 * iplane] = C(0);
@@ -693,12 +691,10 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
         o[I_G3 * iplane] = C(0);
       }
     }
-    if constexpr (MODE == 2) return;
     sS[si] = S_;
     sHz[si] = Hz;
     sHr[si] = Hr;
   });
-  if constexpr (MODE == 2) return;
   __syncthreads();
 
   // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
@@ -1251,16 +1247,6 @@ cudaError_t launch_step(int storage, int sched, int tz, int tr, const InstDesc* 
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                          int toff, int parity, cudaStream_t s) {
   return dispatch_storage(storage, true, SCHED_FUSED, tz, tr, d, ti, nt, toff, parity, s, nullptr);
-}
-
-cudaError_t launch_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
-                         void* inter, size_t plane, cudaStream_t s) {
-  if (storage == AMLBM_STORE_F64) {
-    if (tz == 32 && tr == 8) return launch_t<double, D1, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
-  } else if (storage == AMLBM_STORE_F32) {
-    if (tz == 32 && tr == 8) return launch_t<float, F1, 32, 8, 2>(d, ti, nt, 0, 0, s, inter, plane);
-  }
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
