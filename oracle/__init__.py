@@ -26,8 +26,10 @@ FIELD_NAMES = ("rho jz jr psi Fsc_z Fsc_r Dr Drr Dzr Fg_z Fg_r Fz Fr uz ur ueqz 
                "druz dzur drur S Hz Hr").split()
 DIAG_NAMES = ("mass2d mass3d momz3d Eke umax a2 A neck p_in p_out dp bad sumS").split()
 
-WALL_FREESLIP, WALL_NOSLIP = 0, 1
+WALL_FREESLIP, WALL_NOSLIP, WALL_OUTLET = 0, 1, 2
 SRC_LOCAL, SRC_LINK = 0, 1
+Z_PERIODIC, Z_NOSLIP = 0, 1
+RLO_AXIS, RLO_INLET = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +46,10 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("Nz", ctypes.c_int), ("Nr", ctypes.c_int), ("tau", ctypes.c_double),
                 ("G", ctypes.c_double), ("rho0", ctypes.c_double), ("gz", ctypes.c_double),
-                ("wall", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int)]
+                ("wall", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int),
+                ("zbc", ctypes.c_int), ("rlo", ctypes.c_int), ("r_off", ctypes.c_double),
+                ("rho_out", ctypes.c_double), ("inlet_uz", ctypes.POINTER(ctypes.c_double)),
+                ("inlet_ur", ctypes.POINTER(ctypes.c_double))]
 
 
 def _load():
@@ -79,10 +84,17 @@ class Oracle:
     """One lattice (Nz x Nr) with fixed parameters; state f is float64 [9, Nr, Nz]."""
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, gz=0.0, wall=WALL_FREESLIP,
-                 axisym=1, src_mode=SRC_LOCAL):
+                 axisym=1, src_mode=SRC_LOCAL, zbc=Z_PERIODIC, rlo=RLO_AXIS, r_off=0.0,
+                 rho_out=1.0, inlet=None):
+        """inlet: (u_z, u_r) arrays of Nz values imposed on the inlet row (rlo=RLO_INLET)."""
         self.Nz, self.Nr = int(Nz), int(Nr)
+        if inlet is None:
+            inlet = (np.zeros(self.Nz), np.zeros(self.Nz))
+        # kept alive for as long as the parameter block points at them
+        self._inlet = tuple(np.ascontiguousarray(a, dtype=np.float64).reshape(self.Nz) for a in inlet)
         self.p = _Params(self.Nz, self.Nr, float(tau), float(G), float(rho0), float(gz),
-                         int(wall), int(axisym), int(src_mode))
+                         int(wall), int(axisym), int(src_mode), int(zbc), int(rlo), float(r_off),
+                         float(rho_out), _ptr(self._inlet[0]), _ptr(self._inlet[1]))
         self.lib = _load()
 
     def _c(self, rc):

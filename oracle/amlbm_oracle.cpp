@@ -17,7 +17,9 @@
 // Lattice: D2Q9 on the meridional (z, r) plane, delta t = delta z = delta r = 1
 // (Sec. II.E).  Nodes sit at z_k = k, r_j = j + 1/2, so the axis r = 0 lies
 // half-way between row 0 and its mirror row -1 (mid-grid specular reflection,
-// Sec. II.E; the drop centre (160, 0.5) of Sec. IV.2).
+// Sec. II.E; the drop centre (160, 0.5) of Sec. IV.2).  A lattice that does not
+// reach the axis (the flow between two discs of Sec. III.2, R_i <= r <= R) has
+// its rows shifted outwards: r_j = j + 1/2 + r_off.
 //
 // Memory layout of every field array: a[j * Nz + k] (row j = radial index,
 // k = axial index), populations f[i][j][k].
@@ -49,16 +51,25 @@ const double CS4 = 1.0 / 9.0;
 constexpr int MIRROR_R[Q] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
 constexpr int OPPOSITE[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
-enum { WALL_FREESLIP = 0, WALL_NOSLIP = 1 };
+enum { WALL_FREESLIP = 0, WALL_NOSLIP = 1, WALL_OUTLET = 2 };
 enum { SRC_LOCAL = 0, SRC_LINK = 1 };
+enum { Z_PERIODIC = 0, Z_NOSLIP = 1 };
+enum { RLO_AXIS = 0, RLO_INLET = 1 };
 
 template <class T>
 struct Params {
   int Nz, Nr;
   T tau, G, rho0, gz;
-  int wall;      // outer radial wall: 0 free-slip (mid-grid specular), 1 no-slip (mid-grid bounce-back)
+  int wall;      // outer radial boundary: 0 free-slip (mid-grid specular), 1 no-slip
+                 // (mid-grid bounce-back), 2 outlet (equilibrium row, see step)
   int axisym;    // 1: axisymmetric terms on; 0: planar 2D Shan-Chen (Table I "2D" columns)
   int src_mode;  // how h_i(x + c_i/2, t + 1/2) of Eq. lbm2d_mod_new is discretised (SRC_*)
+  int zbc;       // axial ends: 0 periodic, 1 no-slip walls (mid-grid bounce-back) at z = -1/2, Nz - 1/2
+  int rlo;       // lower radial boundary: 0 the axis, 1 inlet (equilibrium row, see step)
+  double r_off;  // r_j = j + 1/2 + r_off (0 with the axis)
+  double rho_out;            // density imposed on the outlet row
+  const double* inlet_uz;    // velocity imposed on the inlet row, [Nz] each
+  const double* inlet_ur;
 };
 
 // Padded scalar field with explicit ghost cells of width g on every side.
@@ -80,7 +91,26 @@ static inline int mirror_row(int j, int Nr) {
   if (j >= Nr) return 2 * Nr - 1 - j;
   return j;
 }
+// The same for any boundary: mid-grid walls and the axis mirror about the
+// half-way point, inlet and outlet rows about the boundary row itself.
+template <class T>
+static inline int ghost_row(const Params<T>& P, int j) {
+  if (j < 0) return P.rlo == RLO_INLET ? -j : -1 - j;
+  if (j >= P.Nr) return P.wall == WALL_OUTLET ? 2 * (P.Nr - 1) - j : 2 * P.Nr - 1 - j;
+  return j;
+}
+// Column of a ghost column: periodic wrap, or the mirror about a wall at
+// z = -1/2 or z = Nz - 1/2.
+template <class T>
+static inline int ghost_col(const Params<T>& P, int k) {
+  if (P.zbc == Z_PERIODIC) return wrap_z(k, P.Nz);
+  if (k < 0) return -1 - k;
+  if (k >= P.Nz) return 2 * P.Nz - 1 - k;
+  return k;
+}
 static inline double r_of(int j) { return j + 0.5; }
+template <class T>
+static inline double r_at(const Params<T>& P, int j) { return j + 0.5 + P.r_off; }
 
 // Equilibrium distribution, App. A Eq. e_distribution, to second order in the
 // velocity.  Reading: the printed equation mixes u (linear term) and u^eq
@@ -159,12 +189,14 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   }
   // 3. psi with ghost cells of depth 4: periodic in z; even mirror about the
   // axis (symmetry condition for the derivatives at the axis, Sec. II.E) and,
-  // reading, also about the outer wall.
+  // reading, also about the outer wall, the z walls, and the inlet and outlet
+  // rows (zero normal derivative there, the paper's rule for the non-axis
+  // boundaries).
   const int g = 4;
   Pad<T> ps(Nz, Nr, g);
   for (int j = -g; j < Nr + g; ++j)
     for (int k = -g; k < Nz + g; ++k)
-      ps(k, j) = M.psi[(size_t)mirror_row(j, Nr) * Nz + wrap_z(k, Nz)];
+      ps(k, j) = M.psi[(size_t)ghost_row(P, j) * Nz + ghost_col(P, k)];
 
   // 5a. Isotropic d_r psi on the real rows and on two ghost rows each side,
   // evaluated from the ghost-extended psi, and the 1D d_r psi used inside the
@@ -177,7 +209,7 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
     }
 
   for (int j = 0; j < Nr; ++j) {
-    const double r = r_of(j);
+    const double r = r_at(P, j);
     for (int k = 0; k < Nz; ++k) {
       const size_t n = (size_t)j * Nz + k;
       const T psi = ps(k, j);
@@ -224,28 +256,57 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   // 7. Velocity with ghost cells of depth 2: periodic in z; about the axis
   // u_z is even and u_r odd; at the outer wall (reading of "derivatives
   // zero", Sec. II.E: mirror ghosts by the wall's own symmetry) free-slip
-  // keeps u_z even and u_r odd, no-slip makes both odd.
+  // keeps u_z even and u_r odd, no-slip makes both odd; at the no-slip z walls
+  // both are odd.  Beyond an inlet or outlet row b the velocity continues
+  // linearly, u(b - m) = 2 u(b) - u(b + m) (reading: an open boundary with a
+  // zero derivative would halve the viscous term of a u_r ~ 1/r outflow in
+  // the rows next to it).  Ghost columns are filled first, then ghost rows
+  // from the column-extended real rows.
   Pad<T> uzp(Nz, Nr, 2), urp(Nz, Nr, 2);
-  for (int j = -2; j < Nr + 2; ++j)
+  for (int j = 0; j < Nr; ++j)
     for (int k = -2; k < Nz + 2; ++k) {
-      const int jm = mirror_row(j, Nr);
-      const size_t n = (size_t)jm * Nz + wrap_z(k, Nz);
-      double sgn_z = 1.0, sgn_r = 1.0;
-      if (j < 0) { sgn_r = -1.0; }
-      if (j >= Nr) { sgn_r = -1.0; if (P.wall == WALL_NOSLIP) sgn_z = -1.0; }
-      uzp(k, j) = sgn_z * M.uz[n];
-      urp(k, j) = sgn_r * M.ur[n];
+      const size_t n = (size_t)j * Nz + ghost_col(P, k);
+      const double sgn = (P.zbc == Z_NOSLIP && (k < 0 || k >= Nz)) ? -1.0 : 1.0;
+      uzp(k, j) = sgn * M.uz[n];
+      urp(k, j) = sgn * M.ur[n];
+    }
+  for (int m = 1; m <= 2; ++m)
+    for (int k = -2; k < Nz + 2; ++k) {
+      // below row 0
+      if (P.rlo == RLO_INLET) {
+        uzp(k, -m) = 2.0 * uzp(k, 0) - uzp(k, m);
+        urp(k, -m) = 2.0 * urp(k, 0) - urp(k, m);
+      } else {
+        uzp(k, -m) = uzp(k, m - 1);
+        urp(k, -m) = -urp(k, m - 1);
+      }
+      // beyond row Nr - 1
+      const int b = Nr - 1;
+      if (P.wall == WALL_OUTLET) {
+        uzp(k, b + m) = 2.0 * uzp(k, b) - uzp(k, b - m);
+        urp(k, b + m) = 2.0 * urp(k, b) - urp(k, b - m);
+      } else {
+        const double sgn_z = P.wall == WALL_NOSLIP ? -1.0 : 1.0;
+        uzp(k, b + m) = sgn_z * uzp(k, Nr - m);
+        urp(k, b + m) = -urp(k, Nr - m);
+      }
     }
 
   for (int j = 0; j < Nr; ++j) {
-    const double r = r_of(j);
+    const double r = r_at(P, j);
     for (int k = 0; k < Nz; ++k) {
       const size_t n = (size_t)j * Nz + k;
-      // Velocity gradients with the isotropic stencil (reading: the paper
-      // names no stencil for them).
-      const T druz = iso_d(uzp, k, j, 1);
-      const T dzur = iso_d(urp, k, j, 0);
-      const T drur = iso_d(urp, k, j, 1);
+      // Velocity gradients with the 1D fourth-order central differences of
+      // Sec. II.D (reading: the paper names no stencil for them).  The
+      // isotropic stencil is not usable here: on a mode that alternates in z
+      // its diagonal taps reverse the sign of d_r u_z, so the viscous source
+      // mu d_r u_z / r amplifies that mode next to a no-slip wall (it grows
+      // from rounding noise at tau = 1 and blows up at tau = 1.5), whereas
+      // Sec. III.1 reports a steady state whose kinetic energy is constant to
+      // machine precision.
+      const T druz = d1_r(uzp, k, j);
+      const T dzur = d1_z(urp, k, j);
+      const T drur = d1_r(urp, k, j);
       M.druz[n] = druz; M.dzur[n] = dzur; M.drur[n] = drur;
       // 8. Axisymmetric sources, Eq. condition_h and App. A
       // Eqs. corr_cty_eqn, corr_r_ns_eqn, corr_z_ns_eqn, with mu = nu rho and
@@ -287,6 +348,31 @@ static void step(const Params<T>& P, const T* f, T* fn, Macro<T>* keep) {
       fs[(size_t)i * N + n] = fi - (fi - feq(i, M.rho[n], M.ueqz[n], M.ueqr[n])) / P.tau;
       h[(size_t)i * N + n] = h_of(i, M.S[n], M.Hz[n], M.Hr[n]);
     }
+  // Inlet and outlet rows (Sec. II.E: a prescribed velocity or pressure is set
+  // by the equilibrium of the wanted density and hydrodynamic velocity,
+  // imposed before streaming).  Reading: the inlet row holds
+  // f^eq(rho of row 1, u_in(z)) (velocity prescribed, density free), the
+  // outlet row f^eq(rho_out, u of row Nr - 2) (density prescribed, the
+  // velocity leaves freely); both from the moments at time t, without source.
+  // These populations stream out of the boundary row and also become its own
+  // state at t + 1.
+  auto set_boundary_row = [&](int j, int jn, bool inlet) {
+    for (int k = 0; k < Nz; ++k) {
+      const size_t n = (size_t)j * Nz + k, nn = (size_t)jn * Nz + k;
+      const T rho = inlet ? M.rho[nn] : T(P.rho_out);
+      const T uz = inlet ? T(P.inlet_uz[k]) : M.uz[nn];
+      const T ur = inlet ? T(P.inlet_ur[k]) : M.ur[nn];
+      for (int i = 0; i < Q; ++i) {
+        fs[(size_t)i * N + n] = feq(i, rho, uz, ur);
+        h[(size_t)i * N + n] = T(0);
+      }
+    }
+  };
+  if (P.rlo == RLO_INLET) set_boundary_row(0, 1, true);
+  if (P.wall == WALL_OUTLET) set_boundary_row(Nr - 1, Nr - 2, false);
+  auto boundary_row = [&](int j) {
+    return (j == 0 && P.rlo == RLO_INLET) || (j == Nr - 1 && P.wall == WALL_OUTLET);
+  };
   // 10. Pull streaming.  Population i arriving at x left its source site
   // x_s = x - c_i in direction i' = i, except where the link crosses a wall:
   //  - axis r = 0 (mid-grid specular reflection): a population arriving at
@@ -300,11 +386,23 @@ static void step(const Params<T>& P, const T* f, T* fn, Macro<T>* keep) {
   // the oracle, grows an odd-even u_r oscillation from the axis within a few
   // thousand steps (flat interface of Table I, static drop); the
   // departure-site value is stable there.
+  //  - z walls (no-slip, mid-grid bounce-back at z = -1/2 and Nz - 1/2): a
+  //    population whose departure column lies beyond a wall left x itself in
+  //    -c_i; this takes precedence over the radial maps at the corners.
+  //  - inlet and outlet rows are not streamed into: they take their own
+  //    boundary populations.
   for (int j = 0; j < Nr; ++j)
     for (int k = 0; k < Nz; ++k)
       for (int i = 0; i < Q; ++i) {
+        if (boundary_row(j)) {
+          const size_t d = (size_t)i * N + (size_t)j * Nz + k;
+          fn[d] = fs[d];
+          continue;
+        }
         int sk = k - CZ[i], sj = j - CR[i], ii = i;
-        if (sj < 0) {
+        if (P.zbc == Z_NOSLIP && (sk < 0 || sk >= Nz)) {
+          sk = k; sj = j; ii = OPPOSITE[i];
+        } else if (sj < 0) {
           sj = 0; ii = MIRROR_R[i];
         } else if (sj >= Nr) {
           if (P.wall == WALL_NOSLIP) { sk = k; sj = Nr - 1; ii = OPPOSITE[i]; }
@@ -394,13 +492,26 @@ struct orc_params {
   int Nz, Nr;
   double tau, G, rho0, gz;
   int wall, axisym, src_mode;
+  int zbc, rlo;
+  double r_off, rho_out;
+  const double* inlet_uz;  // [Nz], read when rlo is the inlet
+  const double* inlet_ur;
 };
 
 static orc::Params<double> to_p(const orc_params* p) {
-  return {p->Nz, p->Nr, p->tau, p->G, p->rho0, p->gz, p->wall, p->axisym, p->src_mode};
+  return {p->Nz, p->Nr, p->tau, p->G, p->rho0, p->gz, p->wall, p->axisym, p->src_mode,
+          p->zbc, p->rlo, p->r_off, p->rho_out, p->inlet_uz, p->inlet_ur};
 }
+// Sizes are such that every ghost cell of depth 4 mirrors a real site.
 static int check(const orc_params* p) {
   if (!p || p->Nz < 1 || p->Nr < 4 || !(p->tau > 0.5) || !(p->rho0 > 0)) return -1;
+  if (p->wall < 0 || p->wall > 2 || p->zbc < 0 || p->zbc > 1 || p->rlo < 0 || p->rlo > 1) return -1;
+  if (p->zbc == 1 && p->Nz < 4) return -1;
+  if ((p->rlo == 1 || p->wall == 2) && p->Nr < 6) return -1;
+  if (p->rlo == 0 && p->r_off != 0.0) return -1;
+  if (!(p->r_off >= 0.0)) return -1;
+  if (p->rlo == 1 && (!p->inlet_uz || !p->inlet_ur)) return -1;
+  if (p->wall == 2 && !(p->rho_out > 0)) return -1;
   return 0;
 }
 
@@ -513,7 +624,8 @@ int orc_grad(const orc_params* p, int T, double zc, double R, double w, double r
   const int qfirst = grad ? 0 : -1, qlast = grad ? npar - 1 : -1;
   for (int q = qfirst; q <= qlast; ++q) {
     orc::Params<cplx> P{Nz, Nr, cplx(p->tau), cplx(p->G), cplx(p->rho0), cplx(p->gz),
-                        p->wall, p->axisym, p->src_mode};
+                        p->wall, p->axisym, p->src_mode, p->zbc, p->rlo, p->r_off,
+                        p->rho_out, p->inlet_uz, p->inlet_ur};
     std::vector<cplx> a(namp);
     for (int m = 0; m < namp; ++m) a[m] = cplx(amp[m]);
     if (q == 0) P.G += cplx(0, hstep);
@@ -564,7 +676,7 @@ int orc_diag(const orc_params* p, const double* f, double zc, double objR, doubl
   for (int j = 0; j < Nr; ++j)
     for (int k = 0; k < Nz; ++k) {
       const int n = j * Nz + k;
-      const double r = orc::r_of(j), rho = M.rho[n], uz = M.uz[n], ur = M.ur[n];
+      const double r = orc::r_at(P, j), rho = M.rho[n], uz = M.uz[n], ur = M.ur[n];
       const double u2 = uz * uz + ur * ur;
       out[0] += rho;
       out[1] += 2 * pi * r * rho;
@@ -583,12 +695,12 @@ int orc_diag(const orc_params* p, const double* f, double zc, double objR, doubl
     for (int j = 0; j < Nr; ++j) {
       const double rho = M.rho[(size_t)j * Nz + k];
       if (rho < mid) {
-        if (j == 0) return 0.0;
+        if (j == 0) return P.r_off;
         const double r0 = M.rho[(size_t)(j - 1) * Nz + k];
-        return orc::r_of(j - 1) + (r0 - mid) / (r0 - rho);
+        return orc::r_at(P, j - 1) + (r0 - mid) / (r0 - rho);
       }
     }
-    return (double)Nr;
+    return Nr + P.r_off;
   };
   int kc = (int)std::lround(zc);
   kc = orc::wrap_z(kc, Nz);

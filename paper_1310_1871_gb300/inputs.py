@@ -6,8 +6,8 @@ Legendre amplitudes of the differentiable drop.  It contains none of the
 method's arithmetic (no equilibrium, pseudopotential, force or streaming), so
 that both the CUDA path and the CPU oracle can consume exactly the same inputs.
 
-Arrays are float64 with shape [Nr, Nz] (row j = radial index, r_j = j + 1/2;
-column k = axial index, z_k = k).
+Arrays are float64 with shape [Nr, Nz] (row j = radial index, r_j = j + 1/2,
+or R_i + j for the flow between discs; column k = axial index, z_k = k).
 """
 from __future__ import annotations
 
@@ -129,6 +129,62 @@ def coexistence(G: float):
     p0 = brentq(area, max(pmin, p(1e-9)) + eps, pmax - eps)
     lo, hi = branches(p0)
     return hi, lo
+
+
+@dataclass
+class DiscFlow:
+    """The flow between two parallel discs of Sec. III.2: a lattice of H (z)
+    x Nr (r) sites whose rows start at the inlet radius, r_j = R_i + j
+    (r_off = R_i - 1/2), discs (no-slip walls) half a spacing beyond the first
+    and last columns, so z = k + 1/2 is the distance from the lower disc.
+    The inlet row carries Middleman's creeping-flow profile,
+    u_r(z, r) = -U_2 (4 R_i / H^2) z (z - H) / r, with
+    U_2 = u_r(H/2, R_i) = 3 Q / (4 pi R_i H) (Eq. sol-vel-test2)."""
+    H: int
+    R_i: float
+    Nr: int
+    U2: float
+
+    @property
+    def r_off(self) -> float:
+        return self.R_i - 0.5
+
+    @property
+    def z(self):
+        return np.arange(self.H, dtype=np.float64) + 0.5
+
+    @property
+    def r(self):
+        return (np.arange(self.Nr, dtype=np.float64) + self.R_i)[:, None]
+
+    @property
+    def Q(self) -> float:
+        """Volume flow rate, Q = 4 pi R_i H U_2 / 3."""
+        return 4.0 * np.pi * self.R_i * self.H * self.U2 / 3.0
+
+    def analytic(self):
+        """u_r of Middleman's solution on every site, [Nr, H]."""
+        z = self.z[None, :]
+        return -self.U2 * (4.0 * self.R_i / self.H ** 2) * z * (z - self.H) / self.r
+
+    @property
+    def u_in(self):
+        """Radial velocity imposed on the inlet row, [H]."""
+        return self.analytic()[0].copy()
+
+    def fields(self):
+        """Initial state: fluid of density 1 at rest, the inlet row already moving."""
+        rho = np.ones((self.Nr, self.H))
+        uz = np.zeros((self.Nr, self.H))
+        ur = np.zeros((self.Nr, self.H))
+        ur[0] = self.u_in
+        return rho, uz, ur
+
+
+def disc_flow(H: int = 32, R_i: float = 9.5, Nr: int = 111, U2: float = 3.93e-4) -> DiscFlow:
+    """The paper's case by default: 32 x 120 from the axis, R_i = 9.5, R = 119.5
+    (111 rows from R_i to R), Q = 0.5, U_2 = 3.93e-4."""
+    return DiscFlow(H, R_i, Nr, U2)
 
 
 @dataclass

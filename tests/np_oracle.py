@@ -4,7 +4,8 @@ on tiny grids.  It is written from the paper's equations in array form (shifted
 copies of ghost-padded fields) rather than site loops, so that a transcription
 slip in either version shows up as a disagreement.
 
-Fields are [Nr, Nz] (row = radial index, r_j = j + 1/2; column = axial index).
+Fields are [Nr, Nz] (row = radial index, r_j = j + 1/2 + r_off; column = axial
+index).
 """
 import numpy as np
 
@@ -14,20 +15,52 @@ Wt = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 CS2 = 1.0 / 3.0
 
 
-def _pad(a, g, sgn_axis=1.0, sgn_wall=1.0):
-    """Ghost-pad a [Nr, Nz] field by g: periodic in z, mirrored in r with the
-    given parity at the axis (bottom) and at the outer wall (top)."""
-    Nr, Nz = a.shape
-    out = np.empty((Nr + 2 * g, Nz + 2 * g))
-    cols = np.arange(-g, Nz + g) % Nz
+def _index_maps(Nr, Nz, g, zbc, rlo, wall):
+    """Source row / column of every cell of a field padded by g, with the kind
+    of ghost each row is: 'in' (real), 'half' (mirror about a mid-grid
+    boundary: the axis or a wall) or 'node' (mirror about an inlet or outlet
+    row)."""
+    rows, kinds = [], []
     for jj in range(-g, Nr + g):
         if jj < 0:
-            row, s = -1 - jj, sgn_axis
+            rows.append(-jj if rlo == 1 else -1 - jj)
+            kinds.append('node' if rlo == 1 else 'half')
         elif jj >= Nr:
-            row, s = 2 * Nr - 1 - jj, sgn_wall
+            rows.append(2 * (Nr - 1) - jj if wall == 2 else 2 * Nr - 1 - jj)
+            kinds.append('node' if wall == 2 else 'half')
         else:
-            row, s = jj, 1.0
-        out[jj + g] = s * a[row, cols]
+            rows.append(jj)
+            kinds.append('in')
+    ks = np.arange(-g, Nz + g)
+    if zbc == 1:
+        cols = np.where(ks < 0, -1 - ks, np.where(ks >= Nz, 2 * Nz - 1 - ks, ks))
+        colsgn = np.where((ks < 0) | (ks >= Nz), -1.0, 1.0)
+    else:
+        cols = ks % Nz
+        colsgn = np.ones(ks.size)
+    return rows, kinds, cols, colsgn
+
+
+def _pad(a, g, sgn_axis=1.0, sgn_wall=1.0, zbc=0, rlo=0, wall=0, velocity=False):
+    """Ghost-pad a [Nr, Nz] field by g.  Columns: periodic, or mirrored about the
+    z walls (a velocity changes sign there: no-slip).  Rows: mirrored with the
+    given parity about the axis (bottom) and the outer wall (top); beyond an
+    inlet or outlet row a scalar is mirrored about that row and a velocity
+    continued linearly, 2 a(b) - a(b + m)."""
+    Nr, Nz = a.shape
+    rows, kinds, cols, colsgn = _index_maps(Nr, Nz, g, zbc, rlo, wall)
+    ext = a[:, cols] * (colsgn if velocity else 1.0)  # real rows, padded columns
+    out = np.empty((Nr + 2 * g, Nz + 2 * g))
+    for t, jj in enumerate(range(-g, Nr + g)):
+        if kinds[t] == 'in':
+            out[t] = ext[jj]
+        elif kinds[t] == 'half':
+            out[t] = (sgn_axis if jj < 0 else sgn_wall) * ext[rows[t]]
+        elif velocity:
+            b = 0 if jj < 0 else Nr - 1
+            out[t] = 2 * ext[b] - ext[rows[t]]
+        else:
+            out[t] = ext[rows[t]]
     return out
 
 
@@ -47,15 +80,27 @@ def _iso(p, g, Nr, Nz, comp):
     return acc / 36.0
 
 
-def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0):
+def _d1(p, g, Nr, Nz, comp):
+    """1D 4th-order central difference along comp (0 = z, 1 = r), Sec. II.D."""
+    dz, dr = (1, 0) if comp == 0 else (0, 1)
+    return (8 * (_shift(p, g, dz, dr, Nr, Nz) - _shift(p, g, -dz, -dr, Nr, Nz))
+            - (_shift(p, g, 2 * dz, 2 * dr, Nr, Nz) - _shift(p, g, -2 * dz, -2 * dr, Nr, Nz))) / 12.0
+
+
+def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0, zbc=0, rlo=0, r_off=0.0,
+         rho_out=1.0, inlet=None):
+    """One timestep.  wall: 0 free-slip, 1 no-slip, 2 outlet row; zbc: 0
+    periodic, 1 no-slip z walls; rlo: 0 axis, 1 inlet row with velocity
+    inlet = (u_z, u_r) per column; r_j = j + 1/2 + r_off."""
     Q, Nr, Nz = f.shape
-    r = (np.arange(Nr) + 0.5)[:, None] * np.ones((1, Nz))
+    r = (np.arange(Nr) + 0.5 + r_off)[:, None] * np.ones((1, Nz))
     rho = f.sum(0)
     jz = np.tensordot(C[:, 0].astype(float), f, 1)
     jr = np.tensordot(C[:, 1].astype(float), f, 1)
     psi = rho0 * (1 - np.exp(-rho / rho0))
     gp = 6
-    P = _pad(psi, gp)
+    bc = dict(zbc=zbc, rlo=rlo, wall=wall)
+    P = _pad(psi, gp, **bc)
     # Shan-Chen force (radius-1, weighted).
     sz = sum(Wt[i] * C[i, 0] * _shift(P, gp, *C[i], Nr, Nz) for i in range(1, 9))
     sr = sum(Wt[i] * C[i, 1] * _shift(P, gp, *C[i], Nr, Nz) for i in range(1, 9))
@@ -85,11 +130,11 @@ def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0):
     vz, vr = (jz + tau * Fz) / rho, (jr + tau * Fr) / rho
     h = np.zeros_like(f)
     if axisym:
-        UZ = _pad(uz, 2, 1.0, -1.0 if wall == 1 else 1.0)
-        UR = _pad(ur, 2, -1.0, -1.0)
-        druz = _iso(UZ, 2, Nr, Nz, 1)
-        dzur = _iso(UR, 2, Nr, Nz, 0)
-        drur = _iso(UR, 2, Nr, Nz, 1)
+        UZ = _pad(uz, 2, 1.0, -1.0 if wall == 1 else 1.0, velocity=True, **bc)
+        UR = _pad(ur, 2, -1.0, -1.0, velocity=True, **bc)
+        druz = _d1(UZ, 2, Nr, Nz, 1)
+        dzur = _d1(UR, 2, Nr, Nz, 0)
+        drur = _d1(UR, 2, Nr, Nz, 1)
         mu = rho * CS2 * (tau - 0.5)
         S = -rho * ur / r
         Hz = (mu * (druz + dzur) - rho * ur * uz) / r
@@ -99,6 +144,19 @@ def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0):
     cu = C[:, 0, None, None] * vz + C[:, 1, None, None] * vr
     feq = Wt[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (vz ** 2 + vr ** 2))
     post = f - (f - feq) / tau
+    # inlet / outlet rows: the equilibrium of the imposed density and velocity,
+    # without source, is what leaves them and what they hold next
+    bnd = np.zeros(Nr, dtype=bool)
+    if rlo == 1:
+        post[:, 0] = equilibrium(rho[1:2], np.asarray(inlet[0], float)[None],
+                                 np.asarray(inlet[1], float)[None])[:, 0]
+        h[:, 0] = 0.0
+        bnd[0] = True
+    if wall == 2:
+        post[:, Nr - 1] = equilibrium(np.full((1, Nz), rho_out), uz[Nr - 2:Nr - 1],
+                                      ur[Nr - 2:Nr - 1])[:, 0]
+        h[:, Nr - 1] = 0.0
+        bnd[Nr - 1] = True
     # streaming: push every population along its link, then patch the walls
     new = np.empty_like(f)
     rev = {0: 0, 1: 3, 2: 4, 3: 1, 4: 2, 5: 7, 6: 8, 7: 5, 8: 6}
@@ -107,8 +165,13 @@ def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0):
         cz, cr = C[i]
         for j in range(Nr):
             for k in range(Nz):
+                if bnd[j]:
+                    new[i, j, k] = post[i, j, k]
+                    continue
                 sj, sk, si = j - cr, (k - cz) % Nz, i
-                if sj < 0:
+                if zbc == 1 and not 0 <= k - cz < Nz:
+                    sj, sk, si = j, k, rev[i]
+                elif sj < 0:
                     sj, si = 0, mir[i]
                 elif sj >= Nr:
                     if wall == 1:
