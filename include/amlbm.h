@@ -14,10 +14,14 @@
  *   f_i(x + c_i, t + 1) = f_i - (f_i - f^eq_i(rho, u^eq))/tau + h_i   (Eq. lbm2d_mod_new)
  * with mid-grid specular reflection on the axis, mid-grid specular (free-slip)
  * or bounce-back (no-slip) at the outer radial wall, and periodic z (Sec. II.E).
+ * Bounded domains (the flow between two discs, Sec. III.2): no-slip walls at the
+ * ends in z, an inlet row and an outlet row that hold the equilibrium of an
+ * imposed velocity or density (Sec. II.E), and rows that start off the axis.
  *
  * Lattice conventions
  *   Sites (k, j), k = 0..Nz-1 along z (z_k = k), j = 0..Nr-1 along r
- *   (r_j = j + 1/2: the axis lies half a spacing below row 0).
+ *   (r_j = j + 1/2 + r_off; with the axis r_off = 0 and the axis lies half a
+ *   spacing below row 0).
  *   Velocities (c_z, c_r): c_0 = (0,0), c_1 = (1,0), c_2 = (0,1), c_3 = (-1,0),
  *   c_4 = (0,-1), c_5 = (1,1), c_6 = (-1,1), c_7 = (-1,-1), c_8 = (1,-1).
  *   Host field arrays are float64, row-major [Nr][Nz] (a[j * Nz + k]);
@@ -53,9 +57,19 @@ extern "C" {
 #define AMLBM_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
 #define AMLBM_EUNSTABLE (-5) /* diagnostics found a non-finite or non-positive density */
 
-/* Outer radial wall (Sec. II.E). */
+/* Outer radial boundary (Sec. II.E). */
 #define AMLBM_WALL_FREESLIP 0 /* mid-grid specular reflection */
 #define AMLBM_WALL_NOSLIP 1   /* mid-grid bounce-back */
+#define AMLBM_WALL_OUTLET 2   /* outlet row: row Nr-1 holds f^eq(rho_out, u of row Nr-2) */
+
+/* Ends of the lattice in z. */
+#define AMLBM_Z_PERIODIC 0 /* periodic */
+#define AMLBM_Z_NOSLIP 1   /* mid-grid bounce-back walls at z = -1/2 and z = Nz - 1/2 */
+
+/* Lower radial boundary. */
+#define AMLBM_RLO_AXIS 0  /* the axis r = 0, half a spacing below row 0 (r_off = 0) */
+#define AMLBM_RLO_INLET 1 /* inlet row: row 0 holds f^eq(rho of row 1, u_in(z)), u_in set by
+                             amlbm_set_inlet (zero until set) */
 
 /* Discretisation of h_i(x + c_i/2, t + 1/2) in Eq. lbm2d_mod_new. */
 #define AMLBM_SRC_LOCAL 0 /* h at the departure site, time t (default) */
@@ -97,6 +111,11 @@ typedef struct amlbm_bc {
   int rounding;   /* AMLBM_ROUND_* (16-bit storage) */
   double g_z;     /* body acceleration along +z (force rho g_z), Sec. III.1 */
   double rho_ref; /* constant of AMLBM_SHIFT_GLOBAL */
+  /* Bounded domains; all zero gives the periodic lattice on the axis above. */
+  int z_bc;       /* AMLBM_Z_* */
+  int r_lo;       /* AMLBM_RLO_* */
+  double r_off;   /* r_j = j + 1/2 + r_off, r_off >= 0; must be 0 with the axis */
+  double rho_out; /* density of the outlet row (AMLBM_WALL_OUTLET), > 0 */
 } amlbm_bc;
 
 /* Parameters of the diagnostics (where to measure the drop or thread). */
@@ -136,9 +155,12 @@ size_t amlbm_workspace_bytes(int Nz, int Nr, int storage);
 /* Create a lattice of Nz x Nr sites with relaxation time tau (nu = (tau - 1/2)/3),
  * Shan-Chen coupling G and pseudopotential scale rho0.  bc may be NULL (defaults:
  * free-slip, axisymmetric, departure-site source, FP64 storage, default
- * shift, g_z = 0, rho_ref = 1).  Requires Nz >= 1, Nr >= 4, tau > 1/2, rho0 > 0, G >= -6.5
- * (the paper's stability limit is G >= -6, Sec. II.D).  cuda_stream is a
- * cudaStream_t.  workspace: see "Memory and ownership". */
+ * shift, g_z = 0, rho_ref = 1, periodic z on the axis).  Requires Nz >= 1, Nr >= 4,
+ * tau > 1/2, rho0 > 0, G >= -6.5 (the paper's stability limit is G >= -6,
+ * Sec. II.D); z walls need Nz >= 4, inlet or outlet rows Nr >= 6.  A bounded
+ * domain (z walls, inlet or outlet) runs on the fused schedule only and has no
+ * adjoint (AMLBM_EINVAL).  cuda_stream is a cudaStream_t.  workspace: see
+ * "Memory and ownership". */
 int amlbm_create(int Nz, int Nr, double tau, double G, double rho0, const amlbm_bc* bc,
                  void* cuda_stream, void* workspace, size_t workspace_bytes, amlbm_ctx** out);
 
@@ -148,6 +170,13 @@ int amlbm_init_fields(amlbm_ctx* ctx, const double* rho, const double* uz, const
 /* The same from device float64 arrays [Nr][Nz] (uz, ur may be NULL). */
 int amlbm_init_fields_device(amlbm_ctx* ctx, const double* rho, const double* uz,
                              const double* ur);
+
+/* Velocity of the inlet row (AMLBM_RLO_INLET): host arrays of Nz values, the
+ * hydrodynamic u_z and u_r imposed at column k (Sec. II.E; for the flow between
+ * discs, Middleman's profile at r = R_i, Sec. III.2).  Copied on the context's
+ * stream; takes effect from the next step.  AMLBM_EINVAL if the lattice has no
+ * inlet. */
+int amlbm_set_inlet(amlbm_ctx* ctx, const double* uz, const double* ur);
 
 /* Enqueue n timesteps (n >= 0) on the context's stream. */
 int amlbm_step(amlbm_ctx* ctx, int n);
@@ -261,7 +290,8 @@ typedef struct amlbm_instance {
 #define AMLBM_SCHED_SPLIT 2
 
 /* Schedule and tile shape (sites along z x sites along r) of the step kernels;
- * all zero lets the library choose. */
+ * all zero lets the library choose.  A tile given with AMLBM_SCHED_AUTO runs on
+ * the split schedule, or on the fused one if any instance is a bounded domain. */
 typedef struct amlbm_tune {
   int tile_z, tile_r;
   int graph_chunk; /* steps per captured CUDA graph in amlbm_batch_step (0 = no graph) */
@@ -302,6 +332,8 @@ int amlbm_batch_create(int n, const amlbm_instance* inst, const amlbm_tune* tune
                        amlbm_batch** out);
 int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const double* uz,
                             const double* ur);
+/* amlbm_set_inlet for instance k. */
+int amlbm_batch_set_inlet(amlbm_batch* b, int k, const double* uz, const double* ur);
 int amlbm_batch_step(amlbm_batch* b, int n);
 int amlbm_batch_read(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double* f);
 int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* out);

@@ -20,7 +20,9 @@ _lib = None
 _lock = threading.Lock()
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -5
-WALL = {"freeslip": 0, "noslip": 1}
+WALL = {"freeslip": 0, "noslip": 1, "outlet": 2}
+Z_BC = {"periodic": 0, "noslip": 1}
+R_LO = {"axis": 0, "inlet": 1}
 SRC = {"local": 0, "link": 1}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 SHIFT = {"default": 0, "none": 1, "global": 2, "local": 3, "equilibrium": 4}
@@ -38,7 +40,9 @@ class AmlbmError(RuntimeError):
 class BC(ctypes.Structure):
     _fields_ = [("wall_r", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int),
                 ("storage", ctypes.c_int), ("shift", ctypes.c_int), ("rounding", ctypes.c_int),
-                ("g_z", ctypes.c_double), ("rho_ref", ctypes.c_double)]
+                ("g_z", ctypes.c_double), ("rho_ref", ctypes.c_double),
+                ("z_bc", ctypes.c_int), ("r_lo", ctypes.c_int), ("r_off", ctypes.c_double),
+                ("rho_out", ctypes.c_double)]
 
 
 class DiagParams(ctypes.Structure):
@@ -86,7 +90,7 @@ EXPORTS = [
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
     "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
     "amlbm_objective", "amlbm_batch_config", "amlbm_batch_init_all", "amlbm_batch_diagnostics_all",
-    "amlbm_autotune",
+    "amlbm_autotune", "amlbm_set_inlet", "amlbm_batch_set_inlet",
 ]
 
 
@@ -109,6 +113,7 @@ def load(build_if_missing: bool = True):
         lib.amlbm_create.argtypes = [ip, ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.POINTER(BC), vp, vp, sz, ctypes.POINTER(vp)]
         lib.amlbm_init_fields.argtypes = [vp, dp, dp, dp]
+        lib.amlbm_set_inlet.argtypes = [vp, dp, dp]
         lib.amlbm_init_fields_device.argtypes = [vp, vp, vp, vp]
         lib.amlbm_step.argtypes = [vp, ip]
         lib.amlbm_read_fields.argtypes = [vp, dp, dp, dp, dp]
@@ -124,6 +129,7 @@ def load(build_if_missing: bool = True):
         lib.amlbm_batch_create.argtypes = [ip, ctypes.POINTER(InstanceC), ctypes.POINTER(Tune), vp, vp,
                                            sz, ctypes.POINTER(vp)]
         lib.amlbm_batch_init_fields.argtypes = [vp, ip, dp, dp, dp]
+        lib.amlbm_batch_set_inlet.argtypes = [vp, ip, dp, dp]
         lib.amlbm_batch_step.argtypes = [vp, ip]
         lib.amlbm_batch_read.argtypes = [vp, ip, dp, dp, dp, dp]
         lib.amlbm_batch_diagnostics.argtypes = [vp, ip, ctypes.POINTER(DiagParams), ctypes.POINTER(Diag)]
@@ -173,13 +179,16 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream), s
 
 
+def _code(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
 def make_bc(wall="freeslip", axisym=True, src="local", storage="f64", gz=0.0, rho_ref=1.0,
-            shift="default", rounding="default") -> BC:
-    return BC(WALL[wall] if isinstance(wall, str) else int(wall), int(bool(axisym)),
-              SRC[src] if isinstance(src, str) else int(src),
-              STORAGE[storage] if isinstance(storage, str) else int(storage),
-              SHIFT[shift] if isinstance(shift, str) else int(shift),
-              ROUNDING[rounding] if isinstance(rounding, str) else int(rounding), float(gz), float(rho_ref))
+            shift="default", rounding="default", z_bc="periodic", r_lo="axis", r_off=0.0,
+            rho_out=1.0) -> BC:
+    return BC(_code(WALL, wall), int(bool(axisym)), _code(SRC, src), _code(STORAGE, storage),
+              _code(SHIFT, shift), _code(ROUNDING, rounding), float(gz), float(rho_ref),
+              _code(Z_BC, z_bc), _code(R_LO, r_lo), float(r_off), float(rho_out))
 
 
 def _diag_dict(d: Diag) -> dict:
@@ -201,6 +210,10 @@ class InstanceSpec:
     rho_ref: float = 1.0
     shift: str = "default"
     rounding: str = "default"
+    z_bc: str = "periodic"
+    r_lo: str = "axis"
+    r_off: float = 0.0
+    rho_out: float = 1.0
 
 
 def instances_c(specs, storage):
@@ -210,7 +223,7 @@ def instances_c(specs, storage):
     for i, s in enumerate(specs):
         arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
                            make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift,
-                                   s.rounding))
+                                   s.rounding, s.z_bc, s.r_lo, s.r_off, s.rho_out))
     return arr
 
 
@@ -284,6 +297,12 @@ class Batch:
         shp = (s.Nr, s.Nz)
         rho, uz, ur = _host(rho, shp), _host(uz, shp), _host(ur, shp)
         _check(self.lib, self.lib.amlbm_batch_init_fields(self.h, k, _dptr(rho), _dptr(uz), _dptr(ur)))
+
+    def set_inlet(self, k, uz, ur):
+        """Velocity of instance k's inlet row, arrays of Nz values (r_lo="inlet")."""
+        n = self.specs[k].Nz
+        uz, ur = _host(uz, (n,)), _host(ur, (n,))
+        _check(self.lib, self.lib.amlbm_batch_set_inlet(self.h, k, _dptr(uz), _dptr(ur)))
 
     def step(self, n=1):
         _check(self.lib, self.lib.amlbm_batch_step(self.h, int(n)))
@@ -373,13 +392,14 @@ class Lattice:
     """One Nz x Nr lattice (amlbm_ctx)."""
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, wall="freeslip", axisym=True, src="local",
-                 storage="f64", gz=0.0, rho_ref=1.0, shift="default", rounding="default", stream=None):
+                 storage="f64", gz=0.0, rho_ref=1.0, shift="default", rounding="default", stream=None,
+                 z_bc="periodic", r_lo="axis", r_off=0.0, rho_out=1.0):
         import torch
         self.lib = load()
         if not torch.cuda.is_available():
             raise RuntimeError("amlbm needs a CUDA device")
         self.Nz, self.Nr = int(Nz), int(Nr)
-        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift, rounding)
+        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift, rounding, z_bc, r_lo, r_off, rho_out)
         nbytes = self.lib.amlbm_workspace_bytes(self.Nz, self.Nr, bc.storage)
         if nbytes == 0:
             raise AmlbmError(EINVAL, "bad lattice size or storage")
@@ -397,6 +417,11 @@ class Lattice:
         shp = (self.Nr, self.Nz)
         rho, uz, ur = _host(rho, shp), _host(uz, shp), _host(ur, shp)
         _check(self.lib, self.lib.amlbm_init_fields(self.h, _dptr(rho), _dptr(uz), _dptr(ur)))
+
+    def set_inlet(self, uz, ur):
+        """Velocity of the inlet row (r_lo="inlet"), arrays of Nz values."""
+        uz, ur = _host(uz, (self.Nz,)), _host(ur, (self.Nz,))
+        _check(self.lib, self.lib.amlbm_set_inlet(self.h, _dptr(uz), _dptr(ur)))
 
     def init_fields_device(self, rho, uz=None, ur=None):
         """rho, uz, ur: contiguous float64 CUDA tensors [Nr, Nz] (uz, ur optional)."""

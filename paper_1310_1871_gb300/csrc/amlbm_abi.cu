@@ -51,7 +51,16 @@ amlbm_bc default_bc() {
   b.rounding = AMLBM_ROUND_DEFAULT;
   b.g_z = 0.0;
   b.rho_ref = 1.0;
+  b.z_bc = AMLBM_Z_PERIODIC;
+  b.r_lo = AMLBM_RLO_AXIS;
+  b.r_off = 0.0;
+  b.rho_out = 1.0;
   return b;
+}
+
+// A lattice with walls in z, an inlet or an outlet (the fused schedule only).
+bool bounded(const amlbm_bc& bc) {
+  return bc.z_bc != AMLBM_Z_PERIODIC || bc.r_lo != AMLBM_RLO_AXIS || bc.wall_r == AMLBM_WALL_OUTLET;
 }
 
 // Schedule and tile when the caller gives none (fastest on the 64-drop sweep on
@@ -61,11 +70,15 @@ amlbm_bc default_bc() {
 // recomputation).
 void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched, int* tz, int* tr) {
   static const int pref64[][2] = {{32, 16}, {32, 8}, {32, 8}};
+  static const int pref64f[][2] = {{32, 8}, {32, 8}, {32, 8}};  // fused, for bounded lattices
   static const int pref32[][2] = {{26, 16}, {64, 8}, {32, 8}};
+  bool any_bounded = false;
+  for (const auto& I : inst) any_bounded = any_bounded || bounded(I.bc);
   const bool f64 = storage == AMLBM_STORE_F64;
-  *sched = f64 ? amlbm::SCHED_SPLIT : amlbm::SCHED_FUSED;
+  const int(*pref)[2] = f64 ? (any_bounded ? pref64f : pref64) : pref32;
+  *sched = f64 && !any_bounded ? amlbm::SCHED_SPLIT : amlbm::SCHED_FUSED;
   for (int c = 0; c < 3; ++c) {
-    const int z = f64 ? pref64[c][0] : pref32[c][0], r = f64 ? pref64[c][1] : pref32[c][1];
+    const int z = pref[c][0], r = pref[c][1];
     long long tiles = 0;
     for (const auto& I : inst) tiles += (long long)((I.Nz + z - 1) / z) * ((I.Nr + r - 1) / r);
     if (tiles >= 2 * 152) { *tz = z; *tr = r; return; }
@@ -98,8 +111,20 @@ int validate(const amlbm_instance& I, int idx) {
   if (!(I.rho0 > 0) || !std::isfinite(I.rho0)) return fail(AMLBM_EINVAL, w + "rho0 must be positive");
   if (!(I.G >= -6.5) || !std::isfinite(I.G))
     return fail(AMLBM_EINVAL, w + "G below -6.5 (the Shan-Chen model is unstable beyond G ~ -6)");
-  if (I.bc.wall_r != AMLBM_WALL_FREESLIP && I.bc.wall_r != AMLBM_WALL_NOSLIP)
+  if (I.bc.wall_r != AMLBM_WALL_FREESLIP && I.bc.wall_r != AMLBM_WALL_NOSLIP &&
+      I.bc.wall_r != AMLBM_WALL_OUTLET)
     return fail(AMLBM_EINVAL, w + "bad wall_r");
+  if (I.bc.z_bc != AMLBM_Z_PERIODIC && I.bc.z_bc != AMLBM_Z_NOSLIP) return fail(AMLBM_EINVAL, w + "bad z_bc");
+  if (I.bc.r_lo != AMLBM_RLO_AXIS && I.bc.r_lo != AMLBM_RLO_INLET) return fail(AMLBM_EINVAL, w + "bad r_lo");
+  if (!(I.bc.r_off >= 0.0) || !std::isfinite(I.bc.r_off) || I.bc.r_off > 1e6)
+    return fail(AMLBM_EINVAL, w + "r_off must be finite, >= 0 and <= 1e6");
+  if (I.bc.r_lo == AMLBM_RLO_AXIS && I.bc.r_off != 0.0)
+    return fail(AMLBM_EINVAL, w + "a lattice on the axis has r_off = 0");
+  if (I.bc.wall_r == AMLBM_WALL_OUTLET && (!(I.bc.rho_out > 0) || !std::isfinite(I.bc.rho_out)))
+    return fail(AMLBM_EINVAL, w + "the outlet density rho_out must be positive and finite");
+  if (I.bc.z_bc == AMLBM_Z_NOSLIP && I.Nz < 4) return fail(AMLBM_EINVAL, w + "z walls need Nz >= 4");
+  if ((I.bc.r_lo == AMLBM_RLO_INLET || I.bc.wall_r == AMLBM_WALL_OUTLET) && I.Nr < 6)
+    return fail(AMLBM_EINVAL, w + "inlet or outlet rows need Nr >= 6");
   if (I.bc.axisym != 0 && I.bc.axisym != 1) return fail(AMLBM_EINVAL, w + "axisym must be 0 or 1");
   if (I.bc.src_mode != AMLBM_SRC_LOCAL && I.bc.src_mode != AMLBM_SRC_LINK)
     return fail(AMLBM_EINVAL, w + "bad src_mode");
@@ -120,7 +145,7 @@ struct Layout {
   size_t total = 0;
   size_t desc = 0, tiles = 0, rb_tiles = 0, ctr = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
          unpack = 0, site_off = 0, diag_jobs = 0;
-  std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur;
+  std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur, inlet;
   int ntiles = 0, rb_ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
   int all_nblk = 0;  // partial-sum blocks of a diagnostics pass over every instance
   long long sumN = 0, sumNz = 0;
@@ -163,6 +188,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
     L.rho.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
     L.uz.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
     L.ur.push_back(take((size_t)I.Nz * I.Nr * sizeof(double)));
+    L.inlet.push_back(take((size_t)2 * I.Nz * sizeof(double)));
   }
   L.total = o;
   return L;
@@ -245,9 +271,15 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   if (tune && (tune->tile_z || tune->tile_r || tune->schedule)) {
     tz = tune->tile_z;
     tr = tune->tile_r;
-    sched = tune->schedule ? tune->schedule : AMLBM_SCHED_SPLIT;
+    bool any_bounded = false;
+    for (const auto& I : inst) any_bounded = any_bounded || bounded(I.bc);
+    sched = tune->schedule ? tune->schedule : (any_bounded ? AMLBM_SCHED_FUSED : AMLBM_SCHED_SPLIT);
     if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT)
       return fail(AMLBM_EINVAL, "bad schedule");
+    if (sched == AMLBM_SCHED_SPLIT)
+      for (const auto& I : inst)
+        if (bounded(I.bc))
+          return fail(AMLBM_EINVAL, "the split schedule takes periodic lattices on the axis only");
     if (!tz && !tr) {
       int s2;
       pick_tile(storage, inst, &s2, &tz, &tr);
@@ -303,6 +335,8 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.axisym = I.bc.axisym;
     d.src = I.bc.src_mode;
     d.shift = resolve_shift(I.bc);
+    d.zbc = I.bc.z_bc;
+    d.rlo = I.bc.r_lo;
     // 1 = stochastic rounding of the 16-bit stores.  Default: stochastic for BF16
     // with the W_i s shifts (measured: an order of magnitude more accurate there),
     // to nearest for FP16 and for the equilibrium shift (no gain measured)
@@ -321,9 +355,10 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.rho0 = I.rho0;
     d.gz = I.bc.g_z;
     d.rho_ref = I.bc.rho_ref;
-    const double k[9] = {I.tau, 1.0 / I.tau, -I.G, -I.G / 18.0, I.bc.g_z, I.rho0, 1.0 / I.rho0,
-                         (I.tau - 0.5) / 3.0, I.bc.rho_ref};
-    for (int c = 0; c < 9; ++c) {
+    const double k[11] = {I.tau, 1.0 / I.tau, -I.G, -I.G / 18.0, I.bc.g_z, I.rho0, 1.0 / I.rho0,
+                          (I.tau - 0.5) / 3.0, I.bc.rho_ref, I.bc.r_off + 0.5,
+                          I.bc.wall_r == AMLBM_WALL_OUTLET ? I.bc.rho_out : 1.0};
+    for (int c = 0; c < 11; ++c) {
       d.k64[c] = k[c];
       d.k32[c] = (float)k[c];
     }
@@ -335,6 +370,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.rho_out = reinterpret_cast<double*>(b->arena + L.rho[i]);
     d.uz_out = reinterpret_cast<double*>(b->arena + L.uz[i]);
     d.ur_out = reinterpret_cast<double*>(b->arena + L.ur[i]);
+    d.inlet = reinterpret_cast<const double*>(b->arena + L.inlet[i]);
     for (int t = 0; t < d.tiles_z * d.tiles_r; ++t) tiles.push_back(i);
     for (int t = 0; t < d.rb_tiles_z * d.rb_tiles_r; ++t) rb_tiles.push_back(i);
     b->desc.push_back(d);
@@ -354,6 +390,8 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     e = cudaMemcpyAsync(b->d_rb_tiles, rb_tiles.data(), rb_tiles.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 5 * sizeof(int), b->stream);
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(b->arena + L.inlet[i], 0, (size_t)2 * inst[i].Nz * sizeof(double), b->stream);
   std::vector<long long> off(b->n + 1, 0);
   for (int i = 0; i < b->n; ++i) off[i + 1] = off[i] + (long long)inst[i].Nz * inst[i].Nr;
   if (e == cudaSuccess)
@@ -400,6 +438,23 @@ int init_host(amlbm_batch* b, int k, const double* rho, const double* uz, const 
   if (ur) AMLBM_CK(cudaMemcpyAsync(st + 2 * N, ur, N * sizeof(double), cudaMemcpyHostToDevice, b->stream));
   rc = init_device(b, k, st, uz ? st + N : nullptr, ur ? st + 2 * N : nullptr);
   if (rc) return rc;
+  AMLBM_CK(cudaStreamSynchronize(b->stream));
+  return AMLBM_OK;
+}
+
+int set_inlet(amlbm_batch* b, int k, const double* uz, const double* ur) {
+  int rc = check_k(b, k);
+  if (rc) return rc;
+  const InstDesc& d = b->desc[k];
+  if (d.rlo != AMLBM_RLO_INLET) return fail(AMLBM_EINVAL, "the lattice has no inlet row");
+  if (!uz || !ur) return fail(AMLBM_EINVAL, "uz and ur must not be NULL");
+  for (int q = 0; q < d.Nz; ++q)
+    if (!std::isfinite(uz[q]) || !std::isfinite(ur[q]))
+      return fail(AMLBM_EINVAL, "inlet velocities must be finite");
+  double* dst = const_cast<double*>(d.inlet);
+  AMLBM_CK(cudaMemcpyAsync(dst, uz, d.Nz * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  AMLBM_CK(cudaMemcpyAsync(dst + d.Nz, ur, d.Nz * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  // the host arrays are the caller's again when the call returns
   AMLBM_CK(cudaStreamSynchronize(b->stream));
   return AMLBM_OK;
 }
@@ -609,6 +664,10 @@ int amlbm_batch_init_fields(amlbm_batch* b, int k, const double* rho, const doub
   return init_host(b, k, rho, uz, ur);
 }
 
+int amlbm_batch_set_inlet(amlbm_batch* b, int k, const double* uz, const double* ur) {
+  return set_inlet(b, k, uz, ur);
+}
+
 int amlbm_batch_step(amlbm_batch* b, int n) {
   if (!b) return fail(AMLBM_EINVAL, "NULL batch");
   if (n < 0) return fail(AMLBM_EINVAL, "n must be >= 0");
@@ -707,6 +766,11 @@ int amlbm_init_fields_device(amlbm_ctx* c, const double* rho, const double* uz, 
   if (!c) return fail(AMLBM_EINVAL, "NULL context");
   if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
   return init_device(c->b, 0, rho, uz, ur);
+}
+
+int amlbm_set_inlet(amlbm_ctx* c, const double* uz, const double* ur) {
+  if (!c) return fail(AMLBM_EINVAL, "NULL context");
+  return set_inlet(c->b, 0, uz, ur);
 }
 
 int amlbm_step(amlbm_ctx* c, int n) {

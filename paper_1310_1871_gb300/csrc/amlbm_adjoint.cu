@@ -144,6 +144,18 @@ __device__ __forceinline__ C iso_tw(const Win<C, HR>& g, int k, int j, int k0, i
   return s * C(1.0 / 36.0);
 }
 
+// Transpose of the 1D 4th-order difference along r (AX = 1) or z (AX = 0) at the
+// (possibly ghost) position (k, j), on a window.  The forward operator
+// (8 (g(y + e) - g(y - e)) - (g(y + 2e) - g(y - 2e))) / 12 is antisymmetric, so
+// its transpose is its negative.
+template <int AX, class C, int HR>
+__device__ __forceinline__ C d1_tw(const Win<C, HR>& g, int k, int j, int k0, int j0) {
+  const int ez = AX ? 0 : 1, er = AX ? 1 : 0;
+  const C a = wat(g, k + ez, j + er, k0, j0) - wat(g, k - ez, j - er, k0, j0);
+  const C b = wat(g, k + 2 * ez, j + 2 * er, k0, j0) - wat(g, k - 2 * ez, j - 2 * er, k0, j0);
+  return -(C(8) * a - b) * C(1.0 / 12.0);
+}
+
 // ---- post: inverse streaming, collision and source adjoints (per real site)
 template <class C>
 __global__ void __launch_bounds__(ANT) adj_post(Adj<C> A) {
@@ -258,19 +270,19 @@ __global__ void __launch_bounds__(ANT) adj_vel(Adj<C> A) {
   C uzb = A.uzb[o], urb = A.urb[o];
   if (A.axisym) {
     const C szw = A.wall == AMLBM_WALL_NOSLIP ? C(-1) : C(1);
-    uzb += iso_tw<1>(w1, k, j, k0, j0);
-    urb += iso_tw<0>(w2, k, j, k0, j0) + iso_tw<1>(w3, k, j, k0, j0);
+    uzb += d1_tw<1>(w1, k, j, k0, j0);
+    urb += d1_tw<0>(w2, k, j, k0, j0) + d1_tw<1>(w3, k, j, k0, j0);
     // ghost rows (depth 2) that mirror this row: u_z even / u_r odd at the axis;
     // at the wall u_r odd and u_z even (free-slip) or odd (no-slip)
     const int ga = -1 - j;
     if (ga >= -2) {
-      uzb += iso_tw<1>(w1, k, ga, k0, j0);
-      urb -= iso_tw<0>(w2, k, ga, k0, j0) + iso_tw<1>(w3, k, ga, k0, j0);
+      uzb += d1_tw<1>(w1, k, ga, k0, j0);
+      urb -= d1_tw<0>(w2, k, ga, k0, j0) + d1_tw<1>(w3, k, ga, k0, j0);
     }
     const int gw = 2 * A.Nr - 1 - j;
     if (gw <= A.Nr + 1) {
-      uzb += szw * iso_tw<1>(w1, k, gw, k0, j0);
-      urb -= iso_tw<0>(w2, k, gw, k0, j0) + iso_tw<1>(w3, k, gw, k0, j0);
+      uzb += szw * d1_tw<1>(w1, k, gw, k0, j0);
+      urb -= d1_tw<0>(w2, k, gw, k0, j0) + d1_tw<1>(w3, k, gw, k0, j0);
     }
   }
   const C* I = A.inter + o;
@@ -561,6 +573,8 @@ int check_problem(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem* p) {
   if (ci.storage != AMLBM_STORE_F64 && ci.storage != AMLBM_STORE_F32)
     return set_error(AMLBM_EINVAL, "the adjoint needs FP64 or FP32 storage");
   if (ci.host.shift != 0) return set_error(AMLBM_EINVAL, "the adjoint needs unshifted storage");
+  if (ci.host.zbc != AMLBM_Z_PERIODIC || ci.host.rlo != AMLBM_RLO_AXIS || ci.host.wall == AMLBM_WALL_OUTLET)
+    return set_error(AMLBM_EINVAL, "the adjoint takes periodic lattices on the axis only");
   if (ci.host.src != AMLBM_SRC_LOCAL)
     return set_error(AMLBM_EINVAL, "the adjoint implements the departure-site source only");
   if (p->T < 1 || p->ckpt_every < 1) return set_error(AMLBM_EINVAL, "need T >= 1, ckpt_every >= 1");

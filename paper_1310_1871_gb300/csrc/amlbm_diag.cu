@@ -2,7 +2,7 @@
 // interface radius of every column, for one instance or for every instance of
 // a batch in the same three launches.
 //
-// Quantities (r = j + 1/2 is the node radius, sums over real sites):
+// Quantities (r = j + 1/2 + r_off is the node radius, sums over real sites):
 //   mass2d = sum rho, mass3d = sum 2 pi r rho (the volume integral of the
 //   axisymmetric density, Sec. II.A), momz3d = sum 2 pi r rho u_z,
 //   E_ke = pi sum r rho |u|^2 (the kinetic energy whose constancy marks the
@@ -45,10 +45,12 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
-// Interface radius of column k, one warp: the first row (from the axis) whose
-// density is below mid, interpolated linearly against the row before it; 0 when
-// row 0 is already below, Nr when no row is.  Rows are scanned 32 at a time.
-__device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr, int k, double mid) {
+// Interface radius of column k, one warp: the first row (from row 0) whose
+// density is below mid, interpolated linearly against the row before it; r0 - 1/2
+// (the axis, or the lattice's inner edge) when row 0 is already below, Nr + r0 - 1/2
+// when no row is.  r0 is the radius of row 0.  Rows are scanned 32 at a time.
+__device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr, int k, double mid,
+                                  double r0) {
   const int lane = threadIdx.x & 31;
   for (int j0 = 0; j0 < Nr; j0 += 32) {
     const int j = j0 + lane;
@@ -56,12 +58,12 @@ __device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr
     const unsigned m = __ballot_sync(0xffffffffu, below);
     if (m) {
       const int jf = j0 + __ffs(m) - 1;
-      if (jf == 0) return 0.0;
+      if (jf == 0) return r0 - 0.5;
       const double v0 = rho[(size_t)(jf - 1) * Nz + k], v = rho[(size_t)jf * Nz + k];
-      return (jf - 1 + 0.5) + (v0 - mid) / (v0 - v);
+      return (jf - 1 + r0) + (v0 - mid) / (v0 - v);
     }
   }
-  return double(Nr);
+  return Nr + r0 - 0.5;
 }
 
 __device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
@@ -80,10 +82,11 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   const int Nz = D.Nz, Nr = D.Nr, N = Nz * Nr;
   const C two_pi = C(2.0 * 3.14159265358979323846);
   const C inv_dl = C(1.0 / (J.rho_l - J.rho_v)), rho_v = C(J.rho_v), zc = C(J.zc);
+  const C r0 = sizeof(C) == 8 ? C(D.k64[K_R0]) : C(D.k32[K_R0]);
   double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int n = blk * DIAG_NT + threadIdx.x; n < N; n += J.nblk * DIAG_NT) {
     const int j = n / Nz, k = n - j * Nz;
-    const C r = C(j) + C(0.5), rho = C(D.rho_out[n]), uz = C(D.uz_out[n]), ur = C(D.ur_out[n]);
+    const C r = C(j) + r0, rho = C(D.rho_out[n]), uz = C(D.uz_out[n]), ur = C(D.ur_out[n]);
     const C u2 = uz * uz + ur * ur, w = two_pi * r * rho;
     acc[0] += double(rho);
     acc[1] += double(w);
@@ -114,7 +117,7 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   }
   const double mid = 0.5 * (J.rho_l + J.rho_v);
   for (int k = blk * DIAG_WARPS + warp; k < Nz; k += J.nblk * DIAG_WARPS) {
-    const double rad = col_radius_warp(D.rho_out, Nz, Nr, k, mid);
+    const double rad = col_radius_warp(D.rho_out, Nz, Nr, k, mid, D.k64[K_R0]);
     if (lane == 0) cols[J.col0 + k] = rad;
   }
 }

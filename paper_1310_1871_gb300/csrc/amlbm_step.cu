@@ -6,7 +6,8 @@
 //   -> isotropic d_r psi and 1D d_r psi (Sec. II.D), halo 5
 //   -> moments, Shan-Chen force (Eq. scforce), axisymmetric force
 //      (Eq. scAxisExtra), u and u^eq (Eqs. uhydro, ueq), halo 3
-//   -> velocity gradients and the sources S, H_z, H_r (Eq. condition_h), halo 1
+//   -> velocity gradients (1D 4th-order differences of Sec. II.D) and the
+//      sources S, H_z, H_r (Eq. condition_h), halo 1
 //   -> pull streaming of the BGK-collided populations (Eq. lbm2d_mod_new) with
 //      the axis / wall / periodic maps of Sec. II.E, and psi of the new state.
 // Global traffic per site and step: 9 populations read (halo re-reads hit L2),
@@ -216,15 +217,30 @@ __device__ __forceinline__ int reflect_row(int j, int Nr) {
   if (j >= Nr) j = 2 * Nr - 1 - j;
   return j < 0 ? 0 : (j >= Nr ? Nr - 1 : j);
 }
+// The same with inlet and outlet rows, whose ghosts mirror about the boundary
+// row itself (zero normal derivative of psi there).
+__device__ __forceinline__ int ghost_row(int j, int Nr, bool inlet, bool outlet) {
+  if (j < 0) j = inlet ? -j : -1 - j;
+  if (j >= Nr) j = outlet ? 2 * (Nr - 1) - j : 2 * Nr - 1 - j;
+  return j < 0 ? 0 : (j >= Nr ? Nr - 1 : j);
+}
+// Column of a ghost column: periodic wrap, or the mirror about the walls at
+// z = -1/2 and z = Nz - 1/2 (clamped like the rows).
+__device__ __forceinline__ int ghost_col(int k, int Nz, bool walls) {
+  if (!walls) return wrapz(k, Nz);
+  if (k < 0) k = -1 - k;
+  if (k >= Nz) k = 2 * Nz - 1 - k;
+  return k < 0 ? 0 : (k >= Nz ? Nz - 1 : k);
+}
 
 // ------------------------------------------------------------- physics --
-// Isotropic 4th-order first derivatives, Sec. II.D Eq. forthorder_firstderivativex:
-//   d_a phi(x) = (1/36) sum_i c_ia (8 phi(x + c_i) - phi(x + 2 c_i)).
+// Isotropic 4th-order first derivative along r, Sec. II.D Eq. forthorder_firstderivativex:
+//   d_r phi(x) = (1/36) sum_i c_ir (8 phi(x + c_i) - phi(x + 2 c_i)).
 // p points at x in a row-major tile whose rows (r) are `st` apart.  The terms
-// are added in z-mirror pairs (c_1, c_3), (c_5, c_6), (c_8, c_7) so that a
-// field mirrored in z gives an exactly mirrored derivative: without this, the
-// rounding of the FP32 forms carries a net axial bias every step and a drop
-// drifts along the axis.
+// are added in z-mirror pairs (c_5, c_6), (c_8, c_7) so that a field mirrored
+// in z gives an exactly mirrored derivative: without this, the rounding of the
+// FP32 forms carries a net axial bias every step and a drop drifts along the
+// axis.
 template <class T>
 __device__ __forceinline__ T link8(const T* p, int dz, int dr, int st) {
   return fma(lit<T>(8.0), p[dr * st + dz], -p[2 * dr * st + 2 * dz]);
@@ -235,13 +251,11 @@ __device__ __forceinline__ T iso_r(const T* p, int st) {
   const T b = (link8(p, 1, 1, st) + link8(p, -1, 1, st)) - (link8(p, 1, -1, st) + link8(p, -1, -1, st));
   return (a + b) * lit<T>(1.0 / 36.0);
 }
-template <class T>
-__device__ __forceinline__ T iso_z(const T* p, int st) {
-  const T a = link8(p, 1, 0, st) - link8(p, -1, 0, st);
-  const T b = (link8(p, 1, 1, st) - link8(p, -1, 1, st)) + (link8(p, 1, -1, st) - link8(p, -1, -1, st));
-  return (a + b) * lit<T>(1.0 / 36.0);
-}
-// 1D 4th-order central difference with element step `step` (Sec. II.D).
+// 1D 4th-order central difference with element step `step` (Sec. II.D): the
+// inner and outer operators of d_zr psi, and the velocity gradients of the
+// sources.  (The velocity gradients do not take the isotropic stencil: its
+// diagonal taps reverse the sign of d_r u_z on a mode alternating in z, and
+// mu d_r u_z / r then amplifies that mode next to a no-slip wall.)
 template <class T>
 __device__ __forceinline__ T d1(const T* p, int step) {
   return fma(lit<T>(8.0), p[step] - p[-step], -(p[2 * step] - p[-2 * step])) * lit<T>(1.0 / 12.0);
@@ -314,7 +328,6 @@ template <class T>
 struct Par {
   T tau, omega, negG, gfac, gz, rho0, inv_rho0, cmu;
 };
-enum { K_TAU, K_OMEGA, K_NEGG, K_GFAC, K_GZ, K_RHO0, K_INVRHO0, K_CMU, K_RREF };
 __device__ __forceinline__ float kc(const InstDesc& D, int c, float) { return D.k32[c]; }
 __device__ __forceinline__ double kc(const InstDesc& D, int c, double) { return D.k64[c]; }
 template <class T>
@@ -336,9 +349,10 @@ __device__ __forceinline__ Par<T> par_of(const InstDesc& D) {
   q.cmu = splat<T>(kc(D, K_CMU, C()));
   return q;
 }
-// 1 / r of row j, r = j + 1/2 (exact in either precision)
-__device__ __forceinline__ F1 inv_r_of(F1, int j) { return rcp(F1{__int2float_rn(j) + 0.5f}); }
-__device__ __forceinline__ D1 inv_r_of(D1, int j) { return rcp(D1{__int2double_rn(j) + 0.5}); }
+// 1 / r of row j, r = j + r0 with r0 = r_off + 1/2 the radius of row 0 (the sum
+// is exact in either precision for the half-integer radii of the workloads)
+__device__ __forceinline__ F1 inv_r_of(F1, int j, float r0) { return rcp(F1{__int2float_rn(j) + r0}); }
+__device__ __forceinline__ D1 inv_r_of(D1, int j, double r0) { return rcp(D1{__int2double_rn(j) + r0}); }
 
 // Total force on a site (Eq. scforce, Eq. scAxisExtra, body force rho g_z).
 template <class T>
@@ -528,12 +542,17 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   const int shift = D.shift;
   const Par<T> q = par_of<T>(D);
   const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
+  // bounded domains (Sec. II.E, Sec. III.2): walls at both ends in z, an inlet
+  // row at row 0, an outlet row at row Nr - 1
+  const bool zw = D.zbc == AMLBM_Z_NOSLIP;
+  const bool inl = D.rlo == AMLBM_RLO_INLET, outl = D.wall == AMLBM_WALL_OUTLET;
 
-  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = wrapz(k0 - G::HP + i, Nz);
-  for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = reflect_row(j0 - G::HP + i, Nr);
+  for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = ghost_col(k0 - G::HP + i, Nz, zw);
+  for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = ghost_row(j0 - G::HP + i, Nr, inl, outl);
   __syncthreads();
 
-  // Stage 0: psi with ghost cells (periodic z, even mirror in r).
+  // Stage 0: psi with ghost cells (periodic z or mirrored about the z walls,
+  // even mirror in r).
   for_tile<G::PR, G::PZ>([&](int lr, int lc) {
     sPsi[lr * G::PZ + lc] = T{psin[(size_t)rowmap[lr] * P + colmap[lc]]};
   });
@@ -553,7 +572,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   for_tile<G::FR, G::FZ>([&](int lr, int lc) {
     const int j = j0 - G::HF + lr;
     if (j < 0 || j >= Nr) return;
-    const T inv_r = inv_r_of(T(), j);
+    const T inv_r = inv_r_of(T(), j, kc(D, K_R0, C()));
     const bool srow = lr >= 2 && lr < G::FR - 2;
     const T* p = sPsi + (lr + G::HP - G::HF) * G::PZ + (lc + G::HP - G::HF);
     const T psi = p[0];
@@ -626,26 +645,81 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     return;
   }
 
-  // Ghost rows of u (depth 2) on tiles that touch the axis or the wall: u_z even
+  // Ghost columns of u (depth 2) at the z walls: u_z and u_r odd (no-slip) about
+  // the wall half a spacing beyond the first and last columns.
+  if (ax && zw && (k0 < G::HF || k0 + BZ + G::HF > Nz)) {
+    for_tile<G::FR, G::FZ>([&](int lr, int lc) {
+      const int j = j0 - G::HF + lr, k = k0 - G::HF + lc;
+      if (j < 0 || j >= Nr) return;
+      int m;
+      if (k == -1 || k == -2) m = -1 - k;
+      else if (k == Nz || k == Nz + 1) m = 2 * Nz - 1 - k;
+      else return;
+      const int src = lr * G::FZ + (m - (k0 - G::HF));
+      sUz[lr * G::FZ + lc] = -sUz[src];
+      sUr[lr * G::FZ + lc] = -sUr[src];
+    });
+    __syncthreads();
+  }
+
+  // Ghost rows of u (depth 2) on tiles that touch row 0 or row Nr - 1: u_z even
   // and u_r odd about the axis; about the outer wall u_r odd and u_z even
-  // (free-slip) or odd (no-slip).
+  // (free-slip) or odd (no-slip); beyond an inlet or outlet row b the linear
+  // continuation u(b - m) = 2 u(b) - u(b + m).  Ghost columns were filled first.
   if (ax && (j0 < G::HF || j0 + BR + G::HF > Nr)) {
     for_tile<G::FR, G::FZ>([&](int lr, int lc) {
       const int j = j0 - G::HF + lr;
-      int m;
+      int m, b = -1;
       bool flip_z;
       if (j == -1 || j == -2) {
-        m = -1 - j;
+        if (inl) { b = 0; m = -j; } else { m = -1 - j; }
         flip_z = false;
       } else if (j == Nr || j == Nr + 1) {
-        m = 2 * Nr - 1 - j;
+        if (outl) { b = Nr - 1; m = 2 * (Nr - 1) - j; } else { m = 2 * Nr - 1 - j; }
         flip_z = D.wall == AMLBM_WALL_NOSLIP;
       } else {
         return;
       }
       const int src = (m - (j0 - G::HF)) * G::FZ + lc;
-      sUz[lr * G::FZ + lc] = flip_z ? -sUz[src] : sUz[src];
-      sUr[lr * G::FZ + lc] = -sUr[src];
+      if (b >= 0) {
+        const int bi = (b - (j0 - G::HF)) * G::FZ + lc;
+        sUz[lr * G::FZ + lc] = fma(lit<T>(2.0), sUz[bi], -sUz[src]);
+        sUr[lr * G::FZ + lc] = fma(lit<T>(2.0), sUr[bi], -sUr[src]);
+      } else {
+        sUz[lr * G::FZ + lc] = flip_z ? -sUz[src] : sUz[src];
+        sUr[lr * G::FZ + lc] = -sUr[src];
+      }
+    });
+    __syncthreads();
+  }
+
+  // Inlet and outlet rows (Sec. II.E, imposed before streaming): what leaves
+  // them is the equilibrium of the imposed velocity and the density of row 1
+  // (inlet), or of the imposed density and the velocity of row Nr - 2
+  // (outlet), without source; it is also their state after the step.
+  if ((inl && j0 == 0) || (outl && j0 + BR >= Nr - 1)) {
+    for_tile<G::SR, G::SZ>([&](int lr, int lc) {
+      const int j = j0 - 1 + lr, k = k0 - 1 + lc;
+      const bool bin = inl && j == 0, bout = outl && j == Nr - 1;
+      // the ghost columns of a periodic lattice too: column 0 pulls from column -1
+      if (!(bin || bout) || (zw && (k < 0 || k >= Nz))) return;
+      const int kk = wrapz(k, Nz);
+      const int nb = (lr + (bin ? 3 : 1)) * G::FZ + (lc + 2);  // row 1 or Nr - 2, tile + 3 indexing
+      T rho, uz, ur;
+      if (bin) {
+        rho = sRho[nb];
+        uz = splat<T>(C(D.inlet[kk]));
+        ur = splat<T>(C(D.inlet[Nz + kk]));
+      } else {
+        rho = splat<T>(kc(D, K_RHOOUT, C()));
+        uz = sUz[nb];
+        ur = sUr[nb];
+      }
+      T fe[9];
+      equilibrium(rho, uz, ur, fe);
+      const int si = lr * G::SZ + lc;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sFs[i * G::nS + si] = fe[i];
     });
     __syncthreads();
   }
@@ -658,12 +732,13 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     if (j < 0 || j >= Nr) return;
     const int si = lr * G::SZ + lc;
     T S_ = lit<T>(0.0), Hz = lit<T>(0.0), Hr = lit<T>(0.0);
-    if (ax) {
-      const T inv_r = inv_r_of(T(), j);
+    const bool brow = (inl && j == 0) || (outl && j == Nr - 1);  // no source on boundary rows
+    if (ax && !brow) {
+      const T inv_r = inv_r_of(T(), j, kc(D, K_R0, C()));
       const int fi = (lr + 2) * G::FZ + (lc + 2);
-      const T druz = iso_r(sUz + fi, G::FZ);
-      const T dzur = iso_z(sUr + fi, G::FZ);
-      const T drur = iso_r(sUr + fi, G::FZ);
+      const T druz = d1(sUz + fi, G::FZ);
+      const T dzur = d1(sUr + fi, 1);
+      const T drur = d1(sUr + fi, G::FZ);
       if constexpr (MODE == 3) {
         if (lr >= 1 && lr <= BR && lc >= 1 && lc <= BZ && k0 + lc - 1 < Nz) {
           C* o = inter + (size_t)j * P + (k0 + lc - 1);
@@ -697,23 +772,30 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   });
   __syncthreads();
 
-  // Stage 4 (tile): pull streaming.  Away from the axis and the wall every
-  // population comes from x - c_i in the same direction; rows 0 and Nr-1 apply
-  // the reflection maps (a warp covers one row, so the paths never diverge).
-  // Then psi of the new state and the shifted store.
+  // Stage 4 (tile): pull streaming.  Away from the boundaries every population
+  // comes from x - c_i in the same direction; rows 0 and Nr-1 apply the
+  // reflection maps, the first and last columns the bounce-back of the z walls
+  // (which takes precedence at the corners); inlet and outlet rows keep their
+  // own boundary populations.  Then psi of the new state and the shifted store.
   S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
   C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
   for_tile<BR, BZ>([&](int lr, int lc) {
     const int j = j0 + lr, k = k0 + lc;
     if (j >= Nr || k >= Nz) return;
-    const bool edge = (j == 0) || (j == Nr - 1);
+    const bool brow = (inl && j == 0) || (outl && j == Nr - 1);
+    const bool edge = (j == 0) || (j == Nr - 1) || (zw && (k == 0 || k == Nz - 1));
     T fn[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
       if (edge) {
-        if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
+        const int ks = k - cz_(i);
+        if (brow) {  // inlet / outlet row: its own boundary populations
+          sl = lr + 1; sc = lc + 1;
+        } else if (zw && (ks < 0 || ks >= Nz)) {  // through a z wall: bounce-back
+          sl = lr + 1; sc = lc + 1; ii = opp_(i);
+        } else if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
           sl = lr + 1; ii = mirror_(i);
         } else if (cr_(i) < 0 && j == Nr - 1) {  // through the outer wall
           sl = lr + 1;
@@ -723,7 +805,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       }
       fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
     }
-    if (link) {
+    if (link && !brow) {
       const int di = (lr + 1) * G::SZ + (lc + 1);
       T h[9];
       sources(sS[di], sHz[di], sHr[di], h);
@@ -837,7 +919,7 @@ __global__ void __launch_bounds__(NT) force_kernel(const InstDesc* __restrict__ 
   for_tile<BR, BZ>([&](int lr, int lc) {
     const int j = j0 + lr, k = k0 + lc;
     if (j >= Nr || k >= Nz) return;
-    const T inv_r = inv_r_of(T(), j);
+    const T inv_r = inv_r_of(T(), j, kc(D, K_R0, C()));
     const T* p = sPsi + (lr + G::HP) * G::PZ + (lc + G::HP);
     const T psi = p[0];
     T f[9];
@@ -953,11 +1035,11 @@ __global__ void __launch_bounds__(NT) stream_kernel(const InstDesc* __restrict__
     const int si = lr * G::SZ + lc;
     T S_ = lit<T>(0.0), Hz = lit<T>(0.0), Hr = lit<T>(0.0);
     if (ax) {
-      const T inv_r = inv_r_of(T(), j);
+      const T inv_r = inv_r_of(T(), j, kc(D, K_R0, C()));
       const int fi = (lr + 2) * G::FZ + (lc + 2);
-      const T druz = iso_r(sUz + fi, G::FZ);
-      const T dzur = iso_z(sUr + fi, G::FZ);
-      const T drur = iso_r(sUr + fi, G::FZ);
+      const T druz = d1(sUz + fi, G::FZ);
+      const T dzur = d1(sUr + fi, 1);
+      const T drur = d1(sUr + fi, G::FZ);
       site_sources(q, sRho[si], sUz[fi], sUr[fi], druz, dzur, drur, inv_r, S_, Hz, Hr);
       T h[9];
       sources(S_, Hz, Hr, h);

@@ -59,9 +59,14 @@ extern "C" int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void
   long long sites = 0;
   for (int i = 0; i < n; ++i) sites += (long long)inst[i].Nz * inst[i].Nr;
 
+  // lattices with walls in z, an inlet or an outlet run on the fused schedule only
+  bool fused_only = false;
+  for (int i = 0; i < n; ++i)
+    fused_only = fused_only || inst[i].bc.z_bc != AMLBM_Z_PERIODIC ||
+                 inst[i].bc.r_lo != AMLBM_RLO_AXIS || inst[i].bc.wall_r == AMLBM_WALL_OUTLET;
   int timed = 0;
   double best_ms = 1e300;
-  for (int sched = AMLBM_SCHED_FUSED; sched <= AMLBM_SCHED_SPLIT; ++sched) {
+  for (int sched = AMLBM_SCHED_FUSED; sched <= (fused_only ? AMLBM_SCHED_FUSED : AMLBM_SCHED_SPLIT); ++sched) {
     int tz[64], tr[64];
     const int nt = std::min(64, amlbm_tiles(storage, sched, tz, tr, 64));
     for (int c = 0; c < nt; ++c) {

@@ -49,7 +49,7 @@ def test_create_rejects_bad_arguments(lib, Nz, Nr, tau, G, rho0):
 
 def test_bad_flags_and_tiles_rejected(lib):
     h = ctypes.c_void_p()
-    for bc in (amlbm.BC(2, 1, 0, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0, 0, 0.0, 1.0),
+    for bc in (amlbm.BC(3, 1, 0, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 2, 0, 0, 0, 0, 0.0, 1.0),
                amlbm.BC(0, 1, 5, 0, 0, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 9, 0, 0, 0.0, 1.0),
                amlbm.BC(0, 1, 0, 2, 7, 0, 0.0, 1.0), amlbm.BC(0, 1, 0, 0, 3, 0, 0.0, 1.0),
                amlbm.BC(0, 1, 0, 3, 0, 4, 0.0, 1.0), amlbm.BC(0, 1, 0, 3, 0, -1, 0.0, 1.0)):
@@ -59,6 +59,57 @@ def test_bad_flags_and_tiles_rejected(lib):
     tune = amlbm.Tune(128, 8, 0)  # not compiled for FP64
     assert lib.amlbm_batch_create(1, inst, ctypes.byref(tune), None, None, 0, ctypes.byref(h)) == amlbm.EINVAL
     assert b"tile" in lib.amlbm_last_error()
+
+
+@pytest.mark.parametrize("Nz,Nr,kw", [
+    (16, 16, dict(z_bc=2)), (16, 16, dict(r_lo=2)), (16, 16, dict(r_off=1.0)),
+    (16, 16, dict(r_lo="inlet", r_off=-1.0)), (16, 16, dict(r_lo="inlet", r_off=float("inf"))),
+    (16, 16, dict(wall="outlet", rho_out=0.0)), (3, 16, dict(z_bc="noslip")),
+    (16, 5, dict(r_lo="inlet", r_off=2.0)), (16, 5, dict(wall="outlet"))])
+def test_bounded_domain_arguments_rejected(lib, Nz, Nr, kw):
+    """Walls in z, inlet and outlet rows: bad codes, an off-axis lattice with the
+    axis, a non-positive outlet density and too small lattices are EINVAL."""
+    h = ctypes.c_void_p()
+    bc = amlbm.make_bc(**kw)
+    assert lib.amlbm_create(Nz, Nr, 1.0, -5.0, 1.0, ctypes.byref(bc), None, None, 0,
+                            ctypes.byref(h)) == amlbm.EINVAL
+    assert h.value is None
+
+
+def test_bounded_domain_needs_fused_schedule(lib):
+    """The split schedule takes periodic lattices on the axis only."""
+    h = ctypes.c_void_p()
+    bc = amlbm.make_bc(z_bc="noslip", r_lo="inlet", r_off=9.0, wall="outlet")
+    inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(32, 111, 1.0, 0.0, 1.0, bc))
+    tune = amlbm.Tune(32, 8, 0, amlbm.SCHEDULE["split"])
+    assert lib.amlbm_batch_create(1, inst, ctypes.byref(tune), None, None, 0, ctypes.byref(h)) == amlbm.EINVAL
+    assert b"split" in lib.amlbm_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures have the size and field offsets of the C header's."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"amlbm_bc": amlbm.BC, "amlbm_instance": amlbm.InstanceC, "amlbm_tune": amlbm.Tune,
+               "amlbm_diag": amlbm.Diag, "amlbm_diag_params": amlbm.DiagParams}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "amlbm.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
 
 
 def test_tile_lists_and_workspace_sizes(lib):
