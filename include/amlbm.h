@@ -239,7 +239,9 @@ int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm
 typedef struct amlbm_adjoint_problem {
   int T;           /* timesteps (>= 1) */
   int ckpt_every;  /* steps between stored states (>= 1); device memory ~ T/ckpt_every
-                      states + ckpt_every states and their intermediates (26 planes each) */
+                      states + ckpt_every states and their intermediates (26 planes each),
+                      twice when T > ckpt_every (the recompute of one segment overlaps the
+                      backward sweep of the next) */
   int objective;   /* AMLBM_OBJ_* */
   int l0;          /* Legendre degree of amps[0] */
   int n_amps;      /* 0..32 */
@@ -256,7 +258,8 @@ size_t amlbm_adjoint_workspace_bytes(amlbm_ctx* ctx, const amlbm_adjoint_problem
  * nothing): J and dJ/dG, dJ/dtau, dJ/d(amps) (n_amps values).
  * The forward run stores the state every ckpt_every steps; the backward sweep
  * recomputes each segment (keeping every state of it and the forward
- * intermediates of each) and applies the transposed step (inverse streaming,
+ * intermediates of each; on a second stream of its own, overlapping the backward
+ * sweep of the segment after it) and applies the transposed step (inverse streaming,
  * adjoint collision and sources, transposed gradient and force stencils with the
  * mirror ghosts folded back) from the last step to the first.  Parameter
  * gradients accumulate in FP64.  Needs FP64 or FP32 storage without shift and the

@@ -532,6 +532,7 @@ struct AdjLayout {
   size_t ckpt = 0, seg = 0, lam = 0, inter = 0, mu = 0, arr = 0, drp = 0, acc = 0, rho0 = 0,
          red = 0, descs = 0, tiles = 0;
   int nck = 0, nseg = 0, ntiles = 0, nred = 0;
+  int nbuf = 1;            // segment buffers: two when there are several segments
   size_t state_elems = 0;  // 10 planes (f and psi)
 };
 
@@ -545,15 +546,17 @@ AdjLayout adj_layout(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem& p) {
   const size_t plane = (size_t)ci.host.P * ci.Nr;
   L.nck = (p.T + p.ckpt_every - 1) / p.ckpt_every;
   L.nseg = std::min(p.ckpt_every, p.T);
+  L.nbuf = L.nck > 1 ? 2 : 1;
   L.state_elems = 10 * plane;
   L.ntiles = ((ci.Nz + 31) / 32) * ((ci.Nr + 7) / 8);
   L.nred = std::min(1024, (ci.Nz * ci.Nr + 255) / 256);
   size_t o = 0;
   auto take = [&](size_t b) { const size_t a = o; o = al(o + b); return a; };
   L.ckpt = take((size_t)L.nck * L.state_elems * cb);
-  L.seg = take((size_t)(L.nseg + 1) * L.state_elems * cb);  // the segment's states
+  // per segment buffer: the segment's states and their intermediates
+  L.seg = take((size_t)L.nbuf * (L.nseg + 1) * L.state_elems * cb);
   L.lam = take(2 * 9 * plane * cb);
-  L.inter = take((size_t)L.nseg * amlbm::I_COUNT * plane * cb);  // their intermediates
+  L.inter = take((size_t)L.nbuf * L.nseg * amlbm::I_COUNT * plane * cb);
   L.mu = take(9 * plane * cb);
   L.arr = take((size_t)kAdjArrays * plane * cb);
   L.drp = take((size_t)(ci.Nr + 4) * ci.host.P * cb);
@@ -561,7 +564,7 @@ AdjLayout adj_layout(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem& p) {
   L.rho0 = take((size_t)ci.Nz * ci.Nr * sizeof(double));
   const int nblk = amlbm::diag_blocks(ci.Nz, ci.Nr);
   L.red = take((size_t)(std::max(L.nred * 34, 8 * nblk + ci.Nz + 16) + 64) * sizeof(double));
-  L.descs = take((size_t)L.nseg * sizeof(InstDesc));
+  L.descs = take((size_t)L.nbuf * L.nseg * sizeof(InstDesc));
   L.tiles = take((size_t)L.ntiles * sizeof(int));
   L.total = o;
   return L;
@@ -677,19 +680,22 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
                                         lam[0]);
       ADJ_CK(cudaGetLastError());
     }
-    // descriptors of the segment slots (tile 32 x 8): descriptor q steps slot q
-    // into slot q + 1
+    // descriptors of the segment slots (tile 32 x 8): descriptor q of buffer b
+    // steps slot q of that buffer into slot q + 1
     {
-      std::vector<InstDesc> d(L.nseg, ci.host);
-      for (int q = 0; q < L.nseg; ++q) {
-        d[q].tiles_z = (Nz + 31) / 32;
-        d[q].tiles_r = (Nr + 7) / 8;
-        d[q].tile_base = 0;
-        for (int h = 0; h < 2; ++h) {
-          d[q].f[h] = seg + (size_t)(q + h) * L.state_elems;
-          d[q].psi[h] = seg + (size_t)(q + h) * L.state_elems + 9 * plane;
+      std::vector<InstDesc> d((size_t)L.nbuf * L.nseg, ci.host);
+      for (int b = 0; b < L.nbuf; ++b)
+        for (int q = 0; q < L.nseg; ++q) {
+          InstDesc& x = d[(size_t)b * L.nseg + q];
+          x.tiles_z = (Nz + 31) / 32;
+          x.tiles_r = (Nr + 7) / 8;
+          x.tile_base = 0;
+          C* sb = seg + (size_t)b * (L.nseg + 1) * L.state_elems;
+          for (int h = 0; h < 2; ++h) {
+            x.f[h] = sb + (size_t)(q + h) * L.state_elems;
+            x.psi[h] = sb + (size_t)(q + h) * L.state_elems + 9 * plane;
+          }
         }
-      }
       std::vector<int> tiles(L.ntiles, 0);
       ADJ_CK(cudaMemcpyAsync(base + L.descs, d.data(), d.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
       ADJ_CK(cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -718,20 +724,27 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
       const dim3 dgrid((Nz + ATZ - 1) / ATZ, (Nr + 4 + ATR - 1) / ATR);  // padded rows -2 .. Nr + 1
       C* inter_seg = reinterpret_cast<C*>(base + L.inter);
       const size_t iseg = (size_t)I_COUNT * plane;
-      // One segment of `len` steps on stream `st`, starting with lambda in lam[c0]:
-      // the recompute (step + intermediates of every state), then the transposed
-      // steps from the last to the first.
-      auto segment = [&](int len, int c0, cudaStream_t st) -> cudaError_t {
-        Adj<C> B = A;
-        int c = c0;
+      // Segment buffer b: states, intermediates and step descriptors.
+      auto seg_of = [&](int b) { return seg + (size_t)b * (L.nseg + 1) * L.state_elems; };
+      auto inter_of = [&](int b) { return inter_seg + (size_t)b * L.nseg * iseg; };
+      // The recompute of a segment of `len` steps into buffer b (each step writes
+      // the next state and the intermediates of the state it starts from).
+      auto recompute = [&](int len, int b, cudaStream_t st) -> cudaError_t {
         for (int q = 0; q < len; ++q) {
-          const cudaError_t e = launch_step_inter(ci.storage, 32, 8, d_seg + q, d_tiles, L.ntiles,
-                                                  inter_seg + q * iseg, plane, st);
+          const cudaError_t e = launch_step_inter(ci.storage, 32, 8, d_seg + (size_t)b * L.nseg + q, d_tiles,
+                                                  L.ntiles, inter_of(b) + q * iseg, plane, st);
           if (e != cudaSuccess) return e;
         }
+        return cudaSuccess;
+      };
+      // The transposed steps of a segment in buffer b, from the last to the first,
+      // starting with lambda in lam[c0].
+      auto backward = [&](int len, int b, int c0, cudaStream_t st) -> cudaError_t {
+        Adj<C> B = A;
+        int c = c0;
         for (int q = len - 1; q >= 0; --q) {
-          B.inter = inter_seg + q * iseg;
-          B.f = seg + (size_t)q * L.state_elems;
+          B.inter = inter_of(b) + q * iseg;
+          B.f = seg_of(b) + (size_t)q * L.state_elems;
           B.lam_in = lam[c];
           B.lam_out = lam[c ^ 1];
           adj_post<C><<<tgrid, ANT, 0, st>>>(B);
@@ -742,19 +755,41 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
         }
         return cudaGetLastError();
       };
-      // Every full segment issues the same launches with the same arguments (for a
-      // given starting lambda buffer), so after the first segment has run directly
-      // (kernel attributes set) one captured graph per starting buffer replays
-      // them on a private stream ordered after the checkpoint copy on s.  Any
+      // Segments run from the last to the first.  The recompute of segment m - 1
+      // (on stream rs, into the other buffer) does not depend on the backward
+      // sweep of segment m (on s), so the two overlap: each is a few hundred CTAs
+      // and leaves most of the GPU idle.  Events order each recompute after the
+      // backward sweep that last read its buffer, and each backward sweep after
+      // its recompute.  Full segments issue the same launches every time, so after
+      // one direct run each part is replayed from a captured CUDA graph (keyed by
+      // buffer, and by the starting lambda buffer for the backward part).  Any
       // failure of the graph machinery falls back to direct launches.
-      cudaStream_t gs = nullptr;
-      cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-      cudaGraphExec_t gx[2] = {nullptr, nullptr};
-      bool use_graph = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess &&
-                       cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) == cudaSuccess &&
-                       cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) == cudaSuccess;
-      // errors inside the loop leave it (rc set) so that the graph resources below
-      // are always released
+      cudaStream_t rs = nullptr, gs = nullptr;
+      cudaEvent_t ev0 = nullptr, evR[2] = {nullptr, nullptr}, evB[2] = {nullptr, nullptr};
+      cudaGraphExec_t gR[2] = {nullptr, nullptr}, gB[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+      bool usedB[2] = {false, false};
+      bool streams_ok = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking) == cudaSuccess &&
+                        cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming) == cudaSuccess;
+      for (int b = 0; b < 2 && streams_ok; ++b)
+        streams_ok = cudaEventCreateWithFlags(&evR[b], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&evB[b], cudaEventDisableTiming) == cudaSuccess;
+      bool use_graph = streams_ok && cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess;
+      bool r_direct = false, b_direct = false;  // a full segment has run directly
+      // capture `fn` (which launches on its stream argument) into *gx
+      auto capture = [&](cudaGraphExec_t* gx, auto fn) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+        const cudaError_t e1 = e == cudaSuccess ? fn(gs) : e;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(gs, &g);
+        if (e == cudaSuccess && e1 == cudaSuccess) e = cudaGraphInstantiate(gx, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || e1 != cudaSuccess) {
+          use_graph = false;
+          *gx = nullptr;
+          cudaGetLastError();  // the direct path reports real errors
+        }
+      };
+      cudaStream_t rstream = streams_ok ? rs : s;  // without a second stream, no overlap
 #define SEG_CK(call)                                                                          \
   {                                                                                           \
     const cudaError_t e_ = (call);                                                            \
@@ -763,45 +798,71 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
       break;                                                                                  \
     }                                                                                         \
   }
-      int cur = 0, direct_done = 0;
-      for (int m = L.nck - 1; m >= 0 && rc == AMLBM_OK; --m) {
-        const int n0 = m * p->ckpt_every, n1 = std::min(p->T, n0 + p->ckpt_every), len = n1 - n0;
-        SEG_CK(cudaMemcpyAsync(seg, ckpt + (size_t)m * L.state_elems, SB, cudaMemcpyDeviceToDevice, s));
-        bool ran = false;
-        if (use_graph && direct_done > 0 && len == p->ckpt_every) {
-          if (!gx[cur]) {
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
-            const cudaError_t e1 = e == cudaSuccess ? segment(len, cur, gs) : e;
-            if (e == cudaSuccess) e = cudaStreamEndCapture(gs, &g);
-            if (e == cudaSuccess && e1 == cudaSuccess) e = cudaGraphInstantiate(&gx[cur], g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (e != cudaSuccess || e1 != cudaSuccess) {
-              use_graph = false;
-              gx[cur] = nullptr;
-              cudaGetLastError();  // the direct path below reports real errors
-            }
-          }
-          if (use_graph) {
-            SEG_CK(cudaEventRecord(ev_in, s));
-            SEG_CK(cudaStreamWaitEvent(gs, ev_in, 0));
-            SEG_CK(cudaGraphLaunch(gx[cur], gs));
-            SEG_CK(cudaEventRecord(ev_out, gs));
-            SEG_CK(cudaStreamWaitEvent(s, ev_out, 0));
-            ran = true;
-          }
+      // issue the checkpoint copy and the recompute of segment m into buffer b on rstream
+      auto issue_recompute = [&](int m, int b) -> cudaError_t {
+        const int n0 = m * p->ckpt_every, len = std::min(p->T, n0 + p->ckpt_every) - n0;
+        if (streams_ok && usedB[b]) {  // the backward sweep that last read buffer b
+          const cudaError_t e = cudaStreamWaitEvent(rstream, evB[b], 0);
+          if (e != cudaSuccess) return e;
         }
-        if (!ran) {
-          SEG_CK(segment(len, cur, s));
-          ++direct_done;
+        cudaError_t e = cudaMemcpyAsync(seg_of(b), ckpt + (size_t)m * L.state_elems, SB,
+                                        cudaMemcpyDeviceToDevice, rstream);
+        if (e != cudaSuccess) return e;
+        const bool full = len == p->ckpt_every;
+        if (use_graph && r_direct && full) {
+          if (!gR[b]) capture(&gR[b], [&](cudaStream_t st) { return recompute(len, b, st); });
+          if (use_graph) e = cudaGraphLaunch(gR[b], rstream);
+          else e = recompute(len, b, rstream);
+        } else {
+          e = recompute(len, b, rstream);
+          if (full) r_direct = true;
         }
-        if (len & 1) cur ^= 1;
-      }
+        if (e == cudaSuccess && streams_ok) e = cudaEventRecord(evR[b], rstream);
+        return e;
+      };
+      int cur = 0;
+      do {
+        if (streams_ok) {  // the recompute stream starts after the forward run and the seed
+          SEG_CK(cudaEventRecord(ev0, s));
+          SEG_CK(cudaStreamWaitEvent(rs, ev0, 0));
+        }
+        SEG_CK(issue_recompute(L.nck - 1, (L.nck - 1) % L.nbuf));
+        for (int m = L.nck - 1; m >= 0 && rc == AMLBM_OK; --m) {
+          const int b = m % L.nbuf;
+          const int n0 = m * p->ckpt_every, len = std::min(p->T, n0 + p->ckpt_every) - n0;
+          // the next segment's recompute goes ahead on the other buffer; with one
+          // stream it would have to wait for this backward sweep, so it is issued after it
+          if (m >= 1 && streams_ok) SEG_CK(issue_recompute(m - 1, (m - 1) % L.nbuf));
+          if (streams_ok) SEG_CK(cudaStreamWaitEvent(s, evR[b], 0));
+          const bool full = len == p->ckpt_every;
+          if (use_graph && b_direct && full) {
+            if (!gB[b][cur]) capture(&gB[b][cur], [&](cudaStream_t st) { return backward(len, b, cur, st); });
+            if (use_graph) SEG_CK(cudaGraphLaunch(gB[b][cur], s))
+            else SEG_CK(backward(len, b, cur, s))
+          } else {
+            SEG_CK(backward(len, b, cur, s));
+            if (full) b_direct = true;
+          }
+          if (streams_ok) {
+            SEG_CK(cudaEventRecord(evB[b], s));
+            usedB[b] = true;
+          }
+          if (m >= 1 && !streams_ok) SEG_CK(issue_recompute(m - 1, (m - 1) % L.nbuf));
+          if (len & 1) cur ^= 1;
+        }
+      } while (false);
+      // graphs run on s and rs: let them finish before their executables go
+      if (rs) cudaStreamSynchronize(rs);
       if (gs) cudaStreamSynchronize(gs);
-      for (auto& g : gx)
+      cudaStreamSynchronize(s);
+      for (auto& g : gR)
         if (g) cudaGraphExecDestroy(g);
-      if (ev_in) cudaEventDestroy(ev_in);
-      if (ev_out) cudaEventDestroy(ev_out);
+      for (auto& row : gB)
+        for (auto& g : row)
+          if (g) cudaGraphExecDestroy(g);
+      for (auto* ev : {ev0, evR[0], evR[1], evB[0], evB[1]})
+        if (ev) cudaEventDestroy(ev);
+      if (rs) cudaStreamDestroy(rs);
       if (gs) cudaStreamDestroy(gs);
 #undef SEG_CK
       if (rc) goto done;

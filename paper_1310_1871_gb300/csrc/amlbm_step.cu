@@ -786,10 +786,13 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
     const bool brow = (inl && j == 0) || (outl && j == Nr - 1);
     const bool edge = (j == 0) || (j == Nr - 1) || (zw && (k == 0 || k == Nz - 1));
     T fn[9];
+    if (!edge) {  // interior site: constant offsets, no per-population branch
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
-      if (edge) {
+      for (int i = 0; i < 9; ++i) fn[i] = sFs[i * G::nS + (lr + 1 - cr_(i)) * G::SZ + (lc + 1 - cz_(i))];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        int sl = lr + 1 - cr_(i), sc = lc + 1 - cz_(i), ii = i;
         const int ks = k - cz_(i);
         if (brow) {  // inlet / outlet row: its own boundary populations
           sl = lr + 1; sc = lc + 1;
@@ -802,8 +805,8 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
           if (noslip) { sc = lc + 1; ii = opp_(i); }
           else { ii = mirror_(i); }
         }
+        fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
       }
-      fn[i] = sFs[ii * G::nS + sl * G::SZ + sc];
     }
     if (link && !brow) {
       const int di = (lr + 1) * G::SZ + (lc + 1);
