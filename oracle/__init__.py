@@ -30,6 +30,7 @@ WALL_FREESLIP, WALL_NOSLIP, WALL_OUTLET = 0, 1, 2
 SRC_LOCAL, SRC_LINK = 0, 1
 Z_PERIODIC, Z_NOSLIP = 0, 1
 RLO_AXIS, RLO_INLET = 0, 1
+FORCE_SHIFT, FORCE_GUO = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +50,7 @@ class _Params(ctypes.Structure):
                 ("wall", ctypes.c_int), ("axisym", ctypes.c_int), ("src_mode", ctypes.c_int),
                 ("zbc", ctypes.c_int), ("rlo", ctypes.c_int), ("r_off", ctypes.c_double),
                 ("rho_out", ctypes.c_double), ("inlet_uz", ctypes.POINTER(ctypes.c_double)),
-                ("inlet_ur", ctypes.POINTER(ctypes.c_double))]
+                ("inlet_ur", ctypes.POINTER(ctypes.c_double)), ("forcing", ctypes.c_int)]
 
 
 def _load():
@@ -85,7 +86,7 @@ class Oracle:
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, gz=0.0, wall=WALL_FREESLIP,
                  axisym=1, src_mode=SRC_LOCAL, zbc=Z_PERIODIC, rlo=RLO_AXIS, r_off=0.0,
-                 rho_out=1.0, inlet=None):
+                 rho_out=1.0, inlet=None, forcing=FORCE_SHIFT):
         """inlet: (u_z, u_r) arrays of Nz values imposed on the inlet row (rlo=RLO_INLET)."""
         self.Nz, self.Nr = int(Nz), int(Nr)
         if inlet is None:
@@ -94,7 +95,7 @@ class Oracle:
         self._inlet = tuple(np.ascontiguousarray(a, dtype=np.float64).reshape(self.Nz) for a in inlet)
         self.p = _Params(self.Nz, self.Nr, float(tau), float(G), float(rho0), float(gz),
                          int(wall), int(axisym), int(src_mode), int(zbc), int(rlo), float(r_off),
-                         float(rho_out), _ptr(self._inlet[0]), _ptr(self._inlet[1]))
+                         float(rho_out), _ptr(self._inlet[0]), _ptr(self._inlet[1]), int(forcing))
         self.lib = _load()
 
     def _c(self, rc):

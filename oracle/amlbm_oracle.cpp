@@ -55,6 +55,7 @@ enum { WALL_FREESLIP = 0, WALL_NOSLIP = 1, WALL_OUTLET = 2 };
 enum { SRC_LOCAL = 0, SRC_LINK = 1 };
 enum { Z_PERIODIC = 0, Z_NOSLIP = 1 };
 enum { RLO_AXIS = 0, RLO_INLET = 1 };
+enum { FORCE_SHIFT = 0, FORCE_GUO = 1 };
 
 template <class T>
 struct Params {
@@ -70,6 +71,9 @@ struct Params {
   double rho_out;            // density imposed on the outlet row
   const double* inlet_uz;    // velocity imposed on the inlet row, [Nz] each
   const double* inlet_ur;
+  int forcing;   // FORCE_SHIFT: the Shan-Chen velocity shift (Eq. ueq, the paper's
+                 // scheme); FORCE_GUO: the forcing of Guo, Zheng & Shi (2002) that
+                 // Sec. IV.1 compares it with (Table I, Laplace test)
 };
 
 // Padded scalar field with explicit ghost cells of width g on every side.
@@ -341,11 +345,24 @@ static void step(const Params<T>& P, const T* f, T* fn, Macro<T>* keep) {
   macro(P, f, M);
   // 9. BGK collision towards f^eq(rho, u^eq) (Eq. lbm2d) and the source of
   // every population at its own site.
+  // With the Guo forcing (Guo, Zheng & Shi 2002, restated from its definition):
+  // f^eq at the hydrodynamic u, plus (1 - 1/(2 tau)) times the discrete force
+  // W_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F, whose zeroth moment is 0
+  // and first moment F.
   std::vector<T> fs((size_t)Q * N), h((size_t)Q * N);
   for (int n = 0; n < N; ++n)
     for (int i = 0; i < Q; ++i) {
       const T fi = f[(size_t)i * N + n];
-      fs[(size_t)i * N + n] = fi - (fi - feq(i, M.rho[n], M.ueqz[n], M.ueqr[n])) / P.tau;
+      if (P.forcing == FORCE_GUO) {
+        const T uz = M.uz[n], ur = M.ur[n], Fz = M.Fz[n], Fr = M.Fr[n];
+        const T cu = double(CZ[i]) * uz + double(CR[i]) * ur;
+        const T cF = double(CZ[i]) * Fz + double(CR[i]) * Fr;
+        const T uF = uz * Fz + ur * Fr;
+        const T Si = W[i] * ((cF - uF) / CS2 + cu * cF / CS4);
+        fs[(size_t)i * N + n] = fi - (fi - feq(i, M.rho[n], uz, ur)) / P.tau + (1.0 - 0.5 / P.tau) * Si;
+      } else {
+        fs[(size_t)i * N + n] = fi - (fi - feq(i, M.rho[n], M.ueqz[n], M.ueqr[n])) / P.tau;
+      }
       h[(size_t)i * N + n] = h_of(i, M.S[n], M.Hz[n], M.Hr[n]);
     }
   // Inlet and outlet rows (Sec. II.E: a prescribed velocity or pressure is set
@@ -496,11 +513,12 @@ struct orc_params {
   double r_off, rho_out;
   const double* inlet_uz;  // [Nz], read when rlo is the inlet
   const double* inlet_ur;
+  int forcing;
 };
 
 static orc::Params<double> to_p(const orc_params* p) {
   return {p->Nz, p->Nr, p->tau, p->G, p->rho0, p->gz, p->wall, p->axisym, p->src_mode,
-          p->zbc, p->rlo, p->r_off, p->rho_out, p->inlet_uz, p->inlet_ur};
+          p->zbc, p->rlo, p->r_off, p->rho_out, p->inlet_uz, p->inlet_ur, p->forcing};
 }
 // Sizes are such that every ghost cell of depth 4 mirrors a real site.
 static int check(const orc_params* p) {
@@ -512,6 +530,7 @@ static int check(const orc_params* p) {
   if (!(p->r_off >= 0.0)) return -1;
   if (p->rlo == 1 && (!p->inlet_uz || !p->inlet_ur)) return -1;
   if (p->wall == 2 && !(p->rho_out > 0)) return -1;
+  if (p->forcing != 0 && p->forcing != 1) return -1;
   return 0;
 }
 
@@ -625,7 +644,7 @@ int orc_grad(const orc_params* p, int T, double zc, double R, double w, double r
   for (int q = qfirst; q <= qlast; ++q) {
     orc::Params<cplx> P{Nz, Nr, cplx(p->tau), cplx(p->G), cplx(p->rho0), cplx(p->gz),
                         p->wall, p->axisym, p->src_mode, p->zbc, p->rlo, p->r_off,
-                        p->rho_out, p->inlet_uz, p->inlet_ur};
+                        p->rho_out, p->inlet_uz, p->inlet_ur, p->forcing};
     std::vector<cplx> a(namp);
     for (int m = 0; m < namp; ++m) a[m] = cplx(amp[m]);
     if (q == 0) P.G += cplx(0, hstep);

@@ -88,10 +88,11 @@ def _d1(p, g, Nr, Nz, comp):
 
 
 def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0, zbc=0, rlo=0, r_off=0.0,
-         rho_out=1.0, inlet=None):
+         rho_out=1.0, inlet=None, forcing=0):
     """One timestep.  wall: 0 free-slip, 1 no-slip, 2 outlet row; zbc: 0
     periodic, 1 no-slip z walls; rlo: 0 axis, 1 inlet row with velocity
-    inlet = (u_z, u_r) per column; r_j = j + 1/2 + r_off."""
+    inlet = (u_z, u_r) per column; r_j = j + 1/2 + r_off; forcing: 0 the
+    Shan-Chen velocity shift, 1 Guo, Zheng & Shi (2002)."""
     Q, Nr, Nz = f.shape
     r = (np.arange(Nr) + 0.5 + r_off)[:, None] * np.ones((1, Nz))
     rho = f.sum(0)
@@ -141,9 +142,17 @@ def step(f, tau, G, rho0=1.0, gz=0.0, wall=0, axisym=1, src_mode=0, zbc=0, rlo=0
         Hr = (2 * mu * (drur - ur / r) - rho * ur * ur) / r
         for i in range(9):
             h[i] = Wt[i] * (S + (C[i, 0] * Hz + C[i, 1] * Hr) / CS2)
-    cu = C[:, 0, None, None] * vz + C[:, 1, None, None] * vr
-    feq = Wt[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (vz ** 2 + vr ** 2))
-    post = f - (f - feq) / tau
+    if forcing == 1:
+        # Guo: the equilibrium at u and the discrete force
+        # (1 - 1/(2 tau)) W_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F
+        ex, ey = C[:, 0, None, None].astype(float), C[:, 1, None, None].astype(float)
+        force = Wt[:, None, None] * (((ex - uz) * Fz + (ey - ur) * Fr) / CS2
+                                     + (ex * uz + ey * ur) * (ex * Fz + ey * Fr) / CS2 ** 2)
+        post = f - (f - equilibrium(rho, uz, ur)) / tau + (1 - 1 / (2 * tau)) * force
+    else:
+        cu = C[:, 0, None, None] * vz + C[:, 1, None, None] * vr
+        feq = Wt[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * (vz ** 2 + vr ** 2))
+        post = f - (f - feq) / tau
     # inlet / outlet rows: the equilibrium of the imposed density and velocity,
     # without source, is what leaves them and what they hold next
     bnd = np.zeros(Nr, dtype=bool)
