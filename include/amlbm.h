@@ -66,6 +66,11 @@ extern "C" {
 #define AMLBM_Z_PERIODIC 0 /* periodic */
 #define AMLBM_Z_NOSLIP 1   /* mid-grid bounce-back walls at z = -1/2 and z = Nz - 1/2 */
 
+/* How the force F enters the collision (Sec. II.B; Sec. IV.1 compares the two). */
+#define AMLBM_FORCE_SHIFT 0 /* Shan-Chen velocity shift: f^eq at u^eq = (rho u + tau F)/rho */
+#define AMLBM_FORCE_GUO 1   /* Guo, Zheng & Shi (2002): f^eq at u, plus (1 - 1/(2 tau)) times
+                               W_i [3 (c_i - u) + 9 (c_i . u) c_i] . F; fused schedule only, no adjoint */
+
 /* Lower radial boundary. */
 #define AMLBM_RLO_AXIS 0  /* the axis r = 0, half a spacing below row 0 (r_off = 0) */
 #define AMLBM_RLO_INLET 1 /* inlet row: row 0 holds f^eq(rho of row 1, u_in(z)), u_in set by
@@ -116,6 +121,7 @@ typedef struct amlbm_bc {
   int r_lo;       /* AMLBM_RLO_* */
   double r_off;   /* r_j = j + 1/2 + r_off, r_off >= 0; must be 0 with the axis */
   double rho_out; /* density of the outlet row (AMLBM_WALL_OUTLET), > 0 */
+  int forcing;    /* AMLBM_FORCE_* (0: the paper's velocity shift) */
 } amlbm_bc;
 
 /* Parameters of the diagnostics (where to measure the drop or thread). */
@@ -224,6 +230,39 @@ void amlbm_destroy(amlbm_ctx* ctx);
  * Calls no cudaMalloc, cudaFree or allocating library routine. */
 #define AMLBM_NOALLOC_MAX_NZ 8192
 int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* out);
+
+/* ------------------------------------------------------- flat interface tool */
+
+/* Equilibrium of a flat liquid-vapour interface, the measurement of Table I
+ * (Sec. IV.1): a lattice of 1 x n sites (free-slip outer wall) starts from the
+ * slab rho = rho_v0 + (rho_l0 - rho_v0)/2 (1 - tanh((r - n/2)/2)), r = j + 1/2
+ * (liquid below r = n/2), runs `steps` timesteps of the step kernel, then
+ *   gamma       = -(G c_s^4 / 2) sum_j (d_r psi)^2             (Eq. st)
+ *   gamma_tilde = gamma + (tau - 1/2)^2 sum_j F_r^2 / rho       (Eq. stc)
+ * over the rows, with the isotropic d_r psi (Sec. II.D) and the total force F of
+ * the equilibrated state.  gamma_tilde is the tension of the Shan-Chen velocity
+ * shift the library uses; gamma that of a scheme without the tau-correction.
+ * rho_l, rho_v are the densities on row 0 and row n-1: the coexistence densities
+ * once the slab has relaxed (they do not depend on rho_l0, rho_v0, which only
+ * need to lie on either side of the coexistence pair).  axisym = 0 is the planar
+ * model (Table I, "2D"), 1 the axisymmetric one (a liquid cylinder of radius
+ * ~n/2; Table I, "axis").  forcing: AMLBM_FORCE_* (Table I's "SC" columns are
+ * gamma_tilde of the shift, its "Guo" columns gamma of the Guo forcing).
+ * storage: AMLBM_STORE_F64 or AMLBM_STORE_F32.
+ * Allocates and frees its own device memory on cuda_stream and synchronises it;
+ * AMLBM_EINVAL for bad arguments (as amlbm_create, and n < 8, steps < 0,
+ * rho_l0 <= rho_v0 or rho_v0 <= 0). */
+typedef struct amlbm_interface {
+  double gamma;       /* Eq. st */
+  double gamma_tilde; /* Eq. stc */
+  double rho_l;       /* density on row 0 */
+  double rho_v;       /* density on row n-1 */
+  double position;    /* radius where rho crosses (rho_l + rho_v)/2 */
+  double umax;        /* max |u| of the equilibrated state (spurious current) */
+} amlbm_interface;
+
+int amlbm_flat_interface(double G, double tau, double rho0, int axisym, int forcing, int storage, int n,
+                         int steps, double rho_l0, double rho_v0, void* cuda_stream, amlbm_interface* out);
 
 /* ---------------------------------------------------------- differentiation */
 

@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -5
 WALL = {"freeslip": 0, "noslip": 1, "outlet": 2}
 Z_BC = {"periodic": 0, "noslip": 1}
 R_LO = {"axis": 0, "inlet": 1}
+FORCING = {"shift": 0, "guo": 1}
 SRC = {"local": 0, "link": 1}
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 SHIFT = {"default": 0, "none": 1, "global": 2, "local": 3, "equilibrium": 4}
@@ -42,7 +43,7 @@ class BC(ctypes.Structure):
                 ("storage", ctypes.c_int), ("shift", ctypes.c_int), ("rounding", ctypes.c_int),
                 ("g_z", ctypes.c_double), ("rho_ref", ctypes.c_double),
                 ("z_bc", ctypes.c_int), ("r_lo", ctypes.c_int), ("r_off", ctypes.c_double),
-                ("rho_out", ctypes.c_double)]
+                ("rho_out", ctypes.c_double), ("forcing", ctypes.c_int)]
 
 
 class DiagParams(ctypes.Structure):
@@ -75,6 +76,10 @@ class Tune(ctypes.Structure):
                 ("schedule", ctypes.c_int)]
 
 
+class Interface(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("gamma", "gamma_tilde", "rho_l", "rho_v", "position", "umax")]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("tune", Tune), ("ms_per_step", ctypes.c_double), ("mlups", ctypes.c_double)]
 
@@ -90,7 +95,7 @@ EXPORTS = [
     "amlbm_batch_diagnostics", "amlbm_batch_sites", "amlbm_batch_destroy", "amlbm_last_error",
     "amlbm_version", "amlbm_diagnostics_noalloc", "amlbm_adjoint_workspace_bytes", "amlbm_adjoint",
     "amlbm_objective", "amlbm_batch_config", "amlbm_batch_init_all", "amlbm_batch_diagnostics_all",
-    "amlbm_autotune", "amlbm_set_inlet", "amlbm_batch_set_inlet",
+    "amlbm_autotune", "amlbm_set_inlet", "amlbm_batch_set_inlet", "amlbm_flat_interface",
 ]
 
 
@@ -114,6 +119,8 @@ def load(build_if_missing: bool = True):
                                      ctypes.POINTER(BC), vp, vp, sz, ctypes.POINTER(vp)]
         lib.amlbm_init_fields.argtypes = [vp, dp, dp, dp]
         lib.amlbm_set_inlet.argtypes = [vp, dp, dp]
+        lib.amlbm_flat_interface.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int] * 5 + \
+            [ctypes.c_double] * 2 + [vp, ctypes.POINTER(Interface)]
         lib.amlbm_init_fields_device.argtypes = [vp, vp, vp, vp]
         lib.amlbm_step.argtypes = [vp, ip]
         lib.amlbm_read_fields.argtypes = [vp, dp, dp, dp, dp]
@@ -185,10 +192,10 @@ def _code(table, v):
 
 def make_bc(wall="freeslip", axisym=True, src="local", storage="f64", gz=0.0, rho_ref=1.0,
             shift="default", rounding="default", z_bc="periodic", r_lo="axis", r_off=0.0,
-            rho_out=1.0) -> BC:
+            rho_out=1.0, forcing="shift") -> BC:
     return BC(_code(WALL, wall), int(bool(axisym)), _code(SRC, src), _code(STORAGE, storage),
               _code(SHIFT, shift), _code(ROUNDING, rounding), float(gz), float(rho_ref),
-              _code(Z_BC, z_bc), _code(R_LO, r_lo), float(r_off), float(rho_out))
+              _code(Z_BC, z_bc), _code(R_LO, r_lo), float(r_off), float(rho_out), _code(FORCING, forcing))
 
 
 def _diag_dict(d: Diag) -> dict:
@@ -214,6 +221,7 @@ class InstanceSpec:
     r_lo: str = "axis"
     r_off: float = 0.0
     rho_out: float = 1.0
+    forcing: str = "shift"
 
 
 def instances_c(specs, storage):
@@ -223,8 +231,22 @@ def instances_c(specs, storage):
     for i, s in enumerate(specs):
         arr[i] = InstanceC(int(s.Nz), int(s.Nr), float(s.tau), float(s.G), float(s.rho0),
                            make_bc(s.wall, s.axisym, s.src, storage, s.gz, s.rho_ref, s.shift,
-                                   s.rounding, s.z_bc, s.r_lo, s.r_off, s.rho_out))
+                                   s.rounding, s.z_bc, s.r_lo, s.r_off, s.rho_out, s.forcing))
     return arr
+
+
+def flat_interface(G, tau=1.0, rho0=1.0, axisym=True, storage="f64", n=64, steps=20000, rho_l0=2.0,
+                   rho_v0=0.15, forcing="shift", stream=None) -> dict:
+    """amlbm_flat_interface: coexistence densities and surface tension (Table I) of a
+    1 x n flat interface after `steps` timesteps on the GPU."""
+    lib = load()
+    sh, _ = _stream_handle(stream)
+    out = Interface()
+    _check(lib, lib.amlbm_flat_interface(float(G), float(tau), float(rho0), int(bool(axisym)),
+                                         _code(FORCING, forcing), _code(STORAGE, storage), int(n),
+                                         int(steps), float(rho_l0),
+                                         float(rho_v0), sh, ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in Interface._fields_}
 
 
 def autotune_raw(specs, storage, steps=20, stream=None):
@@ -393,13 +415,14 @@ class Lattice:
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, wall="freeslip", axisym=True, src="local",
                  storage="f64", gz=0.0, rho_ref=1.0, shift="default", rounding="default", stream=None,
-                 z_bc="periodic", r_lo="axis", r_off=0.0, rho_out=1.0):
+                 z_bc="periodic", r_lo="axis", r_off=0.0, rho_out=1.0, forcing="shift"):
         import torch
         self.lib = load()
         if not torch.cuda.is_available():
             raise RuntimeError("amlbm needs a CUDA device")
         self.Nz, self.Nr = int(Nz), int(Nr)
-        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift, rounding, z_bc, r_lo, r_off, rho_out)
+        bc = make_bc(wall, axisym, src, storage, gz, rho_ref, shift, rounding, z_bc, r_lo, r_off, rho_out,
+                     forcing)
         nbytes = self.lib.amlbm_workspace_bytes(self.Nz, self.Nr, bc.storage)
         if nbytes == 0:
             raise AmlbmError(EINVAL, "bad lattice size or storage")

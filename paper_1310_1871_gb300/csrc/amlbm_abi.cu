@@ -55,12 +55,15 @@ amlbm_bc default_bc() {
   b.r_lo = AMLBM_RLO_AXIS;
   b.r_off = 0.0;
   b.rho_out = 1.0;
+  b.forcing = AMLBM_FORCE_SHIFT;
   return b;
 }
 
-// A lattice with walls in z, an inlet or an outlet (the fused schedule only).
+// A lattice with walls in z, an inlet or an outlet, or with the Guo forcing:
+// the fused schedule only.
 bool bounded(const amlbm_bc& bc) {
-  return bc.z_bc != AMLBM_Z_PERIODIC || bc.r_lo != AMLBM_RLO_AXIS || bc.wall_r == AMLBM_WALL_OUTLET;
+  return bc.z_bc != AMLBM_Z_PERIODIC || bc.r_lo != AMLBM_RLO_AXIS || bc.wall_r == AMLBM_WALL_OUTLET ||
+         bc.forcing != AMLBM_FORCE_SHIFT;
 }
 
 // Schedule and tile when the caller gives none (fastest on the 64-drop sweep on
@@ -115,6 +118,8 @@ int validate(const amlbm_instance& I, int idx) {
       I.bc.wall_r != AMLBM_WALL_OUTLET)
     return fail(AMLBM_EINVAL, w + "bad wall_r");
   if (I.bc.z_bc != AMLBM_Z_PERIODIC && I.bc.z_bc != AMLBM_Z_NOSLIP) return fail(AMLBM_EINVAL, w + "bad z_bc");
+  if (I.bc.forcing != AMLBM_FORCE_SHIFT && I.bc.forcing != AMLBM_FORCE_GUO)
+    return fail(AMLBM_EINVAL, w + "bad forcing");
   if (I.bc.r_lo != AMLBM_RLO_AXIS && I.bc.r_lo != AMLBM_RLO_INLET) return fail(AMLBM_EINVAL, w + "bad r_lo");
   if (!(I.bc.r_off >= 0.0) || !std::isfinite(I.bc.r_off) || I.bc.r_off > 1e6)
     return fail(AMLBM_EINVAL, w + "r_off must be finite, >= 0 and <= 1e6");
@@ -279,7 +284,8 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     if (sched == AMLBM_SCHED_SPLIT)
       for (const auto& I : inst)
         if (bounded(I.bc))
-          return fail(AMLBM_EINVAL, "the split schedule takes periodic lattices on the axis only");
+          return fail(AMLBM_EINVAL,
+                      "the split schedule takes periodic lattices on the axis with the velocity shift only");
     if (!tz && !tr) {
       int s2;
       pick_tile(storage, inst, &s2, &tz, &tr);
@@ -337,6 +343,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.shift = resolve_shift(I.bc);
     d.zbc = I.bc.z_bc;
     d.rlo = I.bc.r_lo;
+    d.forcing = I.bc.forcing;
     // 1 = stochastic rounding of the 16-bit stores.  Default: stochastic for BF16
     // with the W_i s shifts (measured: an order of magnitude more accurate there),
     // to nearest for FP16 and for the equilibrium shift (no gain measured)
@@ -355,10 +362,10 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.rho0 = I.rho0;
     d.gz = I.bc.g_z;
     d.rho_ref = I.bc.rho_ref;
-    const double k[11] = {I.tau, 1.0 / I.tau, -I.G, -I.G / 18.0, I.bc.g_z, I.rho0, 1.0 / I.rho0,
+    const double k[12] = {I.tau, 1.0 / I.tau, -I.G, -I.G / 18.0, I.bc.g_z, I.rho0, 1.0 / I.rho0,
                           (I.tau - 0.5) / 3.0, I.bc.rho_ref, I.bc.r_off + 0.5,
-                          I.bc.wall_r == AMLBM_WALL_OUTLET ? I.bc.rho_out : 1.0};
-    for (int c = 0; c < 11; ++c) {
+                          I.bc.wall_r == AMLBM_WALL_OUTLET ? I.bc.rho_out : 1.0, 1.0 - 0.5 / I.tau};
+    for (int c = 0; c < 12; ++c) {
       d.k64[c] = k[c];
       d.k32[c] = (float)k[c];
     }

@@ -578,6 +578,8 @@ int check_problem(const amlbm::CtxInfo& ci, const amlbm_adjoint_problem* p) {
   if (ci.host.shift != 0) return set_error(AMLBM_EINVAL, "the adjoint needs unshifted storage");
   if (ci.host.zbc != AMLBM_Z_PERIODIC || ci.host.rlo != AMLBM_RLO_AXIS || ci.host.wall == AMLBM_WALL_OUTLET)
     return set_error(AMLBM_EINVAL, "the adjoint takes periodic lattices on the axis only");
+  if (ci.host.forcing != AMLBM_FORCE_SHIFT)
+    return set_error(AMLBM_EINVAL, "the adjoint implements the velocity-shift forcing only");
   if (ci.host.src != AMLBM_SRC_LOCAL)
     return set_error(AMLBM_EINVAL, "the adjoint implements the departure-site source only");
   if (p->T < 1 || p->ckpt_every < 1) return set_error(AMLBM_EINVAL, "need T >= 1, ckpt_every >= 1");

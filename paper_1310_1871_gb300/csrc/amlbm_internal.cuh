@@ -20,13 +20,14 @@ struct InstDesc {
   int rounding;  // 16-bit storage: 0 to nearest, 1 stochastic
   int zbc;       // AMLBM_Z_*: periodic, or no-slip walls at both ends in z
   int rlo;       // AMLBM_RLO_*: the axis, or an inlet row at row 0
+  int forcing;   // AMLBM_FORCE_*: Shan-Chen velocity shift or Guo forcing
   double tau, G, rho0, gz, rho_ref;
   // the constants of the step, computed on the host in FP64 and also held
   // rounded to FP32 (kernels read them without conversion or division):
   // tau, 1/tau, -G, -G/18, g_z, rho0, 1/rho0, (tau - 1/2)/3, rho_ref,
-  // the radius of row 0 (r_off + 1/2) and the outlet density
-  double k64[11];
-  float k32[11];
+  // the radius of row 0 (r_off + 1/2), the outlet density and 1 - 1/(2 tau)
+  double k64[12];
+  float k32[12];
   const double* inlet;  // inlet row velocity, u_z[Nz] then u_r[Nz] (zero until set)
   void* f[2];
   void* psi[2];
@@ -37,7 +38,7 @@ struct InstDesc {
 };
 
 // Slots of InstDesc::k64 / k32.
-enum { K_TAU, K_OMEGA, K_NEGG, K_GFAC, K_GZ, K_RHO0, K_INVRHO0, K_CMU, K_RREF, K_R0, K_RHOOUT };
+enum { K_TAU, K_OMEGA, K_NEGG, K_GFAC, K_GZ, K_RHO0, K_INVRHO0, K_CMU, K_RREF, K_R0, K_RHOOUT, K_GUO };
 
 // Kernel launchers (defined in amlbm_step.cu).  storage = AMLBM_STORE_*.
 // Every launcher returns the cudaGetLastError() of its launch.

@@ -315,6 +315,19 @@ __device__ __forceinline__ void sources(T S_, T Hz, T Hr, T* h) {
   for (int i = 1; i < 9; ++i) h[i] = lit<T>(w_(i)) * (S_ + cdot(i, z3, r3));
   h[0] = S_ - ((h[2] + h[4]) + ((h[1] + h[3]) + ((h[5] + h[6]) + (h[7] + h[8]))));
 }
+// Discrete force of the Guo forcing (Guo, Zheng & Shi 2002):
+//   s_i = W_i (3 (c_i . F - u . F) + 9 (c_i . u)(c_i . F)),
+// with s_0 = -sum_{i>0} s_i (zeroth moment 0 to rounding; first moment F).
+template <class T>
+__device__ __forceinline__ void guo_force(T uz, T ur, T Fz, T Fr, T* s) {
+  const T uF = fma(uz, Fz, ur * Fr);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const T cF = cdot(i, Fz, Fr), cu = cdot(i, uz, ur);
+    s[i] = lit<T>(w_(i)) * fma(cu * lit<T>(9.0), cF, (cF - uF) * lit<T>(3.0));
+  }
+  s[0] = -((s[2] + s[4]) + ((s[1] + s[3]) + ((s[5] + s[6]) + (s[7] + s[8]))));
+}
 // Shan-Chen neighbour sums sum_i W_i psi(x + c_i) c_i (Eq. scforce) around p.
 template <class T>
 __device__ __forceinline__ void sc_sums(const T* p, int Z, T& sz, T& sr) {
@@ -546,6 +559,7 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
   // row at row 0, an outlet row at row Nr - 1
   const bool zw = D.zbc == AMLBM_Z_NOSLIP;
   const bool inl = D.rlo == AMLBM_RLO_INLET, outl = D.wall == AMLBM_WALL_OUTLET;
+  const bool guo = D.forcing == AMLBM_FORCE_GUO;
 
   for (int i = threadIdx.x; i < G::PZ; i += NT) colmap[i] = ghost_col(k0 - G::HP + i, Nz, zw);
   for (int i = threadIdx.x; i < G::PR; i += NT) rowmap[i] = ghost_row(j0 - G::HP + i, Nr, inl, outl);
@@ -622,12 +636,21 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       }
     }
     if ((MODE == 0 || MODE == 3) && srow && lc >= 2 && lc < G::FZ - 2) {
-      const T vz = fma(Fz, q.tau, jz) * inv_rho, vr = fma(Fr, q.tau, jr) * inv_rho;
-      T fe[9];
-      equilibrium(rho, vz, vr, fe);
       T* out = sFs + (lr - 2) * G::SZ + (lc - 2);
+      T fe[9];
+      if (guo) {  // f^eq at u, plus (1 - 1/(2 tau)) times the discrete force
+        equilibrium(rho, uz, ur, fe);
+        T s[9];
+        guo_force(uz, ur, Fz, Fr, s);
+        const T gk = splat<T>(kc(D, K_GUO, C()));
 #pragma unroll
-      for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(fe[i] - f[i], q.omega, f[i]);
+        for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(s[i], gk, fma(fe[i] - f[i], q.omega, f[i]));
+      } else {    // the velocity shift: f^eq at u^eq
+        const T vz = fma(Fz, q.tau, jz) * inv_rho, vr = fma(Fr, q.tau, jr) * inv_rho;
+        equilibrium(rho, vz, vr, fe);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(fe[i] - f[i], q.omega, f[i]);
+      }
     }
   });
   __syncthreads();

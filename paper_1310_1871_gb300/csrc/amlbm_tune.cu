@@ -59,11 +59,13 @@ extern "C" int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void
   long long sites = 0;
   for (int i = 0; i < n; ++i) sites += (long long)inst[i].Nz * inst[i].Nr;
 
-  // lattices with walls in z, an inlet or an outlet run on the fused schedule only
+  // lattices with walls in z, an inlet, an outlet or the Guo forcing run on the
+  // fused schedule only
   bool fused_only = false;
   for (int i = 0; i < n; ++i)
     fused_only = fused_only || inst[i].bc.z_bc != AMLBM_Z_PERIODIC ||
-                 inst[i].bc.r_lo != AMLBM_RLO_AXIS || inst[i].bc.wall_r == AMLBM_WALL_OUTLET;
+                 inst[i].bc.r_lo != AMLBM_RLO_AXIS || inst[i].bc.wall_r == AMLBM_WALL_OUTLET ||
+                 inst[i].bc.forcing != AMLBM_FORCE_SHIFT;
   int timed = 0;
   double best_ms = 1e300;
   for (int sched = AMLBM_SCHED_FUSED; sched <= (fused_only ? AMLBM_SCHED_FUSED : AMLBM_SCHED_SPLIT); ++sched) {

@@ -64,7 +64,7 @@ def test_bad_flags_and_tiles_rejected(lib):
 @pytest.mark.parametrize("Nz,Nr,kw", [
     (16, 16, dict(z_bc=2)), (16, 16, dict(r_lo=2)), (16, 16, dict(r_off=1.0)),
     (16, 16, dict(r_lo="inlet", r_off=-1.0)), (16, 16, dict(r_lo="inlet", r_off=float("inf"))),
-    (16, 16, dict(wall="outlet", rho_out=0.0)), (3, 16, dict(z_bc="noslip")),
+    (16, 16, dict(wall="outlet", rho_out=0.0)), (3, 16, dict(z_bc="noslip")), (16, 16, dict(forcing=2)),
     (16, 5, dict(r_lo="inlet", r_off=2.0)), (16, 5, dict(wall="outlet"))])
 def test_bounded_domain_arguments_rejected(lib, Nz, Nr, kw):
     """Walls in z, inlet and outlet rows: bad codes, an off-axis lattice with the
@@ -76,10 +76,12 @@ def test_bounded_domain_arguments_rejected(lib, Nz, Nr, kw):
     assert h.value is None
 
 
-def test_bounded_domain_needs_fused_schedule(lib):
-    """The split schedule takes periodic lattices on the axis only."""
+@pytest.mark.parametrize("kw", [dict(z_bc="noslip", r_lo="inlet", r_off=9.0, wall="outlet"),
+                                dict(forcing="guo")])
+def test_bounded_domain_and_guo_need_fused_schedule(lib, kw):
+    """The split schedule takes periodic lattices on the axis with the velocity shift only."""
     h = ctypes.c_void_p()
-    bc = amlbm.make_bc(z_bc="noslip", r_lo="inlet", r_off=9.0, wall="outlet")
+    bc = amlbm.make_bc(**kw)
     inst = (amlbm.InstanceC * 1)(amlbm.InstanceC(32, 111, 1.0, 0.0, 1.0, bc))
     tune = amlbm.Tune(32, 8, 0, amlbm.SCHEDULE["split"])
     assert lib.amlbm_batch_create(1, inst, ctypes.byref(tune), None, None, 0, ctypes.byref(h)) == amlbm.EINVAL
@@ -93,7 +95,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("no C compiler")
     structs = {"amlbm_bc": amlbm.BC, "amlbm_instance": amlbm.InstanceC, "amlbm_tune": amlbm.Tune,
-               "amlbm_diag": amlbm.Diag, "amlbm_diag_params": amlbm.DiagParams}
+               "amlbm_diag": amlbm.Diag, "amlbm_diag_params": amlbm.DiagParams,
+               "amlbm_interface": amlbm.Interface}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "amlbm.h"', 'int main(void) {']
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
@@ -110,6 +113,21 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+@pytest.mark.parametrize("args", [
+    (-5.0, 1.0, 1.0, 0, 0, 2, 64, 100, 2.0, 0.15),   # FP16 storage
+    (-5.0, 1.0, 1.0, 0, 0, 0, 7, 100, 2.0, 0.15),    # n < 8
+    (-5.0, 1.0, 1.0, 0, 0, 0, 64, -1, 2.0, 0.15),    # steps < 0
+    (-5.0, 1.0, 1.0, 0, 0, 0, 64, 100, 0.1, 0.15),   # rho_l0 <= rho_v0
+    (-5.0, 1.0, 1.0, 0, 0, 0, 64, 100, 2.0, 0.0),    # rho_v0 <= 0
+    (-5.0, 1.0, 1.0, 2, 0, 0, 64, 100, 2.0, 0.15),   # bad axisym
+    (-5.0, 1.0, 1.0, 0, 2, 0, 64, 100, 2.0, 0.15)])  # bad forcing
+def test_flat_interface_rejects_bad_arguments(lib, args):
+    """amlbm_flat_interface validates before any device work."""
+    out = amlbm.Interface()
+    assert lib.amlbm_flat_interface(*args, None, ctypes.byref(out)) == amlbm.EINVAL
+    assert b"flat interface" in lib.amlbm_last_error()
 
 
 def test_tile_lists_and_workspace_sizes(lib):

@@ -1,0 +1,80 @@
+"""The Guo forcing (AMLBM_FORCE_GUO) on the GPU against the FP64 oracle: parity of
+whole runs (FP64 to 1e-11, FP32 to 1e-4 in rho), and the flat-interface tool's gamma
+against Table I's Guo columns (within the 6 % the oracle meets)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1310_1871_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1310_1871_gb300 import amlbm  # noqa: E402
+
+WALLS = {0: "freeslip", 1: "noslip"}
+
+
+def run_pair(Nz, Nr, steps, fields, tau, G, wall=0, axisym=1, src=0, gz=0.0, storage="f64", tile=None,
+             z_bc="periodic"):
+    o = O.Oracle(Nz, Nr, tau=tau, G=G, gz=gz, wall=wall, axisym=axisym, src_mode=src, forcing=O.FORCE_GUO,
+                 zbc=O.Z_NOSLIP if z_bc == "noslip" else O.Z_PERIODIC)
+    f_ref = o.run(o.init(*fields), steps)
+    spec = amlbm.InstanceSpec(Nz, Nr, tau, G, 1.0, WALLS[wall], bool(axisym), "link" if src else "local", gz,
+                              1.0, "default", "nearest", z_bc, "axis", 0.0, 1.0, "guo")
+    b = amlbm.Batch([spec], storage=storage, tile=tile)
+    b.init_fields(0, *fields)
+    b.step(steps)
+    f_gpu, (rho, uz, ur) = b.read_f(0), b.read(0)
+    b.close()
+    return f_gpu, f_ref, (rho, uz, ur), o.fields(f_ref)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("wall,src,axisym,gz,tau,G,z_bc", [
+    (0, 0, 1, 0.0, 1.0, -5.0, "periodic"), (1, 0, 1, 1e-4, 0.8, -4.6, "periodic"),
+    (0, 1, 1, 0.0, 0.9, -5.0, "periodic"), (0, 0, 0, 0.0, 1.0, -5.5, "periodic"),
+    (1, 0, 1, 0.0, 0.9, -5.0, "noslip")])
+def test_fp64_guo_parity(wall, src, axisym, gz, tau, G, z_bc):
+    """300 steps of a perturbed drop on 70 x 45 (ragged tiles): FP64 within 1e-11."""
+    fields = I.drop(70, 45, 34.5, 12.0, amps=(0.08,))
+    f_gpu, f_ref, (rho, uz, ur), F = run_pair(70, 45, 300, fields, tau, G, wall, axisym, src, gz, tile=(32, 8),
+                                              z_bc=z_bc)
+    assert rel(f_gpu, f_ref) < 1e-11
+    assert np.abs(rho / F["rho"] - 1).max() < 1e-11
+    umax = max(np.abs(F["uz"]).max(), np.abs(F["ur"]).max())
+    assert max(np.abs(uz - F["uz"]).max(), np.abs(ur - F["ur"]).max()) / umax < 1e-11
+
+
+def test_fp32_guo_static_drop():
+    """The static-drop workload (64 x 32, 1000 steps) with FP32 storage, rho within 1e-4."""
+    fields = I.drop(64, 32, 32.0, 12.0)
+    _, _, (rho, _, _), F = run_pair(64, 32, 1000, fields, 1.0, -5.0, storage="f32")
+    assert np.abs(rho / F["rho"] - 1).max() < 1e-4
+
+
+@pytest.mark.parametrize("G,g2d,gax", [(-4.5, 0.0135, 0.0136), (-5.0, 0.0376, 0.0378), (-5.5, 0.0681, 0.0683)])
+def test_table_I_guo_columns_on_gpu(G, g2d, gax):
+    """The tool's gamma (Eq. st) with the Guo forcing, within 6 % of Table I, and the
+    oracle's own value to 1e-10 (same slab, same steps)."""
+    a = amlbm.flat_interface(G, axisym=True, forcing="guo")
+    b = amlbm.flat_interface(G, axisym=False, forcing="guo")
+    assert abs(a["gamma"] / gax - 1) < 0.06
+    assert abs(b["gamma"] / g2d - 1) < 0.06
+    o = O.Oracle(1, 64, tau=1.0, G=G, axisym=0, forcing=O.FORCE_GUO)
+    F = o.fields(o.run(o.init(I.slab(1, 64, 32.0, 2.0, 0.15)[0]), 20000))
+    assert abs(b["gamma"] / (-(G / 18) * np.sum(F["Dr"] ** 2)) - 1) < 1e-10
+
+
+def test_guo_adjoint_rejected():
+    lat = amlbm.Lattice(48, 24, tau=0.9, G=-5.0, forcing="guo")
+    with pytest.raises(amlbm.AmlbmError) as e:
+        lat.adjoint(4, I.legendre_amplitudes(4), 24.0, 8.0)
+    assert e.value.code == amlbm.EINVAL
+    lat.close()
