@@ -384,7 +384,9 @@ int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, 
  * hold all instances back to back in instance order: instance k's [Nr][Nz]
  * block starts at the sum of Nz*Nr over the instances before it, and the total
  * length is amlbm_batch_sites().  uz and ur may be NULL (zero velocity).  One
- * host-to-device copy per array and one kernel launch; rho is checked on the
+ * kernel launch; it reads page-locked (pinned) host arrays in place over the
+ * CPU-GPU link, and any other array is first copied to the device (one
+ * host-to-device copy per array).  The arrays are read during the call only.  rho is checked on the
  * device and the call returns AMLBM_EINVAL, with every instance's state
  * unchanged, if any value is not positive and finite.  Resets every instance's
  * step count and restarts the stochastic-rounding stream, so that the steps

@@ -149,7 +149,7 @@ int validate(const amlbm_instance& I, int idx) {
 struct Layout {
   size_t total = 0;
   size_t desc = 0, tiles = 0, rb_tiles = 0, ctr = 0, diag_part = 0, diag_cols = 0, diag_out = 0, upload = 0,
-         unpack = 0, site_off = 0, diag_jobs = 0;
+         unpack = 0, site_off = 0, diag_jobs = 0, diag_blkjob = 0;
   std::vector<size_t> f0, f1, p0, p1, uv, rho, uz, ur, inlet;
   int ntiles = 0, rb_ntiles = 0, maxN = 0, maxNz = 0, diag_nblk = 1;
   int all_nblk = 0;  // partial-sum blocks of a diagnostics pass over every instance
@@ -163,7 +163,9 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   const size_t n = inst.size();
   for (const auto& I : inst) {
     L.ntiles += ((I.Nz + tz - 1) / tz) * ((I.Nr + tr - 1) / tr);
-    L.rb_ntiles += ((I.Nz + 31) / 32) * ((I.Nr + 7) / 8);
+    int rz, rr;
+    amlbm::rb_tile(storage, &rz, &rr);
+    L.rb_ntiles += ((I.Nz + rz - 1) / rz) * ((I.Nr + rr - 1) / rr);
     L.maxN = std::max(L.maxN, I.Nz * I.Nr);
     L.maxNz = std::max(L.maxNz, I.Nz);
     L.diag_nblk = std::max(L.diag_nblk, amlbm::diag_blocks(I.Nz, I.Nr));
@@ -179,6 +181,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   L.diag_cols = take((size_t)L.sumNz * sizeof(double));
   L.diag_out = take(16 * n * sizeof(double));
   L.diag_jobs = take(n * sizeof(amlbm::DiagJob));
+  L.diag_blkjob = take((size_t)std::max(1, L.all_nblk) * sizeof(int));
   L.site_off = take((n + 1) * sizeof(long long));
   L.upload = take((size_t)3 * L.sumN * sizeof(double));
   L.unpack = take((size_t)9 * L.maxN * sizeof(double));
@@ -354,8 +357,10 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.tiles_z = (I.Nz + tz - 1) / tz;
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
-    d.rb_tiles_z = (I.Nz + 31) / 32;
-    d.rb_tiles_r = (I.Nr + 7) / 8;
+    int rz, rr;
+    amlbm::rb_tile(storage, &rz, &rr);
+    d.rb_tiles_z = (I.Nz + rz - 1) / rz;
+    d.rb_tiles_r = (I.Nr + rr - 1) / rr;
     d.rb_tile_base = (int)rb_tiles.size();
     d.tau = I.tau;
     d.G = I.G;
@@ -374,9 +379,9 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.psi[0] = b->arena + L.p0[i];
     d.psi[1] = b->arena + L.p1[i];
     d.uv = b->arena + L.uv[i];
-    d.rho_out = reinterpret_cast<double*>(b->arena + L.rho[i]);
-    d.uz_out = reinterpret_cast<double*>(b->arena + L.uz[i]);
-    d.ur_out = reinterpret_cast<double*>(b->arena + L.ur[i]);
+    d.rho_out = b->arena + L.rho[i];
+    d.uz_out = b->arena + L.uz[i];
+    d.ur_out = b->arena + L.ur[i];
     d.inlet = reinterpret_cast<const double*>(b->arena + L.inlet[i]);
     for (int t = 0; t < d.tiles_z * d.tiles_r; ++t) tiles.push_back(i);
     for (int t = 0; t < d.rb_tiles_z * d.rb_tiles_r; ++t) rb_tiles.push_back(i);
@@ -403,6 +408,14 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   for (int i = 0; i < b->n; ++i) off[i + 1] = off[i] + (long long)inst[i].Nz * inst[i].Nr;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->arena + L.site_off, off.data(), off.size() * sizeof(long long),
+                        cudaMemcpyHostToDevice, b->stream);
+  // the instance of every block of a whole-batch diagnostics pass
+  std::vector<int> blkjob;
+  blkjob.reserve(L.all_nblk);
+  for (int i = 0; i < b->n; ++i)
+    for (int q = 0; q < amlbm::diag_blocks(inst[i].Nz, inst[i].Nr); ++q) blkjob.push_back(i);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->arena + L.diag_blkjob, blkjob.data(), blkjob.size() * sizeof(int),
                         cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
@@ -469,7 +482,9 @@ int set_inlet(amlbm_batch* b, int k, const double* uz, const double* ur) {
 int macro_for(amlbm_batch* b, int k) {
   const InstDesc& d = b->desc[k];
   const int nt = d.rb_tiles_z * d.rb_tiles_r;
-  const cudaError_t e = amlbm::launch_macro(b->storage, 32, 8, b->d_desc, b->d_rb_tiles, nt,
+  int rz, rr;
+  amlbm::rb_tile(b->storage, &rz, &rr);
+  const cudaError_t e = amlbm::launch_macro(b->storage, rz, rr, b->d_desc, b->d_rb_tiles, nt,
                                             d.rb_tile_base, b->parity, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
   return AMLBM_OK;
@@ -480,12 +495,24 @@ int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double
   if (rc) return rc;
   const InstDesc& d = b->desc[k];
   const size_t N = (size_t)d.Nz * d.Nr;
+  // the read-back holds the compute type: FP64 copies straight into the caller's
+  // arrays, FP32 through host staging, widened after the copy
+  double* dst[3] = {rho, uz, ur};
+  void* srcs[3] = {d.rho_out, d.uz_out, d.ur_out};
+  const bool wide = compute_bytes(b->storage) == 8;
+  std::vector<float> stage[3];
   if (rho || uz || ur) {
     rc = macro_for(b, k);
     if (rc) return rc;
-    if (rho) AMLBM_CK(cudaMemcpyAsync(rho, d.rho_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-    if (uz) AMLBM_CK(cudaMemcpyAsync(uz, d.uz_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
-    if (ur) AMLBM_CK(cudaMemcpyAsync(ur, d.ur_out, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    for (int q = 0; q < 3; ++q) {
+      if (!dst[q]) continue;
+      if (wide) {
+        AMLBM_CK(cudaMemcpyAsync(dst[q], srcs[q], N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+      } else {
+        stage[q].resize(N);
+        AMLBM_CK(cudaMemcpyAsync(stage[q].data(), srcs[q], N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+      }
+    }
   }
   if (f) {
     double* un = reinterpret_cast<double*>(b->arena + b->L.unpack);
@@ -494,6 +521,9 @@ int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double
     AMLBM_CK(cudaMemcpyAsync(f, un, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
   }
   AMLBM_CK(cudaStreamSynchronize(b->stream));
+  for (int q = 0; q < 3; ++q)
+    if (dst[q] && !wide)
+      for (size_t n = 0; n < N; ++n) dst[q][n] = double(stage[q][n]);
   return AMLBM_OK;
 }
 
@@ -514,6 +544,18 @@ amlbm_diag_params diag_defaults(const InstDesc& d) {
 // Every instance from host arrays holding them back to back.  The new state is
 // written into the buffers of the other parity, and becomes current only when
 // the device check finds every rho positive and finite.
+// Device address of a host array the GPU can read in place (page-locked memory,
+// mapped into the unified address space), or nullptr.
+const double* device_view(const double* h) {
+  if (!h) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const double*>(a.devicePointer) : nullptr;
+}
+
 int init_all_host(amlbm_batch* b, const double* rho, const double* uz, const double* ur) {
   if (!b) return fail(AMLBM_EINVAL, "NULL batch");
   if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
@@ -521,12 +563,21 @@ int init_all_host(amlbm_batch* b, const double* rho, const double* uz, const dou
   double* st = reinterpret_cast<double*>(b->arena + b->L.upload);
   const long long* off = reinterpret_cast<const long long*>(b->arena + b->L.site_off);
   int* bad = b->d_ctr + 4;
-  AMLBM_CK(cudaMemcpyAsync(st, rho, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-  if (uz) AMLBM_CK(cudaMemcpyAsync(st + T, uz, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-  if (ur) AMLBM_CK(cudaMemcpyAsync(st + 2 * T, ur, T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  // Page-locked host arrays are read by the init kernel in place (over the
+  // CPU-GPU link, without a separate copy); others are copied to the device first.
+  const double* src[3] = {rho, uz, ur};
+  const double* dev[3] = {nullptr, nullptr, nullptr};
+  for (int q = 0; q < 3; ++q) {
+    if (!src[q]) continue;
+    dev[q] = device_view(src[q]);
+    if (!dev[q]) {
+      AMLBM_CK(cudaMemcpyAsync(st + q * T, src[q], T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+      dev[q] = st + q * T;
+    }
+  }
   AMLBM_CK(cudaMemsetAsync(bad, 0, sizeof(int), b->stream));
-  const cudaError_t e = amlbm::launch_init_all(b->storage, b->d_desc, b->n, off, T, st, uz ? st + T : nullptr,
-                                               ur ? st + 2 * T : nullptr, b->parity ^ 1, bad, b->stream);
+  const cudaError_t e = amlbm::launch_init_all(b->storage, b->d_desc, b->n, off, T, dev[0], dev[1], dev[2],
+                                               b->parity ^ 1, bad, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("init kernel: ") + cudaGetErrorString(e));
   int nbad = 0;
   AMLBM_CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
@@ -557,6 +608,7 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
       return fail(AMLBM_EINVAL, "diag params of instance " + std::to_string(k) + ": need R > 0, rho_l != rho_v");
     amlbm::DiagJob& J = jobs[k];
     J.zc = p.zc; J.R = p.R; J.rho_l = p.rho_l; J.rho_v = p.rho_v;
+    J.a2norm = amlbm::a2_norm(p.R);
     J.inst = k;
     J.blk0 = blk;
     J.nblk = amlbm::diag_blocks(d.Nz, d.Nr);
@@ -581,13 +633,17 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
     if (!b->pin) AMLBM_CK(cudaStreamSynchronize(b->stream));  // the pageable source goes out of scope
     b->last_jobs = jobs;
   }
-  cudaError_t e = amlbm::launch_macro(b->storage, 32, 8, b->d_desc, b->d_rb_tiles, b->L.rb_ntiles, 0,
+  int rz, rr;
+  amlbm::rb_tile(b->storage, &rz, &rr);
+  cudaError_t e = amlbm::launch_macro(b->storage, rz, rr, b->d_desc, b->d_rb_tiles, b->L.rb_ntiles, 0,
                                       b->parity, b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
   double* part = reinterpret_cast<double*>(b->arena + b->L.diag_part);
   double* cols = reinterpret_cast<double*>(b->arena + b->L.diag_cols);
   double* res = reinterpret_cast<double*>(b->arena + b->L.diag_out);
-  e = amlbm::launch_diag_all(b->storage, b->d_desc, d_jobs, b->n, blk, b->parity, part, cols, res, b->stream);
+  const int* blkjob = reinterpret_cast<const int*>(b->arena + b->L.diag_blkjob);
+  e = amlbm::launch_diag_all(b->storage, b->d_desc, d_jobs, blkjob, b->n, blk, b->parity, part, cols, res,
+                             b->stream);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("diag kernels: ") + cudaGetErrorString(e));
   std::vector<double> hv;
   double* h = b->pin ? reinterpret_cast<double*>(b->pin + jbytes) : nullptr;

@@ -512,10 +512,10 @@ __global__ void seed_kernel(int kind, int Nz, int Nr, int P, size_t plane, doubl
 }
 
 // J of the neck objective from the read-back density (one thread)
-__global__ void neck_kernel(const double* rho, int Nz, int Nr, int kstar, double rho_l, double rho_v,
-                            double* J) {
+template <class C>
+__global__ void neck_kernel(const C* rho, int Nz, int Nr, int kstar, double rho_l, double rho_v, double* J) {
   double s = 0.0;
-  for (int j = 0; j < Nr; ++j) s += (j + 0.5) * (rho[(size_t)j * Nz + kstar] - rho_v) / (rho_l - rho_v);
+  for (int j = 0; j < Nr; ++j) s += (j + 0.5) * (double(rho[(size_t)j * Nz + kstar]) - rho_v) / (rho_l - rho_v);
   *J = sqrt(2.0 * s);
 }
 
@@ -670,7 +670,8 @@ int run(amlbm_ctx* ctx, const amlbm_adjoint_problem* p, void* ws, size_t ws_byte
         ADJ_CK(cudaStreamSynchronize(s));
         Jv = a2 * a2;
       } else {
-        neck_kernel<<<1, 1, 0, s>>>(ci.host.rho_out, Nz, Nr, p->kstar, p->rho_l, p->rho_v, redbuf);
+        neck_kernel<C><<<1, 1, 0, s>>>(static_cast<const C*>(ci.host.rho_out), Nz, Nr, p->kstar, p->rho_l,
+                                       p->rho_v, redbuf);
         ADJ_CK(cudaGetLastError());
         ADJ_CK(cudaMemcpyAsync(&Jv, redbuf, sizeof(double), cudaMemcpyDeviceToHost, s));
         ADJ_CK(cudaStreamSynchronize(s));

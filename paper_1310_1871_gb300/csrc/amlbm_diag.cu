@@ -13,7 +13,7 @@
 //   of state of Sec. II.B with c_s^2 = 1/3) inside and outside the drop.
 //
 // The read-back kernel must have written rho, u_z, u_r of the state into the
-// instance's rho_out / uz_out / ur_out arrays first.
+// instance's rho_out / uz_out / ur_out arrays first (in the compute type C).
 
 #include <cuda_runtime.h>
 
@@ -39,6 +39,20 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+template <class C>
+__device__ __forceinline__ C warp_sum_t(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class C>
+__device__ __forceinline__ C warp_max_t(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -49,18 +63,22 @@ __device__ __forceinline__ double warp_min(double v) {
 // density is below mid, interpolated linearly against the row before it; r0 - 1/2
 // (the axis, or the lattice's inner edge) when row 0 is already below, Nr + r0 - 1/2
 // when no row is.  r0 is the radius of row 0.  Rows are scanned 32 at a time.
-__device__ double col_radius_warp(const double* __restrict__ rho, int Nz, int Nr, int k, double mid,
-                                  double r0) {
+template <class C>
+__device__ double col_radius_warp(const C* __restrict__ rho, int Nz, int Nr, int k, double mid, double r0) {
+  const C midc = C(mid);
   const int lane = threadIdx.x & 31;
   for (int j0 = 0; j0 < Nr; j0 += 32) {
     const int j = j0 + lane;
-    const bool below = j < Nr && rho[(size_t)j * Nz + k] < mid;
+    const bool below = j < Nr && rho[(size_t)j * Nz + k] < midc;
     const unsigned m = __ballot_sync(0xffffffffu, below);
-    if (m) {
+    if (m) {  // one lane interpolates (an FP64 division), the others take its value
       const int jf = j0 + __ffs(m) - 1;
-      if (jf == 0) return r0 - 0.5;
-      const double v0 = rho[(size_t)(jf - 1) * Nz + k], v = rho[(size_t)jf * Nz + k];
-      return (jf - 1 + r0) + (v0 - mid) / (v0 - v);
+      double res = r0 - 0.5;
+      if (lane == 0 && jf > 0) {  // the fraction in C (an FP64 division is slow here)
+        const C v0 = rho[(size_t)(jf - 1) * Nz + k], v = rho[(size_t)jf * Nz + k];
+        res = (jf - 1 + r0) + double((v0 - midc) / (v0 - v));
+      }
+      return __shfl_sync(0xffffffffu, res, 0);
     }
   }
   return Nr + r0 - 0.5;
@@ -73,9 +91,11 @@ __device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
 // blk*NT + tid + m*nblk*NT into partials[(J.blk0 + blk) * NSUM + q], and the
 // radii of the columns blk*WARPS + warp + m*nblk*WARPS into cols[J.col0 + k].
 // The per-site terms are formed in the arithmetic type C of the storage form
-// (its values are no more precise than that) and accumulated in FP64; FP64 runs
-// at a small fraction of the FP32 rate on GB300, so there is no division or
-// square root per site (|u|^2 is max-reduced, its root taken once at the end).
+// (its values are no more precise than that) and summed per thread and per warp
+// in C, then across warps and blocks in FP64; FP64 runs at a small fraction of
+// the FP32 rate on GB300, so there is no FP64 operation, division or square root
+// per site or lane (|u|^2 is max-reduced, its root taken once at the end).  The
+// FP64 form (C = double) is FP64 throughout.
 template <class C>
 __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, double* partials,
                               double* cols) {
@@ -83,27 +103,38 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   const C two_pi = C(2.0 * 3.14159265358979323846);
   const C inv_dl = C(1.0 / (J.rho_l - J.rho_v)), rho_v = C(J.rho_v), zc = C(J.zc);
   const C r0 = sizeof(C) == 8 ? C(D.k64[K_R0]) : C(D.k32[K_R0]);
-  double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const C* __restrict__ rho_o = static_cast<const C*>(D.rho_out);
+  const C* __restrict__ uz_o = static_cast<const C*>(D.uz_out);
+  const C* __restrict__ ur_o = static_cast<const C*>(D.ur_out);
+  // Each thread first adds its own few sites (about four) in C, then the block
+  // and the final pass reduce those per-thread sums in FP64: the FP32 forms then
+  // need one FP64 conversion and addition per sum and thread, not per site.
+  C tacc[NSUM] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
   for (int n = blk * DIAG_NT + threadIdx.x; n < N; n += J.nblk * DIAG_NT) {
     const int j = n / Nz, k = n - j * Nz;
-    const C r = C(j) + r0, rho = C(D.rho_out[n]), uz = C(D.uz_out[n]), ur = C(D.ur_out[n]);
+    const C r = C(j) + r0, rho = rho_o[n], uz = uz_o[n], ur = ur_o[n];
     const C u2 = uz * uz + ur * ur, w = two_pi * r * rho;
-    acc[0] += double(rho);
-    acc[1] += double(w);
-    acc[2] += double(w * uz);
-    acc[3] += double(C(0.5) * w * u2);
+    tacc[0] += rho;
+    tacc[1] += w;
+    tacc[2] += w * uz;
+    tacc[3] += C(0.5) * w * u2;
     const C dz = C(k) - zc;
-    acc[4] += double(two_pi * r * ((rho - rho_v) * inv_dl) * (dz * dz - C(0.5) * r * r));
-    acc[5] += double(-rho * ur * rcp_t(r));
+    tacc[4] += two_pi * r * ((rho - rho_v) * inv_dl) * (dz * dz - C(0.5) * r * r);
+    tacc[5] += -rho * ur * rcp_t(r);
     const bool bad = !(rho > C(0)) || !isfinite(rho) || !isfinite(u2);
-    acc[6] += bad ? 1.0 : 0.0;
-    acc[7] = fmax(acc[7], bad ? 0.0 : double(u2));
+    tacc[6] += bad ? C(1) : C(0);
+    tacc[7] = fmax(tacc[7], bad ? C(0) : u2);
   }
+  // The warp's sums (128 sites) pairwise in C too, then FP64 across warps and
+  // blocks: the FP32 forms convert 8 values per warp instead of per thread.
+#pragma unroll
+  for (int q = 0; q < NSUM - 1; ++q) tacc[q] = warp_sum_t(tacc[q]);
+  tacc[NSUM - 1] = warp_max_t(tacc[NSUM - 1]);
+  double acc[NSUM];
+#pragma unroll
+  for (int q = 0; q < NSUM; ++q) acc[q] = double(tacc[q]);
   __shared__ double red[DIAG_WARPS][NSUM];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NSUM - 1; ++q) acc[q] = warp_sum(acc[q]);
-  acc[NSUM - 1] = warp_max(acc[NSUM - 1]);
   if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < NSUM; ++q) red[warp][q] = acc[q];
@@ -117,7 +148,7 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   }
   const double mid = 0.5 * (J.rho_l + J.rho_v);
   for (int k = blk * DIAG_WARPS + warp; k < Nz; k += J.nblk * DIAG_WARPS) {
-    const double rad = col_radius_warp(D.rho_out, Nz, Nr, k, mid, D.k64[K_R0]);
+    const double rad = col_radius_warp<C>(rho_o, Nz, Nr, k, mid, D.k64[K_R0]);
     if (lane == 0) cols[J.col0 + k] = rad;
   }
 }
@@ -146,23 +177,26 @@ __device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, con
     for (int q = 0; q <= NSUM; ++q) red[warp][q] = acc[q];
   }
   __syncthreads();
+  // one thread per quantity across the warps (short FP64 chains), then thread 0
+  __shared__ double tot[NSUM + 1];
+  if (threadIdx.x <= NSUM) {
+    const int q = threadIdx.x;
+    double v = red[0][q];
+    for (int w = 1; w < DIAG_WARPS; ++w)
+      v = q < NSUM - 1 ? v + red[w][q] : (q == NSUM - 1 ? fmax(v, red[w][q]) : fmin(v, red[w][q]));
+    tot[q] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     double t[NSUM + 1];
 #pragma unroll
-    for (int q = 0; q <= NSUM; ++q) t[q] = red[0][q];
-    for (int w = 1; w < DIAG_WARPS; ++w) {
-#pragma unroll
-      for (int q = 0; q < NSUM - 1; ++q) t[q] += red[w][q];
-      t[NSUM - 1] = fmax(t[NSUM - 1], red[w][NSUM - 1]);
-      t[NSUM] = fmin(t[NSUM], red[w][NSUM]);
-    }
-    const double pi = 3.14159265358979323846;
+    for (int q = 0; q <= NSUM; ++q) t[q] = tot[q];
     out[0] = t[0];
     out[1] = t[1];
     out[2] = t[2];
     out[3] = t[3];
     out[4] = sqrt(t[7]);
-    out[5] = 5.0 * t[4] / (4.0 * pi * pow(J.R, 5.0));
+    out[5] = t[4] * J.a2norm;
     int kc = (int)llround(J.zc);
     kc %= Nz;
     if (kc < 0) kc += Nz;
@@ -171,7 +205,8 @@ __device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, con
     const C* psi = static_cast<const C*>(D.psi[parity]);
     const double G = D.G;
     auto pres = [&](int k, int j) {
-      const double rho = D.rho_out[(size_t)j * Nz + k], ps = double(psi[(size_t)j * D.P + k]);
+      const double rho = double(static_cast<const C*>(D.rho_out)[(size_t)j * Nz + k]);
+      const double ps = double(psi[(size_t)j * D.P + k]);
       return rho / 3.0 + G * ps * ps / 6.0;
     };
     const int ko = (kc + Nz / 2) % Nz;
@@ -197,19 +232,14 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_one(const InstDesc* __rest
   final_block<C>(descs[J.inst], J, parity, partials, cols, out);
 }
 
-// Every job of a batch: block b belongs to the job whose block range
-// [blk0, blk0 + nblk) holds b (jobs sorted by blk0).
+// Every job of a batch: block b belongs to job blkjob[b] (the host's table of
+// the jobs' block ranges [blk0, blk0 + nblk)).
 template <class C>
 __global__ void __launch_bounds__(DIAG_NT) diag_partial_all(const InstDesc* __restrict__ descs,
-                                                            const DiagJob* __restrict__ jobs, int njobs,
+                                                            const DiagJob* __restrict__ jobs,
+                                                            const int* __restrict__ blkjob,
                                                             double* partials, double* cols) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].blk0 <= (int)blockIdx.x) lo = mid;
-    else hi = mid - 1;
-  }
-  const DiagJob J = jobs[lo];
+  const DiagJob J = jobs[blkjob[blockIdx.x]];
   partial_block<C>(descs[J.inst], J, blockIdx.x - J.blk0, partials, cols);
 }
 
@@ -223,6 +253,8 @@ __global__ void __launch_bounds__(DIAG_NT) diag_final_all(const InstDesc* __rest
 }
 
 }  // namespace
+
+double a2_norm(double R) { return 5.0 / (4.0 * 3.14159265358979323846 * std::pow(R, 5.0)); }
 
 int diag_blocks(int Nz, int Nr) {
   const int N = Nz * Nr;
@@ -243,6 +275,7 @@ cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr
   J.R = R;
   J.rho_l = rho_l;
   J.rho_v = rho_v;
+  J.a2norm = a2_norm(R);
   J.inst = inst;
   J.blk0 = 0;
   J.nblk = nblk;
@@ -257,15 +290,15 @@ cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr
   return cudaGetLastError();
 }
 
-cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_jobs, int njobs,
-                            int total_blocks, int parity, double* partials, double* cols, double* out,
-                            cudaStream_t s) {
+cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_jobs, const int* d_blkjob,
+                            int njobs, int total_blocks, int parity, double* partials, double* cols,
+                            double* out, cudaStream_t s) {
   if (njobs < 1 || total_blocks < 1) return cudaErrorInvalidValue;
   if (storage == AMLBM_STORE_F64) {
-    diag_partial_all<double><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
+    diag_partial_all<double><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, d_blkjob, partials, cols);
     diag_final_all<double><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
   } else {
-    diag_partial_all<float><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, njobs, partials, cols);
+    diag_partial_all<float><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, d_blkjob, partials, cols);
     diag_final_all<float><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
   }
   return cudaGetLastError();

@@ -15,7 +15,7 @@ struct InstDesc {
   int Nz, Nr, P;
   int wall, axisym, src;
   int tiles_z, tiles_r, tile_base;     // tiling of the step kernels
-  int rb_tiles_z, rb_tiles_r, rb_tile_base;  // 32 x 8 tiling of the read-back kernel
+  int rb_tiles_z, rb_tiles_r, rb_tile_base;  // tiling of the read-back kernel (rb_tile())
   int shift;     // 0 none, 1 global (rho_ref), 2 local (rho recovered from psi)
   int rounding;  // 16-bit storage: 0 to nearest, 1 stochastic
   int zbc;       // AMLBM_Z_*: periodic, or no-slip walls at both ends in z
@@ -32,9 +32,12 @@ struct InstDesc {
   void* f[2];
   void* psi[2];
   void* uv;         // split schedule: u_z, u_r, u^eq_z, u^eq_r, 4 planes [Nr][P] of the compute type
-  double* rho_out;  // [Nr][Nz] scratch for read-back and diagnostics
-  double* uz_out;
-  double* ur_out;
+  // [Nr][Nz] read-back of rho, u_z, u_r for the diagnostics and the host, in the
+  // compute type (FP64 for FP64 storage, else FP32: GB300's FP64 path is slow, and
+  // the FP32 forms' values are FP32 numbers anyway); room for FP64 either way
+  void* rho_out;
+  void* uz_out;
+  void* ur_out;
 };
 
 // Slots of InstDesc::k64 / k32.
@@ -54,6 +57,13 @@ cudaError_t launch_step(int storage, int schedule, int tz, int tr, const InstDes
                         int* ctr);
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d_desc,
                          const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
+// Tile of the read-back kernel: 26 x 16 for the FP32-arithmetic forms (less halo
+// work per site than 32 x 8), 32 x 8 for FP64.
+inline void rb_tile(int storage, int* tz, int* tr) {
+  const bool f64 = storage == 0;  // AMLBM_STORE_F64
+  *tz = f64 ? 32 : 26;
+  *tr = f64 ? 8 : 16;
+}
 cudaError_t launch_init(int storage, const InstDesc* d_desc, int inst, int Nz, int Nr,
                         const double* rho, const double* uz, const double* ur, int parity,
                         cudaStream_t s);
@@ -85,13 +95,16 @@ int diag_blocks(int Nz, int Nr);
 // its columns [col0, col0 + Nz) of the radius array.
 struct DiagJob {
   double zc, R, rho_l, rho_v;
+  double a2norm;  // 5 / (4 pi R^5), the normalisation of a2 (computed on the host)
   int inst, blk0, nblk, col0;
 };
-// Every job in one partial launch (total_blocks = sum of nblk) and one final
-// launch (one block per job, out[16 * job]).
-cudaError_t launch_diag_all(int storage, const InstDesc* d_desc, const DiagJob* d_jobs, int njobs,
-                            int total_blocks, int parity, double* partials, double* cols, double* out,
-                            cudaStream_t s);
+// Every job in one partial launch (total_blocks = sum of nblk; d_blkjob[b] is
+// the job of partial block b) and one final launch (one block per job,
+// out[16 * job]).
+cudaError_t launch_diag_all(int storage, const InstDesc* d_desc, const DiagJob* d_jobs, const int* d_blkjob,
+                            int njobs, int total_blocks, int parity, double* partials, double* cols,
+                            double* out, cudaStream_t s);
+double a2_norm(double R);
 // f = f^eq(rho, u) for every instance from device arrays holding all
 // instances back to back (site_off: n + 1 prefix offsets); counts the sites
 // whose rho is not positive and finite into *bad (which must start at zero).

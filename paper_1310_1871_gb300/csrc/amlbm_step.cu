@@ -661,9 +661,9 @@ __device__ __forceinline__ void lbm_tile(const InstDesc* __restrict__ descs,
       if (j >= Nr || k >= Nz) return;
       const int fi = (lr + G::HF) * G::FZ + (lc + G::HF);
       const size_t o = (size_t)j * Nz + k;
-      D.rho_out[o] = double((sRho[fi]).v);
-      D.uz_out[o] = double((sUz[fi]).v);
-      D.ur_out[o] = double((sUr[fi]).v);
+      static_cast<C*>(D.rho_out)[o] = (sRho[fi]).v;
+      static_cast<C*>(D.uz_out)[o] = (sUz[fi]).v;
+      static_cast<C*>(D.ur_out)[o] = (sUr[fi]).v;
     });
     return;
   }
@@ -1299,8 +1299,11 @@ cudaError_t dispatch(bool macro, int sched, int tz, int tr, const InstDesc* d, c
   if (tz == TZ && tr == TR)                                                  \
     return macro ? launch_t<S, T, TZ, TR, 1>(d, ti, nt, toff, par, s)        \
                  : launch_t<S, T, TZ, TR, 0>(d, ti, nt, toff, par, s, nullptr, 0, ctr);
-  if (macro) {  // read-back always uses a fused tile compiled for every storage
+  if (macro) {  // read-back: 32 x 8 for every storage, 26 x 16 for the FP32-arithmetic forms
     AMLBM_TILE(32, 8)
+    if constexpr (!std::is_same<S, double>::value) {
+      AMLBM_TILE(26, 16)
+    }
     return cudaErrorInvalidValue;
   }
   AMLBM_TILE(32, 8)

@@ -136,3 +136,37 @@ def test_diagnostics_all_array_forms_and_repeated_calls():
         one = b.diagnostics(k, zc=arr2[k, 0], R=arr2[k, 1], rho_l=1.93, rho_v=0.16)
         assert [res2[k, m] for m in range(len(amlbm.DIAG_FIELDS))] == [one[f] for f in amlbm.DIAG_FIELDS]
     b.close()
+
+
+def _pinned(a):
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+    return t, t.numpy()
+
+
+def test_init_all_reads_pinned_host_arrays_in_place():
+    """Page-locked arrays are read by the init kernel in place; the state is bit for bit
+    the one of the copy path, also with pinned and pageable arrays mixed, and a bad
+    density in a pinned array is still rejected with the state kept."""
+    a, fields = make("bf16")
+    b, _ = make("bf16")
+    cols = [np.concatenate([np.ravel(fl[q]) for fl in fields]) for q in range(3)]
+    keep = [_pinned(c) for c in cols]  # the tensors own the pinned buffers
+    a.init_all(*cols)
+    b.init_all(keep[0][1], keep[1][1], cols[2])
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    b.init_all(*[p[1] for p in keep])
+    a.step(12)
+    b.step(12)
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    before = [b.read_f(k) for k in range(len(fields))]
+    bad = _pinned(cols[0])
+    bad[1][17] = -2.0
+    with pytest.raises(amlbm.AmlbmError) as e:
+        b.init_all(bad[1], keep[1][1], keep[2][1])
+    assert e.value.code == amlbm.EINVAL and "1 sites" in str(e.value)
+    for k in range(len(fields)):
+        assert np.array_equal(b.read_f(k), before[k]), k
+    a.close()
+    b.close()
