@@ -1156,17 +1156,19 @@ __global__ void init_all_kernel(const InstDesc* __restrict__ descs, int n_inst,
                                 int parity, int* bad) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
+  // the inputs first (they may be host memory read over the CPU-GPU link): their
+  // latency overlaps the search for the instance
+  const double rho = rho_in[g];
+  const double uz = uz_in ? uz_in[g] : 0.0, ur = ur_in ? ur_in[g] : 0.0;
   int lo = 0, hi = n_inst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (site_off[mid] <= g) lo = mid;
     else hi = mid - 1;
   }
-  const double rho = rho_in[g];
   const bool ok = rho > 0 && isfinite(rho);
   if (!ok) atomicAdd(bad, 1);
-  init_site<S>(descs[lo], (int)(g - site_off[lo]), ok ? rho : 1.0, uz_in ? uz_in[g] : 0.0,
-               ur_in ? ur_in[g] : 0.0, parity);
+  init_site<S>(descs[lo], (int)(g - site_off[lo]), ok ? rho : 1.0, uz, ur, parity);
 }
 
 template <class S>
