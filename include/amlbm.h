@@ -199,7 +199,9 @@ int amlbm_diagnostics(amlbm_ctx* ctx, const amlbm_diag_params* dp, amlbm_diag* o
 
 /* Copy the full state (populations, psi, the stored velocity of the equilibrium
  * shift, the step count and the position of the stochastic-rounding stream) to /
- * from a host buffer, so that a restarted run continues bit for bit.
+ * from a host buffer, so that a restarted run continues bit for bit.  The inlet
+ * velocity of amlbm_set_inlet is configuration, not state: the context that
+ * loads needs the same call.
  * amlbm_save_state with buf == NULL stores the needed size in *len. */
 int amlbm_save_state(amlbm_ctx* ctx, void* buf, size_t* len);
 int amlbm_load_state(amlbm_ctx* ctx, const void* buf, size_t len);

@@ -75,3 +75,14 @@ def test_every_compiled_tile_gives_the_same_state(storage):
             if not all(np.array_equal(a, c) for a, c in zip(ref, got)):
                 bad.append((sched, tile))
     assert not bad, bad
+
+
+@pytest.mark.parametrize("kw", [dict(z_bc="noslip", wall="noslip"), dict(forcing="guo")])
+def test_autotune_bounded_and_guo_take_fused_tiles_only(kw):
+    """Lattices with z walls or the Guo forcing run on the fused schedule only: the
+    autotuner times the fused tiles and no split candidate."""
+    specs = [amlbm.InstanceSpec(64, 32, 0.9, -5.0, **kw), amlbm.InstanceSpec(48, 24, 1.0, -5.0)]
+    sched, tile, cands = amlbm.autotune_raw(specs, "f32", steps=5)
+    assert sched == "fused"
+    assert len(cands) == len(amlbm.tiles("f32", "fused"))
+    assert all(c["schedule"] == "fused" for c in cands)
