@@ -78,3 +78,21 @@ def test_guo_adjoint_rejected():
         lat.adjoint(4, I.legendre_amplitudes(4), 24.0, 8.0)
     assert e.value.code == amlbm.EINVAL
     lat.close()
+
+
+@pytest.mark.parametrize("storage,shift,bound", [("f16", "equilibrium", 1e-3), ("bf16", "equilibrium", 5e-3),
+                                                 ("bf16", "local", 5e-2)])
+def test_guo_16bit_storage(storage, shift, bound):
+    """The Guo forcing with the 16-bit storage forms: the static drop's density after
+    1000 steps against the FP64 oracle, within the bounds the shift forcing meets."""
+    Nz, Nr = 64, 32
+    fields = I.drop(Nz, Nr, 32.0, 12.0)
+    o = O.Oracle(Nz, Nr, tau=1.0, G=-5.0, forcing=O.FORCE_GUO)
+    F = o.fields(o.run(o.init(*fields), 1000))
+    spec = amlbm.InstanceSpec(Nz, Nr, 1.0, -5.0, shift=shift, forcing="guo")
+    b = amlbm.Batch([spec], storage=storage)
+    b.init_fields(0, *fields)
+    b.step(1000)
+    rho, _, _ = b.read(0)
+    b.close()
+    assert np.abs(rho / F["rho"] - 1).max() < bound

@@ -193,3 +193,15 @@ def test_inlet_and_adjoint_misuse_rejected():
         box.adjoint(4, I.legendre_amplitudes(4), 24.0, 8.0)
     assert e.value.code == amlbm.EINVAL
     box.close()
+
+
+@pytest.mark.parametrize("storage,shift,bound", [("f16", "equilibrium", 1e-3), ("f16", "local", 2e-2)])
+def test_fp16_bounded_disc_flow(storage, shift, bound):
+    """The flow between discs with FP16 storage: density within the bound after 2000 steps,
+    and the radial velocity within 2 % of U_2 of the FP64 oracle's."""
+    c, inp = disc_case()
+    c.spec.shift = shift
+    fields = inp.fields()
+    (_, (rho, _, ur)), (_, F) = c.gpu(fields, 2000, storage=storage), c.oracle(fields, 2000)
+    assert np.abs(rho / F["rho"] - 1).max() < bound
+    assert np.abs(ur - F["ur"]).max() < 0.02 * inp.U2
