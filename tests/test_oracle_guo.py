@@ -66,10 +66,10 @@ def test_table_I_guo_columns(G, sc, guo2d, guoax):
 def test_laplace_guo_much_closer_than_shift():
     """Sec. IV.1: with the Guo forcing the in-out pressure difference of a static drop
     (G = -5, tau = 1, Eq. pressure) is far closer to 2 gamma / R than with the shift.
-    Against the printed gamma = 0.0378 the deviation is 5.5-8.3 % (the shift's, in
-    the SC Laplace test, 23.5-26 %), shrinking with R; the paper reports 2 % and 20 %,
-    so both schemes sit ~5 points further from the law here than there, which points
-    to how Delta p or R is measured rather than to the forcing."""
+    Against the printed gamma = 0.0378 the deviation is 5.5-8.3 % at these small radii
+    (the shift's, in the SC Laplace test, 23.5-26 %), shrinking with R; at R = 16-64 on
+    the GPU (test_gpu_laplace_scale.py, each scheme's own gamma) the deviations come down
+    to the paper's figures: Guo 3.8 -> 1.2 %, the shift 23 -> 21.6 %."""
     gam = 0.0378
     errs = []
     for (Nz, Nr, R) in [(64, 32, 10), (64, 32, 14), (128, 64, 24)]:
