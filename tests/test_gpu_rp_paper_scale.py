@@ -81,3 +81,30 @@ def test_rayleigh_plateau_paper_scale():
         assert pinch[by[(lam, "shift")]] is not None, lam
     for lam in (768, 1024):
         assert 0.5 < rates[(lam, "shift")] < 0.9, (lam, rates[(lam, "shift")])
+
+
+def test_cutoff_returns_to_one_with_the_guo_forcing():
+    """G = -5 (where the Guo forcing is stable), R_C = 80, each forcing started from its own
+    coexistence densities (flat-interface tool).  The shift relaxes kappa* = 0.87 as at
+    G = -6; the Guo forcing, whose Laplace deviation is ~1 % at this radius against ~22 % for
+    the shift, breaks kappa* = 0.87 and 0.93 and relaxes kappa* = 1.12: with the azimuthal
+    pressure right, the cutoff is kappa* = 1, the paper's criterion."""
+    G5 = -5.0
+    coex = {fc: amlbm.flat_interface(G5, axisym=False, forcing=fc) for fc in ("shift", "guo")}
+    cases = [(576, "shift"), (576, "guo"), (540, "guo"), (448, "guo")]
+    specs = [amlbm.InstanceSpec(lam, NR, 1.0, G5, forcing=fc) for lam, fc in cases]
+    b = amlbm.Batch(specs, storage="f32", tile=(26, 16), schedule="fused")
+    fields = [I.thread(lam, NR, R_C, 0.0, coex[fc]["rho_l"], coex[fc]["rho_v"], eps_u=4e-3) for lam, fc in cases]
+    b.init_all([f[0] for f in fields], [f[1] for f in fields], [f[2] for f in fields])
+    params = np.array([[lam / 2, R_C, coex[fc]["rho_l"], coex[fc]["rho_v"]] for lam, fc in cases], float)
+    neck_min = np.full(len(cases), np.inf)
+    for _ in range(40):
+        b.step(2500)
+        d = b.diagnostics_all(params, check=False, as_array=True)
+        neck_min = np.minimum(neck_min, d[:, 7])
+    b.close()
+    print("min neck", {f"{lam}/{fc}": round(float(m), 1) for (lam, fc), m in zip(cases, neck_min)})
+    assert neck_min[0] > 0.5 * R_C                     # shift, kappa* = 0.87: relaxes
+    assert neck_min[1] < 0.25 * R_C                    # Guo, kappa* = 0.87: breaks
+    assert neck_min[2] < 0.25 * R_C                    # Guo, kappa* = 0.93: breaks
+    assert neck_min[3] > 0.7 * R_C                     # Guo, kappa* = 1.12: relaxes
