@@ -16,8 +16,9 @@ flat-interface tool (measured 0.73-0.74 at lambda = 768, 1024; 0.54 at 640, clos
 to the cutoff; 0.87 at 1792).  Pinch-off at 35,000 (lambda = 768) to 58,000 (1792)
 steps.  Finding: with the
 paper's velocity-shift forcing, kappa* = 0.87 (lambda = 576) oscillates and relaxes at
-this radius, so the effective cutoff lies between 0.79 and 0.87 rather than at 1; the
-Laplace test shows the same scheme's deficit in the azimuthal pressure (23.5-26 %).
+this radius, so the effective cutoff lies between 0.79 and 0.87 rather than at 1: the
+shift's azimuthal-pressure deficit (the Laplace test: -21.6 % at R = 64) weakens the
+destabilising curvature; with the Guo forcing the cutoff is back at 1 (the second test).
 """
 import numpy as np
 import pytest
