@@ -18,8 +18,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amlbm_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 NFIELDS = 23
 FIELD_NAMES = ("rho jz jr psi Fsc_z Fsc_r Dr Drr Dzr Fg_z Fg_r Fz Fr uz ur ueqz ueqr "
@@ -33,15 +34,18 @@ RLO_AXIS, RLO_INLET = 0, 1
 FORCE_SHIFT, FORCE_GUO = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (plain -O2, FP contraction off)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (plain -O2, FP contraction off),
+    or with ``omp`` into ``oracle/liboracle_omp.so``: the same source with its site
+    loops run over OpenMP threads (the same arithmetic; bit-identical results)."""
+    lib = _LIB_OMP if omp else _LIB
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
             cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-fPIC",
-                   "-shared", "-o", _LIB + ".tmp", _SRC]
+                   "-shared"] + (["-fopenmp"] if omp else []) + ["-o", lib + ".tmp", _SRC]
             subprocess.run(cmd, check=True)
-            os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+            os.replace(lib + ".tmp", lib)
+    return lib
 
 
 class _Params(ctypes.Structure):
@@ -53,10 +57,9 @@ class _Params(ctypes.Structure):
                 ("inlet_ur", ctypes.POINTER(ctypes.c_double)), ("forcing", ctypes.c_int)]
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _load(omp: bool = False):
+    if omp not in _libs:
+        lib = ctypes.CDLL(build(omp=omp))
         dp = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(_Params)
         lib.orc_init.argtypes = [P, dp, dp, dp, dp]
@@ -72,8 +75,14 @@ def _load():
         lib.orc_grad.argtypes = [P, ctypes.c_int] + [ctypes.c_double] * 5 + \
             [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp]
         lib.orc_diag.argtypes = [P, dp] + [ctypes.c_double] * 4 + [dp]
-        _lib = lib
-    return _lib
+        lib.orc_threads.argtypes = [ctypes.c_int]
+        _libs[omp] = lib
+    return _libs[omp]
+
+
+def threads(n: int = 0) -> int:
+    """Set (n > 0) and return the thread count of the OpenMP build's site loops."""
+    return int(_load(True).orc_threads(int(n)))
 
 
 def _ptr(a: np.ndarray):
@@ -86,8 +95,9 @@ class Oracle:
 
     def __init__(self, Nz, Nr, tau=1.0, G=-5.0, rho0=1.0, gz=0.0, wall=WALL_FREESLIP,
                  axisym=1, src_mode=SRC_LOCAL, zbc=Z_PERIODIC, rlo=RLO_AXIS, r_off=0.0,
-                 rho_out=1.0, inlet=None, forcing=FORCE_SHIFT):
-        """inlet: (u_z, u_r) arrays of Nz values imposed on the inlet row (rlo=RLO_INLET)."""
+                 rho_out=1.0, inlet=None, forcing=FORCE_SHIFT, omp=False):
+        """inlet: (u_z, u_r) arrays of Nz values imposed on the inlet row (rlo=RLO_INLET).
+        omp: run on the OpenMP build (see ``threads``)."""
         self.Nz, self.Nr = int(Nz), int(Nr)
         if inlet is None:
             inlet = (np.zeros(self.Nz), np.zeros(self.Nz))
@@ -96,7 +106,7 @@ class Oracle:
         self.p = _Params(self.Nz, self.Nr, float(tau), float(G), float(rho0), float(gz),
                          int(wall), int(axisym), int(src_mode), int(zbc), int(rlo), float(r_off),
                          float(rho_out), _ptr(self._inlet[0]), _ptr(self._inlet[1]), int(forcing))
-        self.lib = _load()
+        self.lib = _load(bool(omp))
 
     def _c(self, rc):
         if rc != 0:

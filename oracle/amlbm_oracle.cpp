@@ -29,6 +29,15 @@
 #include <cstdint>
 #include <cstring>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+// Built twice: serially, and with -fopenmp for the all-cores CPU baseline.  In
+// the second build the site loops below run their rows (or sites) on several
+// threads; every iteration writes only its own outputs and computes them with
+// the same operations in the same order, so both builds give identical bits.
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
 
 namespace orc {
 
@@ -179,6 +188,7 @@ template <class T>
 static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   const int Nz = P.Nz, Nr = P.Nr, N = Nz * Nr;
   // 1. Moments rho = sum_i f_i, rho u = sum_i c_i f_i (App. A Eq. hydro_var).
+  ORC_PAR
   for (int n = 0; n < N; ++n) {
     T rho = T(0), jz = T(0), jr = T(0);
     for (int i = 0; i < Q; ++i) {
@@ -198,6 +208,7 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   // boundaries).
   const int g = 4;
   Pad<T> ps(Nz, Nr, g);
+  ORC_PAR
   for (int j = -g; j < Nr + g; ++j)
     for (int k = -g; k < Nz + g; ++k)
       ps(k, j) = M.psi[(size_t)ghost_row(P, j) * Nz + ghost_col(P, k)];
@@ -206,12 +217,14 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   // evaluated from the ghost-extended psi, and the 1D d_r psi used inside the
   // mixed derivative.
   Pad<T> dr(Nz, Nr, 2), dr1(Nz, Nr, 2);
+  ORC_PAR
   for (int j = -2; j < Nr + 2; ++j)
     for (int k = -2; k < Nz + 2; ++k) {
       dr(k, j) = iso_d(ps, k, j, 1);
       dr1(k, j) = d1_r(ps, k, j);
     }
 
+  ORC_PAR
   for (int j = 0; j < Nr; ++j) {
     const double r = r_at(P, j);
     for (int k = 0; k < Nz; ++k) {
@@ -267,6 +280,7 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
   // the rows next to it).  Ghost columns are filled first, then ghost rows
   // from the column-extended real rows.
   Pad<T> uzp(Nz, Nr, 2), urp(Nz, Nr, 2);
+  ORC_PAR
   for (int j = 0; j < Nr; ++j)
     for (int k = -2; k < Nz + 2; ++k) {
       const size_t n = (size_t)j * Nz + ghost_col(P, k);
@@ -296,6 +310,7 @@ static void macro(const Params<T>& P, const T* f, Macro<T>& M) {
       }
     }
 
+  ORC_PAR
   for (int j = 0; j < Nr; ++j) {
     const double r = r_at(P, j);
     for (int k = 0; k < Nz; ++k) {
@@ -350,6 +365,7 @@ static void step(const Params<T>& P, const T* f, T* fn, Macro<T>* keep) {
   // W_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . F, whose zeroth moment is 0
   // and first moment F.
   std::vector<T> fs((size_t)Q * N), h((size_t)Q * N);
+  ORC_PAR
   for (int n = 0; n < N; ++n)
     for (int i = 0; i < Q; ++i) {
       const T fi = f[(size_t)i * N + n];
@@ -408,6 +424,7 @@ static void step(const Params<T>& P, const T* f, T* fn, Macro<T>* keep) {
   //    -c_i; this takes precedence over the radial maps at the corners.
   //  - inlet and outlet rows are not streamed into: they take their own
   //    boundary populations.
+  ORC_PAR
   for (int j = 0; j < Nr; ++j)
     for (int k = 0; k < Nz; ++k)
       for (int i = 0; i < Q; ++i) {
@@ -537,6 +554,18 @@ static int check(const orc_params* p) {
 extern "C" {
 
 int orc_num_fields(void) { return 23; }
+
+// Threads of the site loops: n > 0 sets them (OpenMP build only); returns the
+// number a parallel loop uses now (1 in the serial build).
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 // f = f^eq(rho, u), arrays [Nr][Nz], f [9][Nr][Nz].
 int orc_init(const orc_params* p, const double* rho, const double* uz, const double* ur, double* f) {
