@@ -2,13 +2,16 @@
 
 Workload: the batched sweep of 64 independent drops (R ~ U[10, 60], grid 4R x 2R,
 G ~ U[-5.5, -4.6], tau ~ U[0.6, 1.2], l = 2 amplitude ~ U[0, 0.08] on half of
-them, seeds 1234 + k), populations stored as bfloat16 shifted by W_i rho_ref with
-FP32 arithmetic, all instances in one kernel launch per timestep.
+them, seeds 1234 + k), populations stored in FP32 with FP32 arithmetic (the form
+whose density stays within 1e-4 of the FP64 form; the BF16 and FP16 forms are
+reported beside it with their errors), all instances in one kernel launch per
+timestep.
 
 One bench step = one timestep of every site of every instance.  The state
-(~28 MB) fits in L2, so L2 is flushed (a 256 MB write) before every timed step
+(~58 MB) fits in L2, so L2 is flushed (a 256 MB write) before every timed step
 and each step is timed alone with CUDA events on the launching stream: the
-figure is the HBM-fed rate, a lower bound on a run that stays L2-resident.
+figure is the HBM-fed rate, a lower bound on a run that stays L2-resident.  The
+same steps replayed back to back from a captured CUDA graph are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -36,7 +39,7 @@ from paper_1310_1871_gb300 import inputs as I  # noqa: E402
 
 METRIC = "MLUPS & % of HBM roofline, mixed-precision/batched vs plain FP64 at same error"
 UNIT = "MLUPS"
-STORAGE = "bf16"
+STORAGE = "f32"
 BYTES_PER_LU = {"f64": 18 * 8 + 2 * 8, "f32": 18 * 4 + 2 * 4, "f16": 18 * 2 + 2 * 4, "bf16": 18 * 2 + 2 * 4}
 WORKLOAD = ("batched sweep: 64 axisymmetric drops, R~U[10,60], grid 4R x 2R, G~U[-5.5,-4.6], "
             "tau~U[0.6,1.2], a2~U[0,0.08] on odd instances, seeds 1234+k")
@@ -45,10 +48,11 @@ WORKLOAD = ("batched sweep: 64 axisymmetric drops, R~U[10,60], grid 4R x 2R, G~U
 def config(sites, storage=STORAGE, tile=None, schedule=None):
     return {"workload": WORKLOAD, "instances": 64, "sites_per_step": int(sites),
             "storage": (f"{storage}, f_i - W_i*rho(psi) (site density recovered from psi)"
-                        if storage in ("f16", "bf16") else storage),
+                        if storage in ("f16", "bf16") else
+                        f"{storage} populations (unshifted), max rel rho error vs FP64 <= 1e-4"),
             "arithmetic": "f64" if storage == "f64" else "f32",
             "schedule": schedule, "tile": list(tile) if tile else None,
-            "l2": "flushed before every timed step (256 MB write); state 28 MB < L2",
+            "l2": "flushed before every timed step (256 MB write); state < L2",
             "launch": "every tile of all 64 instances in one launch per kernel per timestep"}
 
 
@@ -216,12 +220,16 @@ def run_gpu(args):
             dist.barrier()
         mlups = job_mlups(sites, args.steps, total_ms, world)
         avg_ms = total_ms / args.steps
-        # the same timed steps in five consecutive runs: median and spread of their MLUPS
+        # the timed steps split into five consecutive chunks: median and spread of
+        # the chunks' MLUPS (one run, not five)
         runs = [sites * len(c) / (sum(c) * 1e-3) / 1e6 for c in np.array_split(np.array(times), 5) if len(c)]
         five = {"median_mlups": round(float(np.median(runs)), 1), "min_mlups": round(min(runs), 1),
                 "max_mlups": round(max(runs), 1)}
         hbm, kind = peaks()
         achieved = BYTES_PER_LU[STORAGE] * sites / (avg_ms * 1e-3) / 1e9
+        b.close()
+        graph = graph_back_to_back(torch, rank, stream, max(20, min(args.steps, 2000)))
+        b, inst = build_batch(STORAGE, rank, stream=stream)
 
         # end to end through the public C ABI: every step uploads every instance's
         # fields from pinned host memory (one copy per field array for the whole
@@ -255,21 +263,25 @@ def run_gpu(args):
         scaled = None
         precision = None
         if rank == 0 and not args.no_compare:
-            for st in ("f64", "f32"):
+            # the other storage forms on the same flushed-L2 timing (plain FP64 is the
+            # parity form; the W_i s-shifted BF16 form misses the 1e-4 error target,
+            # see precision_vs_f64)
+            for st in ("f64", "bf16"):
                 bb, _ = build_batch(st, rank, stream=stream)
                 tt = time_steps(torch, bb, min(args.steps, 200), 3, flush, stream)
                 compare[st] = {"mlups": round(bb.sites * len(tt) / (sum(tt) * 1e-3) / 1e6, 1),
                                "schedule": bb.schedule, "tile": list(bb.tile)}
                 bb.close()
-            compare[STORAGE] = {"mlups": round(mlups / world, 1), "schedule": sched, "tile": list(tile)}
-            compare["bf16_over_f64"] = round(compare[STORAGE]["mlups"] / compare["f64"]["mlups"], 2)
+            compare["bf16"]["meets_1e-4"] = False
+            compare[STORAGE] = {"mlups": round(mlups / world, 1), "schedule": sched, "tile": list(tile),
+                                "meets_1e-4": True}
+            compare["f32_over_f64_at_same_error"] = round(compare[STORAGE]["mlups"] / compare["f64"]["mlups"], 2)
             adjoint = adjoint_cost(torch)
             scaled = scaled_cases(torch, tile, sched)
             precision = precision_vs_f64(torch)
 
     traffic, tkernel = profiled_traffic(os.path.join(ROOT, "paper_1310_1871_gb300", "csrc", "amlbm_step.cu"))
-    kname = (f"lbm_persistent<__nv_bfloat16, {tile[0]}, {tile[1]}>" if sched == "fused"
-             else f"stream_kernel<__nv_bfloat16, {tile[0]}, {tile[1]}> + force_kernel")
+    kname = kernel_name(STORAGE, sched, tile)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(seconds=args.cpu_seconds)
@@ -293,16 +305,50 @@ def run_gpu(args):
                             "amlbm_batch_diagnostics_all"},
             "gpu_launches": args.steps * lps,
             "clocks": clk.summary(),
+            "graph_back_to_back": graph,
             "compare_mlups": compare or None,
             "adjoint": adjoint if (rank == 0 and not args.no_compare) else None,
             "scaled_hbm_cases": scaled if (rank == 0 and not args.no_compare) else None,
             "precision_vs_f64": precision if (rank == 0 and not args.no_compare) else None,
             "wall_s_timed_loop": round(wall, 3),
-            "five_runs_per_gpu": five,
+            "five_chunks_of_timed_steps": five,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+CTYPE = {"f64": "double", "f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}
+
+
+def kernel_name(storage, sched, tile):
+    """The step kernel a batch of this storage, schedule and tile launches."""
+    t = CTYPE[storage]
+    if sched == "fused":
+        return f"lbm_persistent<{t}, {tile[0]}, {tile[1]}>"
+    return f"stream_kernel<{t}, {tile[0]}, {tile[1]}> + force_kernel"
+
+
+def graph_back_to_back(torch, rank, stream, steps, chunk=20):
+    """The headline form's steps replayed back to back from captured CUDA graphs of
+    `chunk` timesteps each (amlbm_batch_step with graph_chunk): no L2 flush between
+    steps, so the state stays L2-resident; CUDA events around all `steps`."""
+    steps = max(chunk, steps // chunk * chunk)
+    b, _ = build_batch(STORAGE, rank, graph_chunk=chunk, stream=stream)
+    b.step(3 * chunk)  # warm-up (captures the graphs of both parities)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    b.step(steps)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / steps
+    out = {"mlups": round(b.sites / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 6), "steps": steps,
+           "graph_chunk": chunk, "l2": "not flushed (state L2-resident)",
+           "launch": "amlbm_batch_step replaying captured CUDA graphs of 20 timesteps",
+           "schedule": b.schedule, "tile": list(b.tile)}
+    b.close()
+    return out
 
 
 def adjoint_cost(torch, T=10000):
@@ -341,8 +387,8 @@ def precision_vs_f64(torch, steps=1000):
     inst = I.batch_sweep(64)
     cols = [np.concatenate([np.ravel(x.make_fields()[q]) for x in inst]) for q in range(3)]
 
-    def run(storage, shift):
-        specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G, shift=shift) for x in inst]
+    def run(storage, shift, rounding="default"):
+        specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G, shift=shift, rounding=rounding) for x in inst]
         b = amlbm.Batch(specs, storage=storage, tile="auto")
         b.init_all(*cols)
         torch.cuda.synchronize()
@@ -359,11 +405,13 @@ def precision_vs_f64(torch, steps=1000):
     ok = [k for k in range(len(inst)) if np.isfinite(ref[k]).all()]
     out = {"steps": steps, "instances_compared": len(ok), "unstable_in_f64": len(inst) - len(ok),
            "f64_mlups": round(ref_mlups, 1)}
-    for storage, shift in (("f32", "default"), ("bf16", "default"), ("bf16", "equilibrium"),
-                           ("f16", "default"), ("f16", "equilibrium")):
-        rho, mlups = run(storage, shift)
+    for storage, shift, rounding in (("f32", "default", "default"), ("bf16", "default", "default"),
+                                     ("bf16", "equilibrium", "default"), ("f16", "default", "default"),
+                                     ("f16", "equilibrium", "default"), ("f16", "equilibrium", "stochastic")):
+        rho, mlups = run(storage, shift, rounding)
         err = [float(np.abs(rho[k] / ref[k] - 1).max()) for k in ok]
-        out[f"{storage}/{shift}"] = {"max_rel_rho_err": float(f"{max(err):.3e}"),
+        key = f"{storage}/{shift}" + ("/stochastic" if rounding == "stochastic" else "")
+        out[key] = {"max_rel_rho_err": float(f"{max(err):.3e}"), "meets_1e-4": max(err) <= 1e-4,
                                      "median_rel_rho_err": float(f"{float(np.median(err)):.3e}"),
                                      "mlups": round(mlups, 1), "over_f64": round(mlups / ref_mlups, 2)}
     return out
@@ -372,7 +420,7 @@ def precision_vs_f64(torch, steps=1000):
 def scaled_cases(torch, tile, sched, steps=10):
     """The HBM-sized cases: the oscillating-drop physics (G = -5, tau = 1, P2
     perturbation 5 %) scaled 32x to an 8192 x 4096 lattice (33.5 M sites, R = 1280),
-    and the sweep's recipe with 1024 instances (seeds 1234 + k).  BF16 storage.
+    and the sweep's recipe with 1024 instances (seeds 1234 + k).  The headline storage form.
     Each state is far larger than L2, so back-to-back steps read it from HBM;
     CUDA events around `steps` timesteps after 3 warm-up steps."""
     from paper_1310_1871_gb300 import amlbm
@@ -418,47 +466,87 @@ def scaled_cases(torch, tile, sched, steps=10):
     return out
 
 
-def cpu_baseline(seconds=15.0):
-    """The FP64 oracle, single-threaded, stepping instances of the same workload in
-    turn (one instance-timestep per step) until about `seconds` of work is done."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores():
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_mlups(seconds, omp):
+    """The FP64 oracle stepping the sweep's instances in turn (one instance-timestep per
+    step) until about `seconds` of work is done: (MLUPS, steps, site updates, seconds,
+    threads).  omp: the OpenMP build (its site loops over all host cores)."""
     import oracle as O
+    nthreads = O.threads(host_cores()) if omp else 1
     inst = I.batch_sweep(64)
     states = {}
     done_sites = 0
     elapsed = 0.0
     k = 0
-    n_steps = 0
     while elapsed < seconds:
         x = inst[k % 64]
         if k % 64 not in states:
-            o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+            o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G, omp=omp)
             states[k % 64] = (o, o.init(*x.make_fields()))
         o, f = states[k % 64]
         t1 = time.perf_counter()
         f = o.run(f, 1)
-        done_t = time.perf_counter() - t1
+        elapsed += time.perf_counter() - t1
         states[k % 64] = (o, f)
         done_sites += x.Nz * x.Nr
-        n_steps += 1
         k += 1
-        elapsed += done_t
-    return {"value": round(done_sites / elapsed / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_steps} instance-timesteps of the 64-drop sweep ({done_sites} site updates, "
-                      f"{elapsed:.1f} s), FP64, one thread"}
+    return done_sites / elapsed / 1e6, k, done_sites, elapsed, nthreads
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 oracle on the host, on one thread and with its OpenMP build on every
+    core, each for about `seconds` of the sweep's instance-timesteps."""
+    v1, n1, s1, e1, _ = oracle_mlups(seconds, omp=False)
+    vn, nn, sn, en, thr = oracle_mlups(seconds, omp=True)
+    model = cpu_model()
+    return {"value": round(vn, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{nn} instance-timesteps of the 64-drop sweep in turn ({sn} site updates, "
+                      f"{en:.1f} s), FP64, OpenMP over lattice rows on {thr} threads",
+            "single_thread": {"value": round(v1, 3), "cores": 1,
+                              "sample": f"{n1} instance-timesteps ({s1} site updates, {e1:.1f} s)"},
+            "cpu_model": model}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step advances one instance of the sweep
-    (in turn) by one timestep on the host; MLUPS over the timed steps."""
+    """The oracle as the reference arm, on every host core (its OpenMP build): each
+    step advances one instance of the sweep (in turn) by one timestep; MLUPS over the
+    timed steps."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
+    thr = O.threads(host_cores())
     inst = I.batch_sweep(64)
     states = []
     for x in inst:
-        o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
+        o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G, omp=True)
         states.append([o, o.init(*x.make_fields())])
     for s in range(args.warmup):
         o, f = states[s % 64]
@@ -476,9 +564,10 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(el / max(args.steps, 1) * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference", "config": config(sum(x.Nz * x.Nr for x in inst), "f64"),
-        "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": f"one instance-timestep of the 64-drop sweep per step, instances in "
-                                   f"turn ({sites} site updates in {el:.1f} s), FP64 oracle, one thread"},
+                                   f"turn ({sites} site updates in {el:.1f} s), FP64 oracle, OpenMP "
+                                   f"over lattice rows on {thr} threads", "cpu_model": cpu_model()},
         "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -492,7 +581,7 @@ def main():
     ap.add_argument("--impl", default="amlbm", choices=["amlbm", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64/FP32 comparison runs")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

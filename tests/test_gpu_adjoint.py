@@ -35,6 +35,15 @@ def rel_err(g_gpu, g_ref):
     return np.abs(np.asarray(g_gpu) - np.asarray(g_ref)).max() / np.abs(g_ref).max()
 
 
+def comp_err(g_gpu, g_ref, floor=1e-3):
+    """Largest per-component relative error, each component against its own size
+    (with a floor of `floor` times the largest component, so that a component that
+    is zero to rounding is held to an absolute bar)."""
+    g_gpu, g_ref = np.asarray(g_gpu), np.asarray(g_ref)
+    den = np.maximum(np.abs(g_ref), floor * np.abs(g_ref).max())
+    return float((np.abs(g_gpu - g_ref) / den).max())
+
+
 @pytest.mark.parametrize("case", [
     dict(),                                   # free-slip drop, a2^2
     dict(wall=1, gz=2e-5, tau=0.8),           # no-slip wall, body force
@@ -51,9 +60,10 @@ def test_fp64_adjoint_matches_oracle_complex_step(case):
     J, dG, dT, dA = gpu_grad(Nz, Nr, T, amps, tau, G, ("freeslip", "noslip")[wall], gz, bool(axisym),
                              ("a2sq", "neck")[kind], kstar, ckpt=7)
     g = np.concatenate([[dG, dT], dA])
-    print(case, "J", J, J_ref, "rel grad err", rel_err(g, g_ref))
+    print(case, "J", J, J_ref, "rel grad err", rel_err(g, g_ref), "per component", comp_err(g, g_ref))
     assert abs(J / J_ref - 1) < 1e-11
     assert rel_err(g, g_ref) < 1e-6
+    assert comp_err(g, g_ref) < 1e-6
 
 
 def test_fp64_adjoint_matches_gpu_finite_differences():
@@ -75,6 +85,7 @@ def test_fp64_adjoint_matches_gpu_finite_differences():
         fd.append((Jf(a=ap) - Jf(a=am)) / (2 * h))
     g = np.concatenate([[dG, dT], dA])
     assert rel_err(g, fd) < 1e-6
+    assert comp_err(g, fd) < 1e-6
 
 
 def test_checkpoint_spacing_does_not_change_the_gradient():

@@ -1,8 +1,11 @@
 """The benchmark's own launch configuration and sizes.
 
-- The 64-drop sweep in the configuration `bench.py` times (BF16 storage with the local
-  shift and stochastic rounding, FP32 arithmetic, the fused persistent launch with the
-  autotuner's 26 x 16 tile): three sampled instances against the FP64 oracle.
+- The 64-drop sweep in the configuration `bench.py` times (FP32 storage, FP32
+  arithmetic, the autotuned persistent launch of all 64 instances): five sampled
+  instances against the FP64 oracle after 1000 steps, held to the 1e-4 bound on the
+  density that the headline form must meet.  BF16 storage with the W_i s shift (the
+  fastest 16-bit form, which does not meet that bound) is checked at its measured
+  error, 2e-2 after 200 steps.
 - The largest case the benchmark runs (the 8192 x 4096 drop, 33.5 M sites), where the
   oracle is too slow: properties that hold at any size, in FP64 - the exact z-mirror
   symmetry of a centred drop, the discrete mass budget sum rho(t+1) - sum rho(t) =
@@ -23,24 +26,31 @@ if not torch.cuda.is_available():
 from paper_1310_1871_gb300 import amlbm  # noqa: E402
 
 
-@pytest.mark.parametrize("storage,bound", [("bf16", 2e-2), ("f32", 1e-4)])
-def test_sweep_in_bench_configuration_against_oracle(storage, bound):
+@pytest.mark.parametrize("storage,steps,bound", [("f32", 1000, 1e-4), ("bf16", 200, 2e-2)])
+def test_sweep_in_bench_configuration_against_oracle(storage, steps, bound):
     inst = I.batch_sweep(64)
     specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
-    b = amlbm.Batch(specs, storage=storage, tile=(26, 16), schedule="fused")
+    b = amlbm.Batch(specs, storage=storage, tile="auto")
     b.init_all(*[[x.make_fields()[q] for x in inst] for q in range(3)])
-    steps = 200
     b.step(steps)
     sizes = [x.Nz * x.Nr for x in inst]
-    for k in (int(np.argmin(sizes)), int(np.argmax(sizes)), 1):
+    picks = [int(np.argmin(sizes)), int(np.argmax(sizes)), 1, 17, 42]
+    checked = 0
+    for k in picks:
         x = inst[k]
         o = O.Oracle(x.Nz, x.Nr, tau=x.tau, G=x.G)
         ref = o.fields(o.run(o.init(*x.make_fields()), steps))["rho"]
+        if not np.isfinite(ref).all():
+            print(f"instance {k}: the FP64 scheme itself is unstable here (tau {x.tau:.2f}, G {x.G:.2f})")
+            continue
         rho = b.read(k)[0]
         err = np.abs(rho / ref - 1).max()
-        print(f"{storage} instance {k} ({x.Nz}x{x.Nr}): max rel rho err {err:.2e} after {steps} steps")
+        print(f"{storage} instance {k} ({x.Nz}x{x.Nr}, {b.schedule} {b.tile}): max rel rho err {err:.2e} "
+              f"after {steps} steps")
         assert err < bound, (k, err)
+        checked += 1
     b.close()
+    assert checked >= 4
 
 
 def test_largest_case_properties_fp64():
