@@ -327,11 +327,16 @@ typedef struct amlbm_instance {
 /* How a timestep is launched.  FUSED: one kernel per tile computes the whole
  * update, recomputing forces and velocities on a 3-site halo.  SPLIT: a force
  * kernel writes u and u^eq per site, then a collide-stream kernel reads them with
- * a halo (less recomputation, 16 or 32 more bytes per site through L2).  Both
- * give bit-identical states. */
+ * a halo (less recomputation, 16 or 32 more bytes per site through L2).  PAIR:
+ * the fused update with two adjacent z-sites per thread (vector loads and
+ * stores, stencil taps shared by the pair); it takes periodic lattices on the
+ * axis with an even Nz, a free-slip or no-slip outer wall, the source at the
+ * departure site (AMLBM_SRC_LOCAL) and either forcing, and 9 x pitch x Nr below
+ * 2^31 elements.  All three give bit-identical states. */
 #define AMLBM_SCHED_AUTO 0
 #define AMLBM_SCHED_FUSED 1
 #define AMLBM_SCHED_SPLIT 2
+#define AMLBM_SCHED_PAIR 3
 
 /* Schedule and tile shape (sites along z x sites along r) of the step kernels;
  * all zero lets the library choose.  A tile given with AMLBM_SCHED_AUTO runs on

@@ -84,7 +84,8 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("tune", Tune), ("ms_per_step", ctypes.c_double), ("mlups", ctypes.c_double)]
 
 
-SCHEDULE = {"auto": 0, "fused": 1, "split": 2}
+SCHEDULE = {"auto": 0, "fused": 1, "split": 2, "pair": 3}
+SCHEDULE_NAME = {1: "fused", 2: "split", 3: "pair"}
 
 
 EXPORTS = [
@@ -260,7 +261,7 @@ def autotune_raw(specs, storage, steps=20, stream=None):
     n = lib.amlbm_autotune(len(arr), arr, int(steps), sh, ctypes.byref(best), res, cap)
     if n < 0:
         _check(lib, n)
-    names = {1: "fused", 2: "split"}
+    names = SCHEDULE_NAME
     cands = [{"schedule": names[r.tune.schedule], "tile": [r.tune.tile_z, r.tune.tile_r],
               "ms_per_step": r.ms_per_step, "mlups": r.mlups} for r in res[:min(n, cap)]]
     return names[best.schedule], (best.tile_z, best.tile_r), cands
@@ -310,7 +311,7 @@ class Batch:
         sc, tz, tr, nl = (ctypes.c_int() for _ in range(4))
         _check(self.lib, self.lib.amlbm_batch_config(h, ctypes.byref(sc), ctypes.byref(tz), ctypes.byref(tr),
                                                      ctypes.byref(nl)))
-        self.schedule = {1: "fused", 2: "split"}[sc.value]
+        self.schedule = SCHEDULE_NAME[sc.value]
         self.tile = (tz.value, tr.value)
         self.launches_per_step = nl.value
 

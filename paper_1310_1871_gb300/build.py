@@ -17,14 +17,14 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libamlbm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["amlbm_step.cu", "amlbm_abi.cu", "amlbm_diag.cu", "amlbm_noalloc.cu", "amlbm_adjoint.cu", "amlbm_tune.cu",
+SOURCES = ["amlbm_step.cu", "amlbm_step_pair.cu", "amlbm_abi.cu", "amlbm_diag.cu", "amlbm_noalloc.cu", "amlbm_adjoint.cu", "amlbm_tune.cu",
            "amlbm_interface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # The step kernels state every fused multiply-add explicitly (rounding
 # intrinsics); nothing else may be fused by the compiler, so that every
 # schedule and tiling computes a site with the same operations.
-FILE_FLAGS = {"amlbm_step.cu": ["-fmad=false"]}
+FILE_FLAGS = {"amlbm_step.cu": ["-fmad=false"], "amlbm_step_pair.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:

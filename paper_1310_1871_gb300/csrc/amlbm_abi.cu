@@ -66,6 +66,21 @@ bool bounded(const amlbm_bc& bc) {
          bc.forcing != AMLBM_FORCE_SHIFT;
 }
 
+// A lattice the pair schedule takes: periodic in z with an even Nz, the axis
+// below row 0, a reflecting or bounce-back outer wall, the source at the
+// departure site, and element offsets of all nine planes within 32 bits.
+bool pair_ok(const amlbm_instance& I) {
+  return I.bc.z_bc == AMLBM_Z_PERIODIC && I.bc.r_lo == AMLBM_RLO_AXIS &&
+         (I.bc.wall_r == AMLBM_WALL_FREESLIP || I.bc.wall_r == AMLBM_WALL_NOSLIP) &&
+         I.bc.src_mode == AMLBM_SRC_LOCAL && I.Nz % 2 == 0 &&
+         9LL * pitch_of(I.Nz) * I.Nr < (1LL << 31);
+}
+bool all_pair_ok(const std::vector<amlbm_instance>& inst) {
+  for (const auto& I : inst)
+    if (!pair_ok(I)) return false;
+  return true;
+}
+
 // Schedule and tile when the caller gives none (fastest on the 64-drop sweep on
 // GB300): FP32 arithmetic forms take the fused schedule with the first tile of a
 // preference list that still gives every SM two CTAs over the whole batch; the
@@ -282,8 +297,12 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     bool any_bounded = false;
     for (const auto& I : inst) any_bounded = any_bounded || bounded(I.bc);
     sched = tune->schedule ? tune->schedule : (any_bounded ? AMLBM_SCHED_FUSED : AMLBM_SCHED_SPLIT);
-    if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT)
+    if (sched != AMLBM_SCHED_FUSED && sched != AMLBM_SCHED_SPLIT && sched != AMLBM_SCHED_PAIR)
       return fail(AMLBM_EINVAL, "bad schedule");
+    if (sched == AMLBM_SCHED_PAIR && !all_pair_ok(inst))
+      return fail(AMLBM_EINVAL,
+                  "the pair schedule takes periodic lattices on the axis with an even Nz, a free-slip or "
+                  "no-slip wall and the source at the departure site");
     if (sched == AMLBM_SCHED_SPLIT)
       for (const auto& I : inst)
         if (bounded(I.bc))
@@ -708,7 +727,7 @@ size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
   // room for whichever compiled tile the tune picks (the tile list grows with
   // the number of tiles)
   size_t need = 0;
-  for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_SPLIT; ++sc) {
+  for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_PAIR; ++sc) {
     int tz[32], tr[32];
     const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, sc, tz, tr, 32));
     for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);

@@ -47,8 +47,9 @@ enum { K_TAU, K_OMEGA, K_NEGG, K_GFAC, K_GZ, K_RHO0, K_INVRHO0, K_CMU, K_RREF, K
 // Every launcher returns the cudaGetLastError() of its launch.
 // The step and macro kernels run CTAs for the flattened tiles
 // [toff, toff + ntiles) of the batch.  schedule: 1 fused (one kernel), 2 split
-// (force kernel, then collide-stream kernel).
-enum { SCHED_FUSED = 1, SCHED_SPLIT = 2 };
+// (force kernel, then collide-stream kernel), 3 pair (the fused update with two
+// adjacent z-sites per thread; amlbm_step_pair.cu).
+enum { SCHED_FUSED = 1, SCHED_SPLIT = 2, SCHED_PAIR = 3 };
 // ctr (four ints, zero at creation): tile counters of the persistent fused
 // grid and the step numbers for stochastic rounding, one per parity; nullptr
 // launches one CTA per tile.
@@ -113,6 +114,12 @@ cudaError_t launch_init_all(int storage, const InstDesc* d_desc, int n, const lo
                             int parity, int* bad, cudaStream_t s);
 bool tile_supported(int storage, int schedule, int tz, int tr);
 int tile_list(int storage, int schedule, int* tz, int* tr, int cap);
+// The pair schedule (amlbm_step_pair.cu): its compiled tiles and its persistent
+// launch over all tiles (ctr as for the fused persistent launch).
+bool pair_tile_supported(int storage, int tz, int tr);
+int pair_tile_list(int storage, int* tz, int* tr, int cap);
+cudaError_t launch_step_pair(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
+                             int ntiles, int parity, cudaStream_t s, int* ctr);
 
 // Access to a lattice context for entry points defined outside the ABI file
 // (amlbm_abi.cu implements these).

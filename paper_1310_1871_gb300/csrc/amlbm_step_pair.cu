@@ -1,0 +1,513 @@
+// Fused axisymmetric Shan-Chen LBM step with two adjacent z-sites per thread
+// (the "pair" schedule) for sm_103a (arXiv:1310.1871, Sec. II).
+//
+// The per-site chain is the fused schedule's, stage for stage:
+//   psi, tile + (8 in z, 7 in r), from the previous step's psi
+//   -> isotropic d_r psi and the 1D d_r psi (Sec. II.D), tile + (6, 5)
+//   -> moments, Shan-Chen force (Eq. scforce), axisymmetric force
+//      (Eq. scAxisExtra), u and u^eq (Eqs. uhydro, ueq), tile + (4, 3); the BGK
+//      collision (Eq. lbm2d) on tile + (2, 1)
+//   -> velocity gradients (1D 4th-order differences, Sec. II.D) and the sources
+//      S, H_z, H_r, h_i (Eq. condition_h, App. A) on tile + (2, 1)
+//   -> pull streaming with the axis / wall / periodic maps of Sec. II.E, psi of
+//      the new state, store.
+// Every task of every stage is a pair of adjacent sites (z = 2m, 2m + 1 of the
+// region): populations, psi and the stored velocity move as 2-element vectors
+// between HBM and registers, and each stencil reads its taps as 2-element
+// vectors from shared memory into a small register window that both sites of
+// the pair share.  The arithmetic is the same functions on the same values as
+// the fused schedule, so the two give identical bits.
+//
+// Lattices this schedule takes: z periodic with Nz even, the axis below row 0,
+// an outer wall that reflects (free-slip) or bounces back (no-slip), the source
+// at the departure site, either forcing.  Pairs never straddle the periodic
+// seam because Nz and every tile origin are even.
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <stdint.h>
+
+#include <mutex>
+#include <type_traits>
+
+#include "amlbm.h"
+#include "amlbm_internal.cuh"
+#include "amlbm_physics.cuh"
+
+namespace amlbm {
+namespace {
+
+constexpr int PNT = 256;  // threads per CTA
+
+// Two adjacent elements of a storage or compute type as one vector access.
+template <class S> struct Vec2;
+template <> struct Vec2<double> { using V = double2; };
+template <> struct Vec2<float> { using V = float2; };
+template <> struct Vec2<__half> { using V = __half2; };
+template <> struct Vec2<__nv_bfloat16> { using V = __nv_bfloat162; };
+
+template <class S>
+__device__ __forceinline__ void ld2(const S* p, S& a, S& b) {
+  const typename Vec2<S>::V v = *reinterpret_cast<const typename Vec2<S>::V*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <class S>
+__device__ __forceinline__ void st2(S* p, S a, S b) {
+  typename Vec2<S>::V v;
+  v.x = a;
+  v.y = b;
+  *reinterpret_cast<typename Vec2<S>::V*>(p) = v;
+}
+// Lane-typed shared-memory pairs (the lane types are one scalar wide).
+template <class T>
+__device__ __forceinline__ void lds2(const T* p, T& a, T& b) {
+  using C = typename Lane<T>::C;
+  C x, y;
+  ld2<C>(reinterpret_cast<const C*>(p), x, y);
+  a = T{x};
+  b = T{y};
+}
+template <class T>
+__device__ __forceinline__ void sts2(T* p, T a, T b) {
+  using C = typename Lane<T>::C;
+  st2<C>(reinterpret_cast<C*>(p), a.v, b.v);
+}
+// Row r of a register window `w` (rows of W values): the pairs of a shared
+// memory row starting at p + 2 * (first pair), covering columns [c0, c0 + 2 n).
+template <class T, int N>
+__device__ __forceinline__ void load_row(const T* p, T* w) {
+#pragma unroll
+  for (int m = 0; m < N; ++m) lds2(p + 2 * m, w[2 * m], w[2 * m + 1]);
+}
+
+// Tile geometry (BZ x BR sites, BZ even).  Halos in (z, r): psi (8, 7),
+// d_r psi (6, 5), rho and u (4, 3), collided populations (2, 1); the z halos
+// are the fused schedule's rounded up to whole pairs.
+template <class T, int BZ, int BR>
+struct PGeo {
+  static_assert(BZ % 2 == 0, "pair tiles are an even number of sites wide");
+  static constexpr int PZ = BZ + 16, PR = BR + 14;
+  static constexpr int DZ = BZ + 12, DR = BR + 10;
+  static constexpr int FZ = BZ + 8, FR = BR + 6;
+  static constexpr int SZ = BZ + 4, SR = BR + 2;
+  static constexpr int nP = PZ * PR, nD = DZ * DR, nF = FZ * FR, nS = SZ * SR;
+  // psi, d_r psi, 1D d_r psi, rho, u_z, u_r, then nine collided populations
+  static constexpr size_t elems = (size_t)nP + 2 * nD + 3 * nF + 9 * nS;
+  static constexpr size_t bytes = sizeof(T) * elems;
+};
+
+// Resident CTAs per SM the register allocation must allow (as many as the
+// tile's shared memory fits, at most three).
+template <class S, class T, int BZ, int BR>
+struct PMinBlocks {
+  static constexpr int fit = int((228u * 1024u) / (PGeo<T, BZ, BR>::bytes + 1024u));
+  static constexpr int value = std::is_same<S, double>::value ? 1 : (fit > 3 ? 3 : (fit < 1 ? 1 : fit));
+};
+
+// Flat walk over the pair tasks of a ROWS x PAIRS region.
+template <int ROWS, int PAIRS, class F>
+__device__ __forceinline__ void for_pairs(F&& body) {
+  for (int t = threadIdx.x; t < ROWS * PAIRS; t += PNT) {
+    const int lr = t / PAIRS, cp = t - lr * PAIRS;
+    body(lr, cp);
+  }
+}
+
+// Column of the periodic lattice for a region column k in [-16, Nz + BZ + 16).
+__device__ __forceinline__ int wrap_col(int k, int Nz, bool tiny) {
+  if (tiny) return wrapz(k, Nz);
+  return k < 0 ? k + Nz : (k >= Nz ? k - Nz : k);
+}
+
+template <class S, class T, int BZ, int BR>
+__device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst,
+                                          int tile, int parity, uint32_t step) {
+  using C = typename Store<S>::C;
+  using G = PGeo<T, BZ, BR>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sPsi = reinterpret_cast<T*>(smem_raw);
+  T* sDr = sPsi + G::nP;
+  T* sD1 = sDr + G::nD;
+  T* sRho = sD1 + G::nD;
+  T* sUz = sRho + G::nF;
+  T* sUr = sUz + G::nF;
+  T* sFs = sUr + G::nF;
+
+  const int inst = tile_inst[tile];
+  const InstDesc& D = descs[inst];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P;
+  const int l = tile - D.tile_base;
+  const int k0 = (l % D.tiles_z) * BZ, j0 = (l / D.tiles_z) * BR;
+  const int plane = P * Nr;  // < 2^31 / 9 (the batch checks it)
+  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
+  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
+  const bool ax = D.axisym != 0;
+  const int shift = D.shift;
+  const Par<T> q = par_of<T>(D);
+  const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
+  const C r0c = kc(D, K_R0, C());
+  const bool guo = D.forcing == AMLBM_FORCE_GUO;
+  const bool tiny = Nz < BZ + 16;  // region columns may wrap more than once
+
+  // Stage 0: psi on tile + (8, 7); rows mirrored about the axis and the wall.
+  for_pairs<G::PR, G::PZ / 2>([&](int lr, int cp) {
+    const int jj = reflect_row(j0 - 7 + lr, Nr);
+    const int kk = wrap_col(k0 - 8 + 2 * cp, Nz, tiny);
+    C a, b;
+    ld2<C>(psin + jj * P + kk, a, b);
+    sts2(sPsi + lr * G::PZ + 2 * cp, T{a}, T{b});
+  });
+  __syncthreads();
+
+  // Stage 1: isotropic d_r psi and 1D d_r psi on tile + (6, 5).
+  if (ax) {
+    for_pairs<G::DR, G::DZ / 2>([&](int lr, int cp) {
+      // psi rows -2..2 around the pair, columns -2..3 (row 0 is not a tap)
+      T w[5 * 6];
+      const T* p = sPsi + (lr + 2) * G::PZ + 2 * cp;  // column -2 of the window at row 0
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+        if (r != 2) load_row<T, 3>(p + (r - 2) * G::PZ, w + 6 * r);
+      T dr[2], d1r[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        dr[s] = iso_r(w + 12 + 2 + s, 6);
+        d1r[s] = d1(w + 12 + 2 + s, 6);
+      }
+      sts2(sDr + lr * G::DZ + 2 * cp, dr[0], dr[1]);
+      sts2(sD1 + lr * G::DZ + 2 * cp, d1r[0], d1r[1]);
+    });
+    __syncthreads();
+  }
+
+  // Stage 2 (tile + (4, 3)): moments, forces, u; on tile + (2, 1) also u^eq and
+  // the BGK collision of all nine populations into shared memory.
+  for_pairs<G::FR, G::FZ / 2>([&](int lr, int cp) {
+    const int j = j0 - 3 + lr;
+    if (j < 0 || j >= Nr) return;
+    const int kk = wrap_col(k0 - 4 + 2 * cp, Nz, tiny);
+    const int so = j * P + kk;
+    S qa[9], qb[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ld2<S>(fin + i * plane + so, qa[i], qb[i]);
+    C va = C(0), vb = C(0), wa = C(0), wb = C(0);
+    if (shift == 3) {
+      ld2<C>(psin + plane + so, va, vb);
+      ld2<C>(psin + 2 * plane + so, wa, wb);
+    }
+    // psi rows -1..1, columns -2..3 around the pair
+    T wp[3 * 6];
+    const T* p = sPsi + (lr + 4) * G::PZ + 2 * cp + 2;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) load_row<T, 3>(p + (r - 1) * G::PZ, wp + 6 * r);
+    // d_r psi rows -2..2 (columns -2..3), 1D d_r psi row 0 (columns -2..3)
+    T wd[5 * 6], we[6];
+    if (ax) {
+      const T* pd = sDr + (lr + 2) * G::DZ + 2 * cp;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) load_row<T, 3>(pd + (r - 2) * G::DZ, wd + 6 * r);
+      load_row<T, 3>(sD1 + (lr + 2) * G::DZ + 2 * cp, we);
+    }
+    const T inv_r = inv_r_of(T(), j, r0c);
+    const bool coll = lr >= 2 && lr < G::FR - 2 && cp >= 1 && cp < G::FZ / 2 - 1;
+    T rho2[2], uz2[2], ur2[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T psi = wp[6 + 2 + s];
+      T f[9];
+      decode_values<S>(shift, s ? qb : qa, psi.v, s ? vb : va, s ? wb : wa, inv_rho0c, rho0c, rrefc, f);
+      const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
+      T sz, sr;
+      sc_sums(wp + 6 + 2 + s, 6, sz, sr);
+      T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
+      if (ax) {
+        dr0 = wd[12 + 2 + s];
+        Drr = iso_r(wd + 12 + 2 + s, 6);
+        T e[5];
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) e[m + 2] = m ? we[2 + s + m] : lit<T>(0.0);
+        Dzr = d1(e + 2, 1);
+      }
+      T Fz, Fr;
+      forces(q, rho, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz, Fr);
+      const T inv_rho = rcp(rho);
+      const T uz = fma(Fz, lit<T>(0.5), jz) * inv_rho, ur = fma(Fr, lit<T>(0.5), jr) * inv_rho;
+      rho2[s] = rho;
+      uz2[s] = uz;
+      ur2[s] = ur;
+      if (coll) {
+        T* out = sFs + (lr - 2) * G::SZ + (2 * cp - 2) + s;
+        T fe[9];
+        if (guo) {
+          equilibrium(rho, uz, ur, fe);
+          T sg[9];
+          guo_force(uz, ur, Fz, Fr, sg);
+          const T gk = splat<T>(kc(D, K_GUO, C()));
+#pragma unroll
+          for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(sg[i], gk, fma(fe[i] - f[i], q.omega, f[i]));
+        } else {
+          const T vz = fma(Fz, q.tau, jz) * inv_rho, vr = fma(Fr, q.tau, jr) * inv_rho;
+          equilibrium(rho, vz, vr, fe);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) out[i * G::nS] = fma(fe[i] - f[i], q.omega, f[i]);
+        }
+      }
+    }
+    const int fi = lr * G::FZ + 2 * cp;
+    sts2(sRho + fi, rho2[0], rho2[1]);
+    sts2(sUz + fi, uz2[0], uz2[1]);
+    sts2(sUr + fi, ur2[0], ur2[1]);
+  });
+  __syncthreads();
+
+  // Ghost rows of u (depth 2) on tiles that touch row 0 or row Nr - 1: u_z even
+  // and u_r odd about the axis; about the outer wall u_r odd and u_z even
+  // (free-slip) or odd (no-slip).
+  if (ax && (j0 < 3 || j0 + BR + 3 > Nr)) {
+    const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
+    for_pairs<G::FR, G::FZ / 2>([&](int lr, int cp) {
+      const int j = j0 - 3 + lr;
+      int m;
+      bool flip_z;
+      if (j == -1 || j == -2) {
+        m = -1 - j;
+        flip_z = false;
+      } else if (j == Nr || j == Nr + 1) {
+        m = 2 * Nr - 1 - j;
+        flip_z = noslip;
+      } else {
+        return;
+      }
+      const int src = (m - (j0 - 3)) * G::FZ + 2 * cp, dst = lr * G::FZ + 2 * cp;
+      T a, b;
+      lds2(sUz + src, a, b);
+      sts2(sUz + dst, flip_z ? -a : a, flip_z ? -b : b);
+      lds2(sUr + src, a, b);
+      sts2(sUr + dst, -a, -b);
+    });
+    __syncthreads();
+  }
+
+  // Stage 3 (tile + (2, 1)): velocity gradients and the sources of App. A,
+  // added to the collided populations.
+  if (ax) {
+    for_pairs<G::SR, G::SZ / 2>([&](int lr, int cp) {
+      const int j = j0 - 1 + lr;
+      if (j < 0 || j >= Nr) return;
+      const int fi = (lr + 2) * G::FZ + 2 * cp + 2;  // u at the pair's first site
+      // u_z rows -2..2 and u_r rows -2..2 at the pair; u_r row 0 columns -2..3
+      T wz[5 * 2], wr[5 * 2], wr0[6];
+#pragma unroll
+      for (int r = 0; r < 5; ++r) {
+        lds2(sUz + fi + (r - 2) * G::FZ, wz[2 * r], wz[2 * r + 1]);
+        if (r != 2) lds2(sUr + fi + (r - 2) * G::FZ, wr[2 * r], wr[2 * r + 1]);
+      }
+      load_row<T, 3>(sUr + fi - 2, wr0);
+      wr[4] = wr0[2];
+      wr[5] = wr0[3];
+      T rr[2];
+      lds2(sRho + fi, rr[0], rr[1]);
+      const T inv_r = inv_r_of(T(), j, r0c);
+      T hs[2][9];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T druz = d1(wz + 4 + s, 2);
+        const T dzur = d1(wr0 + 2 + s, 1);
+        const T drur = d1(wr + 4 + s, 2);
+        T S_, Hz, Hr;
+        site_sources(q, rr[s], wz[4 + s], wr[4 + s], druz, dzur, drur, inv_r, S_, Hz, Hr);
+        sources(S_, Hz, Hr, hs[s]);
+      }
+      T* o = sFs + lr * G::SZ + 2 * cp;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        T a, b;
+        lds2(o + i * G::nS, a, b);
+        sts2(o + i * G::nS, a + hs[0][i], b + hs[1][i]);
+      }
+    });
+    __syncthreads();
+  }
+
+  // Stage 4 (tile): pull streaming.  Away from rows 0 and Nr - 1 every
+  // population comes from x - c_i in the same direction; those two rows apply
+  // the axis and wall maps.  Then psi of the new state and the store.
+  S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
+  C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
+  const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
+  for_pairs<BR, BZ / 2>([&](int lr, int cp) {
+    const int j = j0 + lr, k = k0 + 2 * cp;
+    if (j >= Nr || k >= Nz) return;
+    const bool edge = (j == 0) || (j == Nr - 1);
+    T fn[2][9];
+    const T* c0 = sFs + (lr + 1) * G::SZ + 2 * cp + 2;  // the pair's first site
+    if (!edge) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const T* src = c0 + i * G::nS - cr_(i) * G::SZ - cz_(i);
+        if (cz_(i) == 0) {
+          lds2(src, fn[0][i], fn[1][i]);
+        } else {
+          fn[0][i] = src[0];
+          fn[1][i] = src[1];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          int dl = -cr_(i), dc = -cz_(i), ii = i;
+          if (cr_(i) > 0 && j == 0) {  // through the axis: specular reflection
+            dl = 0;
+            ii = mirror_(i);
+          } else if (cr_(i) < 0 && j == Nr - 1) {  // through the outer wall
+            dl = 0;
+            if (noslip) { dc = 0; ii = opp_(i); }
+            else { ii = mirror_(i); }
+          }
+          fn[s][i] = c0[ii * G::nS + dl * G::SZ + dc + s];
+        }
+    }
+    S qa[9], qb[9];
+    C va, vb, wa, wb, pa, pb;
+    {
+      const T rho = moment0(fn[0]);
+      pa = psi_of(q, rho).v;
+      encode_values<S>(shift, fn[0], rho, pa, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k), step,
+                       qa, va, wa);
+    }
+    {
+      const T rho = moment0(fn[1]);
+      pb = psi_of(q, rho).v;
+      encode_values<S>(shift, fn[1], rho, pb, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k + 1),
+                       step, qb, vb, wb);
+    }
+    const int o = j * P + k;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) st2<S>(fout + i * plane + o, qa[i], qb[i]);
+    st2<C>(psout + o, pa, pb);
+    if (shift == 3) {
+      st2<C>(psout + plane + o, va, vb);
+      st2<C>(psout + 2 * plane + o, wa, wb);
+    }
+  });
+}
+
+// The timestep as a persistent grid: CTAs take tiles from a counter until none
+// is left (ctr as for the fused schedule: this step's tile counter and step
+// number at [parity] and [2 + parity], the next step's reset here).
+template <class S, class T, int BZ, int BR>
+__global__ void __launch_bounds__(PNT, (PMinBlocks<S, T, BZ, BR>::value)) pair_persistent(
+    const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
+    int* __restrict__ ctr) {
+  __shared__ int s_tile;
+  const uint32_t step = (uint32_t)ctr[2 + parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr[parity ^ 1] = 0;
+    ctr[2 + (parity ^ 1)] = (int)(step + 1);
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctr[parity], 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) return;
+    pair_tile<S, T, BZ, BR>(descs, tile_inst, t, parity, step);
+    __syncthreads();
+  }
+}
+
+constexpr int kMaxDev = 64;
+struct PairOnce {
+  std::once_flag once[kMaxDev];
+  cudaError_t err[kMaxDev] = {};
+  int grid_cap[kMaxDev] = {};
+};
+
+template <class S, int BZ, int BR>
+cudaError_t launch_pair_t(const InstDesc* d, const int* ti, int ntiles, int parity, cudaStream_t s, int* ctr) {
+  using T = typename Store<S>::T;
+  constexpr size_t smem = PGeo<T, BZ, BR>::bytes;
+  static PairOnce st;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::call_once(st.once[dev], [&] {
+    cudaError_t r = cudaFuncSetAttribute(pair_persistent<S, T, BZ, BR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int sms = 0, per_sm = 0;
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_persistent<S, T, BZ, BR>, PNT, smem);
+    st.grid_cap[dev] = sms * (per_sm > 0 ? per_sm : 1);
+    st.err[dev] = r;
+  });
+  if (st.err[dev] != cudaSuccess) return st.err[dev];
+  if (!ctr) return cudaErrorInvalidValue;
+  const int grid = ntiles < st.grid_cap[dev] ? ntiles : st.grid_cap[dev];
+  pair_persistent<S, T, BZ, BR><<<grid, PNT, smem, s>>>(d, ti, ntiles, parity, ctr);
+  return cudaGetLastError();
+}
+
+struct PairTile { int storage, tz, tr; };
+#define AMLBM_PAIR_TILES(ST) {ST, 32, 16}, {ST, 32, 8}, {ST, 64, 8}, {ST, 28, 16}, {ST, 32, 32}, {ST, 64, 16}
+constexpr PairTile kPairTiles[] = {
+    {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 28, 8},
+    AMLBM_PAIR_TILES(AMLBM_STORE_F32), AMLBM_PAIR_TILES(AMLBM_STORE_F16), AMLBM_PAIR_TILES(AMLBM_STORE_BF16),
+};
+#undef AMLBM_PAIR_TILES
+
+template <class S>
+cudaError_t pair_dispatch(int tz, int tr, const InstDesc* d, const int* ti, int nt, int par, cudaStream_t s,
+                          int* ctr) {
+  if (nt <= 0) return cudaSuccess;
+#define AMLBM_PT(TZ, TR) \
+  if (tz == TZ && tr == TR) return launch_pair_t<S, TZ, TR>(d, ti, nt, par, s, ctr);
+  if constexpr (std::is_same<S, double>::value) {
+    AMLBM_PT(32, 8)
+    AMLBM_PT(28, 8)
+  } else {
+    AMLBM_PT(32, 16)
+    AMLBM_PT(32, 8)
+    AMLBM_PT(64, 8)
+    AMLBM_PT(28, 16)
+    AMLBM_PT(32, 32)
+    AMLBM_PT(64, 16)
+  }
+#undef AMLBM_PT
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool pair_tile_supported(int storage, int tz, int tr) {
+  for (const auto& e : kPairTiles)
+    if (e.storage == storage && e.tz == tz && e.tr == tr) return true;
+  return false;
+}
+
+int pair_tile_list(int storage, int* tz, int* tr, int cap) {
+  int n = 0;
+  for (const auto& e : kPairTiles)
+    if (e.storage == storage) {
+      if (n < cap && tz && tr) { tz[n] = e.tz; tr[n] = e.tr; }
+      ++n;
+    }
+  return n;
+}
+
+cudaError_t launch_step_pair(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt, int parity,
+                             cudaStream_t s, int* ctr) {
+  switch (storage) {
+    case AMLBM_STORE_F64: return pair_dispatch<double>(tz, tr, d, ti, nt, parity, s, ctr);
+    case AMLBM_STORE_F32: return pair_dispatch<float>(tz, tr, d, ti, nt, parity, s, ctr);
+    case AMLBM_STORE_F16: return pair_dispatch<__half>(tz, tr, d, ti, nt, parity, s, ctr);
+    case AMLBM_STORE_BF16: return pair_dispatch<__nv_bfloat16>(tz, tr, d, ti, nt, parity, s, ctr);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace amlbm

@@ -61,14 +61,21 @@ extern "C" int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void
 
   // lattices with walls in z, an inlet, an outlet or the Guo forcing run on the
   // fused schedule only
-  bool fused_only = false;
-  for (int i = 0; i < n; ++i)
+  bool fused_only = false, pair = true;
+  for (int i = 0; i < n; ++i) {
     fused_only = fused_only || inst[i].bc.z_bc != AMLBM_Z_PERIODIC ||
                  inst[i].bc.r_lo != AMLBM_RLO_AXIS || inst[i].bc.wall_r == AMLBM_WALL_OUTLET ||
                  inst[i].bc.forcing != AMLBM_FORCE_SHIFT;
+    // the pair schedule's conditions (amlbm_batch_create checks the rest)
+    pair = pair && inst[i].bc.z_bc == AMLBM_Z_PERIODIC && inst[i].bc.r_lo == AMLBM_RLO_AXIS &&
+           inst[i].bc.wall_r != AMLBM_WALL_OUTLET && inst[i].bc.src_mode == AMLBM_SRC_LOCAL &&
+           inst[i].Nz % 2 == 0;
+  }
   int timed = 0;
   double best_ms = 1e300;
-  for (int sched = AMLBM_SCHED_FUSED; sched <= (fused_only ? AMLBM_SCHED_FUSED : AMLBM_SCHED_SPLIT); ++sched) {
+  for (int sched = AMLBM_SCHED_FUSED; sched <= AMLBM_SCHED_PAIR; ++sched) {
+    if (sched == AMLBM_SCHED_SPLIT && fused_only) continue;
+    if (sched == AMLBM_SCHED_PAIR && !pair) continue;
     int tz[64], tr[64];
     const int nt = std::min(64, amlbm_tiles(storage, sched, tz, tr, 64));
     for (int c = 0; c < nt; ++c) {
@@ -80,6 +87,7 @@ extern "C" int amlbm_autotune(int n, const amlbm_instance* inst, int steps, void
       amlbm_batch* b = nullptr;
       int rc = amlbm_batch_create(n, inst, &t, stream, nullptr, 0, &b);
       if (rc == AMLBM_ENOMEM) continue;  // a tile whose workspace does not fit is no candidate
+      if (rc == AMLBM_EINVAL && sched == AMLBM_SCHED_PAIR) continue;  // lattices too large for it
       if (rc) return rc;
       for (int i = 0; i < n && !rc; ++i) rc = amlbm_batch_init_fields(b, i, rho[i].data(), nullptr, nullptr);
       if (!rc) rc = amlbm_batch_step(b, 3);  // warm-up: kernel attributes, first-touch
