@@ -38,7 +38,11 @@
 namespace amlbm {
 namespace {
 
-constexpr int PNT = 256;  // threads per CTA
+// Threads per CTA and the resident CTAs per SM the register budget must allow:
+// for the FP32-arithmetic forms 256 threads at 64 registers (four CTAs per SM
+// where the tile's shared memory fits four), for FP64 256 threads, one CTA.
+template <class T> struct Threads { static constexpr int value = 256, min_blocks = 4; };
+template <> struct Threads<D1> { static constexpr int value = 256, min_blocks = 1; };
 
 // Two adjacent elements of a storage or compute type as one vector access.
 template <class S> struct Vec2;
@@ -74,8 +78,7 @@ __device__ __forceinline__ void sts2(T* p, T a, T b) {
   using C = typename Lane<T>::C;
   st2<C>(reinterpret_cast<C*>(p), a.v, b.v);
 }
-// Row r of a register window `w` (rows of W values): the pairs of a shared
-// memory row starting at p + 2 * (first pair), covering columns [c0, c0 + 2 n).
+// N pairs of a shared-memory row from p into w[0 .. 2N).
 template <class T, int N>
 __device__ __forceinline__ void load_row(const T* p, T* w) {
 #pragma unroll
@@ -84,7 +87,10 @@ __device__ __forceinline__ void load_row(const T* p, T* w) {
 
 // Tile geometry (BZ x BR sites, BZ even).  Halos in (z, r): psi (8, 7),
 // d_r psi (6, 5), rho and u (4, 3), collided populations (2, 1); the z halos
-// are the fused schedule's rounded up to whole pairs.
+// are the fused schedule's rounded up to whole pairs.  Region A holds psi, d_r psi
+// and 1D d_r psi until the forces are known, then the nine collided populations;
+// region B rho, u_z, u_r and, between the two halves of stage 2, the forces
+// without the body force and psi.
 template <class T, int BZ, int BR>
 struct PGeo {
   static_assert(BZ % 2 == 0, "pair tiles are an even number of sites wide");
@@ -93,23 +99,15 @@ struct PGeo {
   static constexpr int FZ = BZ + 8, FR = BR + 6;
   static constexpr int SZ = BZ + 4, SR = BR + 2;
   static constexpr int nP = PZ * PR, nD = DZ * DR, nF = FZ * FR, nS = SZ * SR;
-  // psi, d_r psi, 1D d_r psi, rho, u_z, u_r, then nine collided populations
-  static constexpr size_t elems = (size_t)nP + 2 * nD + 3 * nF + 9 * nS;
+  static constexpr int nA = (nP + 2 * nD) > 9 * nS ? (nP + 2 * nD) : 9 * nS;
+  static constexpr size_t elems = (size_t)nA + 6 * nF;
   static constexpr size_t bytes = sizeof(T) * elems;
 };
 
-// Resident CTAs per SM the register allocation must allow (as many as the
-// tile's shared memory fits, at most three).
-template <class S, class T, int BZ, int BR>
-struct PMinBlocks {
-  static constexpr int fit = int((228u * 1024u) / (PGeo<T, BZ, BR>::bytes + 1024u));
-  static constexpr int value = std::is_same<S, double>::value ? 1 : (fit > 3 ? 3 : (fit < 1 ? 1 : fit));
-};
-
 // Flat walk over the pair tasks of a ROWS x PAIRS region.
-template <int ROWS, int PAIRS, class F>
+template <int NTH, int ROWS, int PAIRS, class F>
 __device__ __forceinline__ void for_pairs(F&& body) {
-  for (int t = threadIdx.x; t < ROWS * PAIRS; t += PNT) {
+  for (int t = threadIdx.x; t < ROWS * PAIRS; t += NTH) {
     const int lr = t / PAIRS, cp = t - lr * PAIRS;
     body(lr, cp);
   }
@@ -121,19 +119,39 @@ __device__ __forceinline__ int wrap_col(int k, int Nz, bool tiny) {
   return k < 0 ? k + Nz : (k >= Nz ? k - Nz : k);
 }
 
+// The force of Eq. scforce and Eq. scAxisExtra without the body force rho g_z
+// (forces() of the fused schedule, operation for operation, up to its last
+// fused multiply-add, which the caller applies once rho is known).
+template <class T>
+__device__ __forceinline__ void forces_partial(const Par<T>& q, T psi, T sz, T sr, bool ax, T dr0, T Drr, T Dzr,
+                                               T inv_r, T& Fz, T& Fr) {
+  const T gpsi = psi * q.negG;
+  Fz = gpsi * sz;
+  Fr = gpsi * sr;
+  if (ax) {
+    const T g = (psi * q.gfac) * inv_r;
+    Fz = fma(g, Dzr, Fz);
+    Fr = fma(g, fma(-dr0, inv_r, Drr), Fr);
+  }
+}
+
 template <class S, class T, int BZ, int BR>
 __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst,
                                           int tile, int parity, uint32_t step) {
   using C = typename Store<S>::C;
   using G = PGeo<T, BZ, BR>;
+  constexpr int NTH = Threads<T>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sPsi = reinterpret_cast<T*>(smem_raw);
+  T* sPsi = reinterpret_cast<T*>(smem_raw);  // region A, stages 0-2a
   T* sDr = sPsi + G::nP;
   T* sD1 = sDr + G::nD;
-  T* sRho = sD1 + G::nD;
+  T* sFs = sPsi;  // region A, stages 2b-4
+  T* sRho = sPsi + G::nA;  // region B
   T* sUz = sRho + G::nF;
   T* sUr = sUz + G::nF;
-  T* sFs = sUr + G::nF;
+  T* sFz = sUr + G::nF;
+  T* sFr = sFz + G::nF;
+  T* sPs = sFr + G::nF;
 
   const int inst = tile_inst[tile];
   const InstDesc& D = descs[inst];
@@ -152,18 +170,32 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   const bool tiny = Nz < BZ + 16;  // region columns may wrap more than once
 
   // Stage 0: psi on tile + (8, 7); rows mirrored about the axis and the wall.
-  for_pairs<G::PR, G::PZ / 2>([&](int lr, int cp) {
-    const int jj = reflect_row(j0 - 7 + lr, Nr);
-    const int kk = wrap_col(k0 - 8 + 2 * cp, Nz, tiny);
-    C a, b;
-    ld2<C>(psin + jj * P + kk, a, b);
-    sts2(sPsi + lr * G::PZ + 2 * cp, T{a}, T{b});
-  });
+  // All of a thread's loads are issued before its first store, so that their
+  // latencies overlap.
+  {
+    constexpr int PP = G::PZ / 2, TOT = G::PR * PP, NB = (TOT + NTH - 1) / NTH;
+    C va[NB], vb[NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n) {
+      const int t = threadIdx.x + n * NTH;
+      if (t < TOT) {
+        const int lr = t / PP, cp = t - lr * PP;
+        const int jj = reflect_row(j0 - 7 + lr, Nr);
+        const int kk = wrap_col(k0 - 8 + 2 * cp, Nz, tiny);
+        ld2<C>(psin + jj * P + kk, va[n], vb[n]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NB; ++n) {
+      const int t = threadIdx.x + n * NTH;
+      if (t < TOT) sts2(sPsi + 2 * t, T{va[n]}, T{vb[n]});  // PZ = 2 PP: row-major pairs
+    }
+  }
   __syncthreads();
 
   // Stage 1: isotropic d_r psi and 1D d_r psi on tile + (6, 5).
   if (ax) {
-    for_pairs<G::DR, G::DZ / 2>([&](int lr, int cp) {
+    for_pairs<NTH, G::DR, G::DZ / 2>([&](int lr, int cp) {
       // psi rows -2..2 around the pair, columns -2..3 (row 0 is not a tap)
       T w[5 * 6];
       const T* p = sPsi + (lr + 2) * G::PZ + 2 * cp;  // column -2 of the window at row 0
@@ -182,13 +214,61 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
     __syncthreads();
   }
 
-  // Stage 2 (tile + (4, 3)): moments, forces, u; on tile + (2, 1) also u^eq and
-  // the BGK collision of all nine populations into shared memory.
-  for_pairs<G::FR, G::FZ / 2>([&](int lr, int cp) {
+  // Stage 2a (tile + (4, 3)): Shan-Chen sums, d_rr psi, d_zr psi and the force
+  // without its body-force term; psi copied beside it (region A is reused next).
+  for_pairs<NTH, G::FR, G::FZ / 2>([&](int lr, int cp) {
     const int j = j0 - 3 + lr;
     if (j < 0 || j >= Nr) return;
-    const int kk = wrap_col(k0 - 4 + 2 * cp, Nz, tiny);
-    const int so = j * P + kk;
+    // psi rows -1..1, columns -2..3 around the pair
+    T wp[3 * 6];
+    const T* p = sPsi + (lr + 4) * G::PZ + 2 * cp + 2;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) load_row<T, 3>(p + (r - 1) * G::PZ, wp + 6 * r);
+    const T inv_r = inv_r_of(T(), j, r0c);
+    T Fz2[2], Fr2[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T psi = wp[6 + 2 + s];
+      T sz, sr;
+      sc_sums(wp + 6 + 2 + s, 6, sz, sr);
+      T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
+      if (ax) {
+        // d_r psi rows -2..2 (columns -1..2 on rows -1, 1; -2..3 on rows -2, 2; 0..1
+        // on row 0) and 1D d_r psi row 0 (columns -2..3)
+        const T* pd = sDr + (lr + 2) * G::DZ + 2 * cp + 2 + s;
+        T w[5 * 5];
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            const bool tap = (r == 2 && c == 2) || ((r == 1 || r == 3) && c >= 1 && c <= 3) ||
+                             ((r == 0 || r == 4) && (c == 0 || c == 2 || c == 4));
+            if (tap) w[5 * r + c] = pd[(r - 2) * G::DZ + (c - 2)];
+          }
+        dr0 = w[12];
+        Drr = iso_r(w + 12, 5);
+        const T* pe = sD1 + (lr + 2) * G::DZ + 2 * cp + 2 + s;
+        T e[5];
+#pragma unroll
+        for (int m = -2; m <= 2; ++m) e[m + 2] = m ? pe[m] : lit<T>(0.0);
+        Dzr = d1(e + 2, 1);
+      }
+      forces_partial(q, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz2[s], Fr2[s]);
+    }
+    const int fi = lr * G::FZ + 2 * cp;
+    sts2(sFz + fi, Fz2[0], Fz2[1]);
+    sts2(sFr + fi, Fr2[0], Fr2[1]);
+    sts2(sPs + fi, wp[8], wp[9]);
+  });
+  __syncthreads();
+
+  // Stage 2b (tile + (4, 3)): populations from global memory, moments, the body
+  // force, u (Eq. uhydro); on tile + (2, 1) also u^eq (Eq. ueq) and the BGK
+  // collision of all nine populations into region A.
+  for_pairs<NTH, G::FR, G::FZ / 2>([&](int lr, int cp) {
+    const int j = j0 - 3 + lr;
+    if (j < 0 || j >= Nr) return;
+    const int so = j * P + wrap_col(k0 - 4 + 2 * cp, Nz, tiny);
     S qa[9], qb[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) ld2<S>(fin + i * plane + so, qa[i], qb[i]);
@@ -197,41 +277,19 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
       ld2<C>(psin + plane + so, va, vb);
       ld2<C>(psin + 2 * plane + so, wa, wb);
     }
-    // psi rows -1..1, columns -2..3 around the pair
-    T wp[3 * 6];
-    const T* p = sPsi + (lr + 4) * G::PZ + 2 * cp + 2;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) load_row<T, 3>(p + (r - 1) * G::PZ, wp + 6 * r);
-    // d_r psi rows -2..2 (columns -2..3), 1D d_r psi row 0 (columns -2..3)
-    T wd[5 * 6], we[6];
-    if (ax) {
-      const T* pd = sDr + (lr + 2) * G::DZ + 2 * cp;
-#pragma unroll
-      for (int r = 0; r < 5; ++r) load_row<T, 3>(pd + (r - 2) * G::DZ, wd + 6 * r);
-      load_row<T, 3>(sD1 + (lr + 2) * G::DZ + 2 * cp, we);
-    }
-    const T inv_r = inv_r_of(T(), j, r0c);
+    const int fi = lr * G::FZ + 2 * cp;
+    T ps[2], fz[2], fr[2];
+    lds2(sPs + fi, ps[0], ps[1]);
+    lds2(sFz + fi, fz[0], fz[1]);
+    lds2(sFr + fi, fr[0], fr[1]);
     const bool coll = lr >= 2 && lr < G::FR - 2 && cp >= 1 && cp < G::FZ / 2 - 1;
     T rho2[2], uz2[2], ur2[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const T psi = wp[6 + 2 + s];
       T f[9];
-      decode_values<S>(shift, s ? qb : qa, psi.v, s ? vb : va, s ? wb : wa, inv_rho0c, rho0c, rrefc, f);
+      decode_values<S>(shift, s ? qb : qa, ps[s].v, s ? vb : va, s ? wb : wa, inv_rho0c, rho0c, rrefc, f);
       const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
-      T sz, sr;
-      sc_sums(wp + 6 + 2 + s, 6, sz, sr);
-      T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
-      if (ax) {
-        dr0 = wd[12 + 2 + s];
-        Drr = iso_r(wd + 12 + 2 + s, 6);
-        T e[5];
-#pragma unroll
-        for (int m = -2; m <= 2; ++m) e[m + 2] = m ? we[2 + s + m] : lit<T>(0.0);
-        Dzr = d1(e + 2, 1);
-      }
-      T Fz, Fr;
-      forces(q, rho, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz, Fr);
+      const T Fz = fma(rho, q.gz, fz[s]), Fr = fr[s];
       const T inv_rho = rcp(rho);
       const T uz = fma(Fz, lit<T>(0.5), jz) * inv_rho, ur = fma(Fr, lit<T>(0.5), jr) * inv_rho;
       rho2[s] = rho;
@@ -255,7 +313,6 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
         }
       }
     }
-    const int fi = lr * G::FZ + 2 * cp;
     sts2(sRho + fi, rho2[0], rho2[1]);
     sts2(sUz + fi, uz2[0], uz2[1]);
     sts2(sUr + fi, ur2[0], ur2[1]);
@@ -267,7 +324,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   // (free-slip) or odd (no-slip).
   if (ax && (j0 < 3 || j0 + BR + 3 > Nr)) {
     const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
-    for_pairs<G::FR, G::FZ / 2>([&](int lr, int cp) {
+    for_pairs<NTH, G::FR, G::FZ / 2>([&](int lr, int cp) {
       const int j = j0 - 3 + lr;
       int m;
       bool flip_z;
@@ -293,7 +350,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   // Stage 3 (tile + (2, 1)): velocity gradients and the sources of App. A,
   // added to the collided populations.
   if (ax) {
-    for_pairs<G::SR, G::SZ / 2>([&](int lr, int cp) {
+    for_pairs<NTH, G::SR, G::SZ / 2>([&](int lr, int cp) {
       const int j = j0 - 1 + lr;
       if (j < 0 || j >= Nr) return;
       const int fi = (lr + 2) * G::FZ + 2 * cp + 2;  // u at the pair's first site
@@ -310,7 +367,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
       T rr[2];
       lds2(sRho + fi, rr[0], rr[1]);
       const T inv_r = inv_r_of(T(), j, r0c);
-      T hs[2][9];
+      T* o = sFs + lr * G::SZ + 2 * cp;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const T druz = d1(wz + 4 + s, 2);
@@ -318,14 +375,10 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
         const T drur = d1(wr + 4 + s, 2);
         T S_, Hz, Hr;
         site_sources(q, rr[s], wz[4 + s], wr[4 + s], druz, dzur, drur, inv_r, S_, Hz, Hr);
-        sources(S_, Hz, Hr, hs[s]);
-      }
-      T* o = sFs + lr * G::SZ + 2 * cp;
+        T h[9];
+        sources(S_, Hz, Hr, h);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        T a, b;
-        lds2(o + i * G::nS, a, b);
-        sts2(o + i * G::nS, a + hs[0][i], b + hs[1][i]);
+        for (int i = 0; i < 9; ++i) o[i * G::nS + s] = o[i * G::nS + s] + h[i];
       }
     });
     __syncthreads();
@@ -337,26 +390,21 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   S* __restrict__ fout = static_cast<S*>(D.f[parity ^ 1]);
   C* __restrict__ psout = static_cast<C*>(D.psi[parity ^ 1]);
   const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
-  for_pairs<BR, BZ / 2>([&](int lr, int cp) {
+  for_pairs<NTH, BR, BZ / 2>([&](int lr, int cp) {
     const int j = j0 + lr, k = k0 + 2 * cp;
     if (j >= Nr || k >= Nz) return;
     const bool edge = (j == 0) || (j == Nr - 1);
-    T fn[2][9];
     const T* c0 = sFs + (lr + 1) * G::SZ + 2 * cp + 2;  // the pair's first site
-    if (!edge) {
+    const int o = j * P + k;
+    S qv[2][9];
+    C ps[2], vz[2], vr[2];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const T* src = c0 + i * G::nS - cr_(i) * G::SZ - cz_(i);
-        if (cz_(i) == 0) {
-          lds2(src, fn[0][i], fn[1][i]);
-        } else {
-          fn[0][i] = src[0];
-          fn[1][i] = src[1];
-        }
-      }
-    } else {
+    for (int s = 0; s < 2; ++s) {
+      T fn[9];
+      if (!edge) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < 9; ++i) fn[i] = c0[i * G::nS - cr_(i) * G::SZ - cz_(i) + s];
+      } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           int dl = -cr_(i), dc = -cz_(i), ii = i;
@@ -368,30 +416,20 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
             if (noslip) { dc = 0; ii = opp_(i); }
             else { ii = mirror_(i); }
           }
-          fn[s][i] = c0[ii * G::nS + dl * G::SZ + dc + s];
+          fn[i] = c0[ii * G::nS + dl * G::SZ + dc + s];
         }
+      }
+      const T rho = moment0(fn);
+      ps[s] = psi_of(q, rho).v;
+      encode_values<S>(shift, fn, rho, ps[s], inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k + s),
+                       step, qv[s], vz[s], vr[s]);
     }
-    S qa[9], qb[9];
-    C va, vb, wa, wb, pa, pb;
-    {
-      const T rho = moment0(fn[0]);
-      pa = psi_of(q, rho).v;
-      encode_values<S>(shift, fn[0], rho, pa, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k), step,
-                       qa, va, wa);
-    }
-    {
-      const T rho = moment0(fn[1]);
-      pb = psi_of(q, rho).v;
-      encode_values<S>(shift, fn[1], rho, pb, inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k + 1),
-                       step, qb, vb, wb);
-    }
-    const int o = j * P + k;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) st2<S>(fout + i * plane + o, qa[i], qb[i]);
-    st2<C>(psout + o, pa, pb);
+    for (int i = 0; i < 9; ++i) st2<S>(fout + i * plane + o, qv[0][i], qv[1][i]);
+    st2<C>(psout + o, ps[0], ps[1]);
     if (shift == 3) {
-      st2<C>(psout + plane + o, va, vb);
-      st2<C>(psout + 2 * plane + o, wa, wb);
+      st2<C>(psout + plane + o, vz[0], vz[1]);
+      st2<C>(psout + 2 * plane + o, vr[0], vr[1]);
     }
   });
 }
@@ -400,7 +438,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
 // is left (ctr as for the fused schedule: this step's tile counter and step
 // number at [parity] and [2 + parity], the next step's reset here).
 template <class S, class T, int BZ, int BR>
-__global__ void __launch_bounds__(PNT, (PMinBlocks<S, T, BZ, BR>::value)) pair_persistent(
+__global__ void __launch_bounds__(Threads<T>::value, Threads<T>::min_blocks) pair_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
@@ -441,19 +479,21 @@ cudaError_t launch_pair_t(const InstDesc* d, const int* ti, int ntiles, int pari
     int sms = 0, per_sm = 0;
     if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (r == cudaSuccess)
-      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_persistent<S, T, BZ, BR>, PNT, smem);
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_persistent<S, T, BZ, BR>,
+                                                        Threads<T>::value, smem);
     st.grid_cap[dev] = sms * (per_sm > 0 ? per_sm : 1);
     st.err[dev] = r;
   });
   if (st.err[dev] != cudaSuccess) return st.err[dev];
   if (!ctr) return cudaErrorInvalidValue;
   const int grid = ntiles < st.grid_cap[dev] ? ntiles : st.grid_cap[dev];
-  pair_persistent<S, T, BZ, BR><<<grid, PNT, smem, s>>>(d, ti, ntiles, parity, ctr);
+  pair_persistent<S, T, BZ, BR><<<grid, Threads<T>::value, smem, s>>>(d, ti, ntiles, parity, ctr);
   return cudaGetLastError();
 }
 
 struct PairTile { int storage, tz, tr; };
-#define AMLBM_PAIR_TILES(ST) {ST, 32, 16}, {ST, 32, 8}, {ST, 64, 8}, {ST, 28, 16}, {ST, 32, 32}, {ST, 64, 16}
+#define AMLBM_PAIR_TILES(ST) {ST, 32, 16}, {ST, 40, 16}, {ST, 24, 16}, {ST, 64, 8}, {ST, 40, 8}, {ST, 32, 32}, \
+                             {ST, 64, 16}
 constexpr PairTile kPairTiles[] = {
     {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 28, 8},
     AMLBM_PAIR_TILES(AMLBM_STORE_F32), AMLBM_PAIR_TILES(AMLBM_STORE_F16), AMLBM_PAIR_TILES(AMLBM_STORE_BF16),
@@ -471,9 +511,10 @@ cudaError_t pair_dispatch(int tz, int tr, const InstDesc* d, const int* ti, int 
     AMLBM_PT(28, 8)
   } else {
     AMLBM_PT(32, 16)
-    AMLBM_PT(32, 8)
+    AMLBM_PT(40, 16)
+    AMLBM_PT(24, 16)
     AMLBM_PT(64, 8)
-    AMLBM_PT(28, 16)
+    AMLBM_PT(40, 8)
     AMLBM_PT(32, 32)
     AMLBM_PT(64, 16)
   }

@@ -59,8 +59,9 @@ def test_pair_small_and_odd_shapes_bitwise(Nz, Nr):
     for storage in ("f32", "f64"):
         spec = amlbm.InstanceSpec(Nz, Nr, 0.9, -4.8)
         ref = run([spec], [fl], storage, "fused", (32, 8), 100)[0]
-        got = run([spec], [fl], storage, "pair", (32, 8), 100)[0]
-        assert np.array_equal(ref, got), (storage, np.abs(ref - got).max())
+        for tile in amlbm.tiles(storage, "pair"):
+            got = run([spec], [fl], storage, "pair", tuple(tile), 100)[0]
+            assert np.array_equal(ref, got), (storage, tile, np.abs(ref - got).max())
 
 
 def test_pair_fp64_matches_oracle_1000_steps():
@@ -92,5 +93,5 @@ def test_pair_sweep_equals_fused_bitwise(storage):
 def test_pair_rejects_lattices_outside_its_scope(kw, Nz):
     spec = amlbm.InstanceSpec(Nz, 16, 0.9, -5.0, **kw)
     with pytest.raises(amlbm.AmlbmError) as e:
-        amlbm.Batch([spec], storage="f32", tile=(32, 8), schedule="pair")
+        amlbm.Batch([spec], storage="f32", tile=(32, 16), schedule="pair")
     assert e.value.code == amlbm.EINVAL
