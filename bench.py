@@ -159,10 +159,21 @@ def max_over_ranks(value, world, device="cpu"):
     return float(t.item())
 
 
-def job_mlups(sites_per_rank, steps, max_ms, world):
-    """Whole-job lattice updates per second (millions): every rank's sites, over the
-    slowest rank's time."""
-    return world * sites_per_rank * steps / (max_ms * 1e-3) / 1e6
+def sum_over_ranks(value, world, device="cpu"):
+    """The sum of a per-rank value over all ranks."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_mlups(job_sites, steps, max_ms):
+    """Whole-job lattice updates per second (millions): the sites of all ranks (each
+    rank its own batch), over the slowest rank's time."""
+    return job_sites * steps / (max_ms * 1e-3) / 1e6
 
 
 def build_batch(storage, rank, tile="auto", graph_chunk=0, stream=None):
@@ -218,7 +229,8 @@ def run_gpu(args):
         total_ms = max_over_ranks(float(sum(times)), world, "cuda")
         if world > 1:
             dist.barrier()
-        mlups = job_mlups(sites, args.steps, total_ms, world)
+        job_sites = sum_over_ranks(sites, world, "cuda")
+        mlups = job_mlups(job_sites, args.steps, total_ms)
         avg_ms = total_ms / args.steps
         # the timed steps split into five consecutive chunks: median and spread of
         # the chunks' MLUPS (one run, not five)
@@ -253,7 +265,7 @@ def run_gpu(args):
             b.diagnostics_all(params, check=False, as_array=True)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e_val = job_mlups(sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3, world)
+        e2e_val = job_mlups(job_sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3)
         b.close()
 
         # the same workload in the other storage forms (plain FP64 is the
@@ -280,8 +292,8 @@ def run_gpu(args):
             scaled = scaled_cases(torch, tile, sched)
             precision = precision_vs_f64(torch)
 
-    traffic, tkernel = profiled_traffic(os.path.join(ROOT, "paper_1310_1871_gb300", "csrc", "amlbm_step.cu"))
-    kname = kernel_name(STORAGE, sched, tile)
+    kname, ksrc = kernel_name(STORAGE, sched, tile)
+    traffic, tkernel = profiled_traffic(ksrc)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(seconds=args.cpu_seconds)
@@ -322,11 +334,15 @@ CTYPE = {"f64": "double", "f32": "float", "f16": "__half", "bf16": "__nv_bfloat1
 
 
 def kernel_name(storage, sched, tile):
-    """The step kernel a batch of this storage, schedule and tile launches."""
+    """The step kernel a batch of this storage, schedule and tile launches, and the
+    source file that holds it."""
     t = CTYPE[storage]
+    csrc = os.path.join(ROOT, "paper_1310_1871_gb300", "csrc")
+    if sched == "pair":
+        return f"pair_persistent<{t}, {tile[0]}, {tile[1]}>", os.path.join(csrc, "amlbm_step_pair.cu")
     if sched == "fused":
-        return f"lbm_persistent<{t}, {tile[0]}, {tile[1]}>"
-    return f"stream_kernel<{t}, {tile[0]}, {tile[1]}> + force_kernel"
+        return f"lbm_persistent<{t}, {tile[0]}, {tile[1]}>", os.path.join(csrc, "amlbm_step.cu")
+    return f"stream_kernel<{t}, {tile[0]}, {tile[1]}> + force_kernel", os.path.join(csrc, "amlbm_step.cu")
 
 
 def graph_back_to_back(torch, rank, stream, steps, chunk=20):

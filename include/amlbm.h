@@ -220,12 +220,14 @@ void amlbm_destroy(amlbm_ctx* ctx);
  * cudaMalloc may then fail, and cudaMalloc / cudaFree synchronise the whole
  * device).  Same arguments, result and errors as amlbm_diagnostics; the
  * context is the input and *out the output.  The reduction scratch is a fixed
- * array of the library's own device memory (131,200 bytes, reserved on every
- * device that loads the library and held until the process exits), so:
+ * array of the library's own device memory (131,200 bytes on every device
+ * where the library's code is loaded, held until the process exits).  The
+ * CUDA runtime loads that code lazily; amlbm_create (which allocates anyway)
+ * loads it, and the code of the diagnostics kernels, on its device and looks up
+ * the array's address there, so this call triggers no loading and no
+ * allocation.  So:
  *   - lattices with Nz > AMLBM_NOALLOC_MAX_NZ are rejected with AMLBM_EINVAL;
- *   - the first call on a device looks up the array's address on that device
- *     (cudaGetSymbolAddress); make that first call, with the context's device
- *     current, before any stream capture;
+ *   - call it with the context's device current;
  *   - every call shares the array: each call writes every entry it reads, so
  *     nothing needs clearing, but calls that overlap on the GPU (several host
  *     threads or streams of one device) race and must be serialised.

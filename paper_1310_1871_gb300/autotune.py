@@ -29,7 +29,7 @@ def cache_path():
 def signature(specs, storage, device_name, version):
     """Key of a tuning: what the step's speed depends on (not tau, G or the fields)."""
     shapes = [[int(s.Nz), int(s.Nr), bool(s.axisym), str(s.src), str(s.wall), str(s.shift),
-               str(s.rounding), float(s.gz) != 0.0] for s in specs]
+               str(s.rounding), float(s.gz) != 0.0, str(s.forcing), str(s.z_bc), str(s.r_lo)] for s in specs]
     blob = json.dumps({"device": device_name, "version": version, "storage": storage, "shapes": shapes},
                       sort_keys=True)
     return hashlib.sha256(blob.encode()).hexdigest()[:32]

@@ -17,6 +17,32 @@
 
 using amlbm::InstDesc;
 
+namespace amlbm {
+// The amlbm_diag of a diagnostics result out[16] (h) after `steps` steps.
+void fill_diag(const double* h, long long steps, amlbm_diag* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
+  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
+  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
+  out->steps = (double)steps;
+}
+
+// The diagnostics parameters used when the caller passes none.
+amlbm_diag_params diag_defaults(const InstDesc& d) {
+  amlbm_diag_params p;
+  p.zc = d.Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1;
+  return p;
+}
+
+// The same error for a state whose diagnostics found bad sites, from every
+// diagnostics entry point.
+std::string unstable_message(double bad) {
+  return "non-finite or non-positive density at " + std::to_string((long long)bad) + " sites";
+}
+}  // namespace amlbm
+using amlbm::diag_defaults;
+using amlbm::fill_diag;
+
 namespace {
 
 thread_local std::string g_err;
@@ -82,25 +108,28 @@ bool all_pair_ok(const std::vector<amlbm_instance>& inst) {
 }
 
 // Schedule and tile when the caller gives none (fastest on the 64-drop sweep on
-// GB300): FP32 arithmetic forms take the fused schedule with the first tile of a
-// preference list that still gives every SM two CTAs over the whole batch; the
-// FP64 form, bound by FP64 arithmetic, takes the split schedule (less
-// recomputation).
+// GB300): the FP32-arithmetic forms take the pair schedule where every lattice
+// allows it (else the fused one), with the first tile of a preference list that
+// still gives every SM two CTAs over the whole batch; the FP64 form, bound by
+// FP64 arithmetic, takes the split schedule (less recomputation).
 void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched, int* tz, int* tr) {
   static const int pref64[][2] = {{32, 16}, {32, 8}, {32, 8}};
   static const int pref64f[][2] = {{32, 8}, {32, 8}, {32, 8}};  // fused, for bounded lattices
   static const int pref32[][2] = {{26, 16}, {64, 8}, {32, 8}};
+  static const int prefpair[][2] = {{32, 16}, {24, 16}, {24, 16}};
   bool any_bounded = false;
   for (const auto& I : inst) any_bounded = any_bounded || bounded(I.bc);
   const bool f64 = storage == AMLBM_STORE_F64;
-  const int(*pref)[2] = f64 ? (any_bounded ? pref64f : pref64) : pref32;
-  *sched = f64 && !any_bounded ? amlbm::SCHED_SPLIT : amlbm::SCHED_FUSED;
+  const bool pair = !f64 && all_pair_ok(inst);
+  const int(*pref)[2] = f64 ? (any_bounded ? pref64f : pref64) : pair ? prefpair : pref32;
+  *sched = f64 && !any_bounded ? amlbm::SCHED_SPLIT : pair ? amlbm::SCHED_PAIR : amlbm::SCHED_FUSED;
   for (int c = 0; c < 3; ++c) {
     const int z = pref[c][0], r = pref[c][1];
     long long tiles = 0;
     for (const auto& I : inst) tiles += (long long)((I.Nz + z - 1) / z) * ((I.Nr + r - 1) / r);
     if (tiles >= 2 * 152) { *tz = z; *tr = r; return; }
   }
+  *sched = f64 && !any_bounded ? amlbm::SCHED_SPLIT : amlbm::SCHED_FUSED;
   *tz = 32;
   *tr = 8;
 }
@@ -442,6 +471,9 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     delete b;
     return fail(AMLBM_ECUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
   }
+  // the allocation-free diagnostics' scratch: looked up now, in a call that
+  // allocates anyway (its failure surfaces at that entry point, not here)
+  amlbm::noalloc_prepare(storage);
   *out = b;
   return AMLBM_OK;
 }
@@ -544,20 +576,6 @@ int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double
     if (dst[q] && !wide)
       for (size_t n = 0; n < N; ++n) dst[q][n] = double(stage[q][n]);
   return AMLBM_OK;
-}
-
-void fill_diag(const double* h, long long steps, amlbm_diag* out) {
-  std::memset(out, 0, sizeof(*out));
-  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
-  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
-  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
-  out->steps = (double)steps;
-}
-
-amlbm_diag_params diag_defaults(const InstDesc& d) {
-  amlbm_diag_params p;
-  p.zc = d.Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1;
-  return p;
 }
 
 // Every instance from host arrays holding them back to back.  The new state is
@@ -703,8 +721,7 @@ int diag_host(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* ou
   AMLBM_CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
   AMLBM_CK(cudaStreamSynchronize(b->stream));
   fill_diag(h, b->steps[k], out);
-  if (out->bad > 0) return fail(AMLBM_EUNSTABLE, "non-finite or non-positive density at " +
-                                                    std::to_string((long long)out->bad) + " sites");
+  if (out->bad > 0) return fail(AMLBM_EUNSTABLE, amlbm::unstable_message(out->bad));
   return AMLBM_OK;
 }
 
@@ -713,7 +730,7 @@ int diag_host(amlbm_batch* b, int k, const amlbm_diag_params* dp, amlbm_diag* ou
 extern "C" {
 
 const char* amlbm_last_error(void) { return g_err.c_str(); }
-const char* amlbm_version(void) { return "amlbm 0.1 (sm_103a)"; }
+const char* amlbm_version(void) { return "amlbm 0.2 (sm_103a)"; }
 
 int amlbm_tiles(int storage, int schedule, int* tz, int* tr, int cap) {
   return amlbm::tile_list(storage, schedule, tz, tr, cap);

@@ -290,6 +290,15 @@ cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr
   return cudaGetLastError();
 }
 
+cudaError_t diag_preload() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, diag_partial_one<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, diag_final_one<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, diag_partial_one<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, diag_final_one<float>);
+  return e;
+}
+
 cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_jobs, const int* d_blkjob,
                             int njobs, int total_blocks, int parity, double* partials, double* cols,
                             double* out, cudaStream_t s) {

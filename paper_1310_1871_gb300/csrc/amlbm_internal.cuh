@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include "amlbm.h"
+
 namespace amlbm {
 
 // One lattice of a batch as the kernels see it.  Populations are stored as
@@ -58,6 +60,9 @@ cudaError_t launch_step(int storage, int schedule, int tz, int tr, const InstDes
                         int* ctr);
 cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d_desc,
                          const int* d_tile_inst, int ntiles, int toff, int parity, cudaStream_t s);
+// Loads the code of the read-back kernel of a storage form on the current
+// device (the CUDA runtime otherwise loads it at its first launch).
+cudaError_t macro_preload(int storage);
 // Tile of the read-back kernel: 26 x 16 for the FP32-arithmetic forms (less halo
 // work per site than 32 x 8), 32 x 8 for FP64.
 inline void rb_tile(int storage, int* tz, int* tr) {
@@ -91,6 +96,9 @@ cudaError_t launch_diag(int storage, const InstDesc* d_desc, int inst, int Nz, i
                         int parity, double zc, double R, double rho_l, double rho_v,
                         double* partials, int nblk, double* cols, double* out, cudaStream_t s);
 int diag_blocks(int Nz, int Nr);
+// Loads the code of the single-lattice diagnostics kernels on the current device
+// (the CUDA runtime otherwise loads it at their first launch).
+cudaError_t diag_preload();
 // One instance's share of a batched diagnostics pass: its parameters, its
 // blocks [blk0, blk0 + nblk) of the partial-sum grid (nblk = diag_blocks) and
 // its columns [col0, col0 + Nz) of the radius array.
@@ -139,5 +147,17 @@ int ctx_info(amlbm_ctx* ctx, CtxInfo* out);
 int ctx_readback(amlbm_ctx* ctx);
 // Record a message for amlbm_last_error() and return code.
 int set_error(int code, const std::string& msg);
+// Shared by the diagnostics entry points (amlbm_abi.cu): the amlbm_diag of a
+// result out[16] after `steps` steps, the parameters used when the caller
+// passes none, and the message of AMLBM_EUNSTABLE.
+void fill_diag(const double* h, long long steps, amlbm_diag* out);
+amlbm_diag_params diag_defaults(const InstDesc& d);
+std::string unstable_message(double bad);
+// Looks up, once per device and with that device current, the device address of
+// the allocation-free diagnostics' scratch array (amlbm_noalloc.cu), and loads
+// the code of the kernels that entry point launches for this storage form.
+// Lattice creation calls it, so that the lookup and the loading (which the CUDA
+// runtime otherwise does lazily) happen in a call that allocates anyway.
+int noalloc_prepare(int storage);
 
 }  // namespace amlbm

@@ -8,9 +8,13 @@
 // device, stalling the application's other streams).  This entry point
 // therefore takes its reduction scratch (per-block partial sums, per-column
 // interface radii and the 16-double result) from a fixed array in the
-// library's own device memory, reserved when the library is loaded on a
-// device and held until the process exits.  The lattice context supplies the
-// input (its current state); the caller supplies the output struct.
+// library's own device memory, held from the moment the library's code is
+// loaded on a device until the process exits.  The CUDA runtime loads that
+// code lazily; the first lattice created on a device looks up the array's
+// address there and loads the code of the diagnostics kernels (noalloc_prepare),
+// so that code is on the device before this entry point can be called and the
+// entry point itself never triggers the loading.  The lattice context supplies the input (its current state); the
+// caller supplies the output struct.
 //
 // The array is shared by every call on a device: a call overwrites every
 // entry it reads before reading it, so nothing has to be cleared between
@@ -45,7 +49,8 @@ double* g_scratch_ptr[kMaxDevices] = {};
 thread_local std::string g_err_local;
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current (by the first lattice created there, or
+// else by the first call).
 int scratch_for_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -74,6 +79,18 @@ int scratch_for_current_device(double** out) {
 
 }  // namespace
 
+namespace amlbm {
+int noalloc_prepare(int storage) {
+  double* p = nullptr;
+  const int rc = scratch_for_current_device(&p);
+  if (rc) return rc;
+  // the code of the kernels it launches (read-back, diagnostics), so that its
+  // first call loads nothing
+  if (macro_preload(storage) != cudaSuccess || diag_preload() != cudaSuccess) return AMLBM_ECUDA;
+  return AMLBM_OK;
+}
+}  // namespace amlbm
+
 extern "C" int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params* dp,
                                          amlbm_diag* out) {
   using amlbm::set_error;
@@ -92,12 +109,7 @@ extern "C" int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params
   double* scratch = nullptr;
   rc = scratch_for_current_device(&scratch);
   if (rc) return set_error(rc, g_err_local);
-  amlbm_diag_params p;
-  if (dp) {
-    p = *dp;
-  } else {
-    p.zc = Nz / 2.0; p.R = 1.0; p.rho_l = 2.0; p.rho_v = 0.1;
-  }
+  const amlbm_diag_params p = dp ? *dp : amlbm::diag_defaults(ci.host);
   if (!(p.R > 0) || !(p.rho_l != p.rho_v))
     return set_error(AMLBM_EINVAL, "diag params: need R > 0, rho_l != rho_v");
   rc = amlbm::ctx_readback(ctx);  // rho and u of the current state into the context's buffers
@@ -113,11 +125,7 @@ extern "C" int amlbm_diagnostics_noalloc(amlbm_ctx* ctx, const amlbm_diag_params
   e = cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(AMLBM_ECUDA, std::string("diag read-back: ") + cudaGetErrorString(e));
-  std::memset(out, 0, sizeof(*out));
-  out->mass2d = h[0]; out->mass3d = h[1]; out->momz3d = h[2]; out->Eke = h[3]; out->umax = h[4];
-  out->a2 = h[5]; out->A = h[6]; out->neck = h[7]; out->p_in = h[8]; out->p_out = h[9];
-  out->dp = h[10]; out->bad = h[11]; out->sumS = h[12];
-  out->steps = (double)ci.steps;
-  if (out->bad > 0) return set_error(AMLBM_EUNSTABLE, "non-finite or non-positive density");
+  amlbm::fill_diag(h, ci.steps, out);
+  if (out->bad > 0) return set_error(AMLBM_EUNSTABLE, amlbm::unstable_message(out->bad));
   return AMLBM_OK;
 }

@@ -116,7 +116,9 @@ __device__ __forceinline__ float fma_c(float a, float b, float c) { return __fma
 __device__ __forceinline__ double fma_c(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Random words of the stochastic rounding.  Each site seeds its own stream with
-// an integer hash (a xorshift-multiply mixer) of (site, step); the nine
+// an integer hash of (site, step): the xorshift-multiply mixer with shifts
+// 16, 15, 16 and multipliers 0x7feb352d, 0x846ca68b published by C. Wellons
+// ("lowbias32", hash-prospector, 2018); the nine
 // populations then take successive states of the linear congruential generator
 // x <- 1664525 x + 1013904223 (mod 2^32) (Knuth / Numerical Recipes constants),
 // whose top bits are the ones the codecs use.

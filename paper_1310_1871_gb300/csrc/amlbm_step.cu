@@ -955,6 +955,17 @@ cudaError_t launch_macro(int storage, int tz, int tr, const InstDesc* d, const i
   return dispatch_storage(storage, true, SCHED_FUSED, tz, tr, d, ti, nt, toff, parity, s, nullptr);
 }
 
+cudaError_t macro_preload(int storage) {
+  cudaFuncAttributes a;
+  switch (storage) {  // the read-back tiles of rb_tile()
+    case AMLBM_STORE_F64: return cudaFuncGetAttributes(&a, lbm_kernel<double, 32, 8, 1>);
+    case AMLBM_STORE_F32: return cudaFuncGetAttributes(&a, lbm_kernel<float, 26, 16, 1>);
+    case AMLBM_STORE_F16: return cudaFuncGetAttributes(&a, lbm_kernel<__half, 26, 16, 1>);
+    case AMLBM_STORE_BF16: return cudaFuncGetAttributes(&a, lbm_kernel<__nv_bfloat16, 26, 16, 1>);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_step_inter(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
                               void* inter, size_t plane, cudaStream_t s) {
   if (storage == AMLBM_STORE_F64) {

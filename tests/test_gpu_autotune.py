@@ -23,7 +23,8 @@ def sweep(n=6):
 def test_autotune_times_every_candidate(storage):
     _, specs = sweep()
     sched, tile, cands = amlbm.autotune_raw(specs, storage, steps=5)
-    n_expected = len(amlbm.tiles(storage, "fused")) + len(amlbm.tiles(storage, "split"))
+    n_expected = (len(amlbm.tiles(storage, "fused")) + len(amlbm.tiles(storage, "split")) +
+                  len(amlbm.tiles(storage, "pair")))
     assert len(cands) == n_expected
     assert all(c["ms_per_step"] > 0 for c in cands)
     fastest = min(cands, key=lambda c: c["ms_per_step"])
@@ -77,12 +78,14 @@ def test_every_compiled_tile_gives_the_same_state(storage):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("kw", [dict(z_bc="noslip", wall="noslip"), dict(forcing="guo")])
-def test_autotune_bounded_and_guo_take_fused_tiles_only(kw):
-    """Lattices with z walls or the Guo forcing run on the fused schedule only: the
-    autotuner times the fused tiles and no split candidate."""
+@pytest.mark.parametrize("kw,scheds", [(dict(z_bc="noslip", wall="noslip"), ("fused",)),
+                                       (dict(forcing="guo"), ("fused", "pair"))])
+def test_autotune_offers_only_the_schedules_a_lattice_allows(kw, scheds):
+    """Lattices with z walls run on the fused schedule only; the Guo forcing on the
+    fused and the pair schedules (not the split one): the autotuner times exactly
+    those candidates."""
     specs = [amlbm.InstanceSpec(64, 32, 0.9, -5.0, **kw), amlbm.InstanceSpec(48, 24, 1.0, -5.0)]
     sched, tile, cands = amlbm.autotune_raw(specs, "f32", steps=5)
-    assert sched == "fused"
-    assert len(cands) == len(amlbm.tiles("f32", "fused"))
-    assert all(c["schedule"] == "fused" for c in cands)
+    assert sched in scheds
+    assert len(cands) == sum(len(amlbm.tiles("f32", s)) for s in scheds)
+    assert all(c["schedule"] in scheds for c in cands)

@@ -55,6 +55,25 @@ def test_noalloc_diagnostics_match_two_calls_in_a_row(storage):
     lat.close()
 
 
+def test_noalloc_calls_allocate_no_device_memory():
+    """The property the entry point exists for: once the lattice exists (amlbm_create
+    loads the code and looks up the scratch array), repeated calls leave the
+    device's free memory exactly as it was."""
+    Nz, Nr = 64, 32
+    lat = amlbm.Lattice(Nz, Nr, tau=1.0, G=-5.0, storage="f32")
+    lat.init_fields(*I.drop(Nz, Nr, 32.0, 10.0))
+    lat.step(5)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        rc, d = noalloc(lat, 32.0, 10.0, 1.93, 0.16)
+        assert rc == amlbm.OK and d["bad"] == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    lat.close()
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_rejects_lattices_beyond_the_static_limit():
     Nz = 8192 + 1
     lat = amlbm.Lattice(Nz, 4, tau=1.0, G=-5.0)
