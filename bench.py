@@ -176,11 +176,21 @@ def job_mlups(job_sites, steps, max_ms):
     return job_sites * steps / (max_ms * 1e-3) / 1e6
 
 
-def build_batch(storage, rank, tile="auto", graph_chunk=0, stream=None):
+def parse_launch(text):
+    """'auto' or 'SCHEDULE:TZxTR' (e.g. pair:32x16) -> (tile, schedule) for amlbm.Batch."""
+    if text == "auto":
+        return "auto", "auto"
+    sched, tile = text.split(":")
+    tz, tr = (int(v) for v in tile.lower().split("x"))
+    return (tz, tr), sched
+
+
+def build_batch(storage, rank, tile="auto", graph_chunk=0, stream=None, schedule="auto"):
     from paper_1310_1871_gb300 import amlbm
     inst = I.batch_sweep(64, seed0=rank_seed0(rank))
     specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
-    b = amlbm.Batch(specs, storage=storage, tile=tile, graph_chunk=graph_chunk, stream=stream)
+    b = amlbm.Batch(specs, storage=storage, tile=tile, graph_chunk=graph_chunk, stream=stream,
+                    schedule=schedule)
     for k, x in enumerate(inst):
         b.init_fields(k, *x.make_fields())
     return b, inst
@@ -215,7 +225,8 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
-        b, inst = build_batch(STORAGE, rank, stream=stream)
+        tile0, sched0 = parse_launch(args.launch)
+        b, inst = build_batch(STORAGE, rank, tile=tile0, schedule=sched0, stream=stream)
         sites = b.sites
         sched, tile, lps = b.schedule, b.tile, b.launches_per_step
         tuned = b.tuned
@@ -240,8 +251,8 @@ def run_gpu(args):
         hbm, kind = peaks()
         achieved = BYTES_PER_LU[STORAGE] * sites / (avg_ms * 1e-3) / 1e9
         b.close()
-        graph = graph_back_to_back(torch, rank, stream, max(20, min(args.steps, 2000)))
-        b, inst = build_batch(STORAGE, rank, stream=stream)
+        graph = graph_back_to_back(torch, rank, stream, max(20, min(args.steps, 2000)), tile0, sched0)
+        b, inst = build_batch(STORAGE, rank, tile=tile0, schedule=sched0, stream=stream)
 
         # end to end through the public C ABI: every step uploads every instance's
         # fields from pinned host memory (one copy per field array for the whole
@@ -309,7 +320,8 @@ def run_gpu(args):
                          "traffic": (round(traffic) if traffic and tkernel == kname else None),
                          "peak_kind": f"{kind} (HBM copy bandwidth)", "bytes_per_lu": BYTES_PER_LU[STORAGE],
                          "kernel": kname,
-                         "limiter": "instruction issue of the per-site stencil chain, not HBM"},
+                         "limiter": "latency of the per-tile stage chain (barrier and load stalls, 54 % issue), "
+                                    "not HBM (DRAM 11 % busy)"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
@@ -345,12 +357,12 @@ def kernel_name(storage, sched, tile):
     return f"stream_kernel<{t}, {tile[0]}, {tile[1]}> + force_kernel", os.path.join(csrc, "amlbm_step.cu")
 
 
-def graph_back_to_back(torch, rank, stream, steps, chunk=20):
+def graph_back_to_back(torch, rank, stream, steps, tile="auto", schedule="auto", chunk=20):
     """The headline form's steps replayed back to back from captured CUDA graphs of
     `chunk` timesteps each (amlbm_batch_step with graph_chunk): no L2 flush between
     steps, so the state stays L2-resident; CUDA events around all `steps`."""
     steps = max(chunk, steps // chunk * chunk)
-    b, _ = build_batch(STORAGE, rank, graph_chunk=chunk, stream=stream)
+    b, _ = build_batch(STORAGE, rank, tile=tile, graph_chunk=chunk, stream=stream, schedule=schedule)
     b.step(3 * chunk)  # warm-up (captures the graphs of both parities)
     torch.cuda.synchronize()
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -598,6 +610,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64/FP32 comparison runs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--launch", default="auto",
+                    help="launch of the timed batch: auto (the autotuner's choice) or SCHEDULE:TZxTR, "
+                         "e.g. pair:32x16")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
