@@ -39,18 +39,13 @@
 namespace amlbm {
 namespace {
 
-// Threads per CTA and the resident CTAs per SM the register budget must allow:
-// for the FP32-arithmetic forms 256 threads at 64 registers (four CTAs per SM
-// where the tile's shared memory fits four), for FP64 256 threads, one CTA.
-template <class T> struct Threads { static constexpr int value = 256, min_blocks = 4; };
-template <> struct Threads<D1> { static constexpr int value = 256, min_blocks = 1; };
-
 // Tile geometry (BZ x BR sites, BZ even).  Halos in (z, r): psi (8, 7),
 // d_r psi (6, 5), rho and u (4, 3), collided populations (2, 1); the z halos
 // are the fused schedule's rounded up to whole pairs.  Region A holds psi, d_r psi
-// and 1D d_r psi until the forces are known, then the nine collided populations;
-// region B rho, u_z, u_r and, between the two halves of stage 2, the forces
-// without the body force and psi.
+// and 1D d_r psi until the forces are known, then the nine collided populations.
+// Region B holds three planes of the force region: between the two halves of
+// stage 2 psi and the force without the body force, then rho, u_z and u_r, each
+// written over the value the same thread read from it.
 template <class T, int BZ, int BR>
 struct PGeo {
   static_assert(BZ % 2 == 0, "pair tiles are an even number of sites wide");
@@ -60,8 +55,23 @@ struct PGeo {
   static constexpr int SZ = BZ + 4, SR = BR + 2;
   static constexpr int nP = PZ * PR, nD = DZ * DR, nF = FZ * FR, nS = SZ * SR;
   static constexpr int nA = (nP + 2 * nD) > 9 * nS ? (nP + 2 * nD) : 9 * nS;
-  static constexpr size_t elems = (size_t)nA + 6 * nF;
+  static constexpr size_t elems = (size_t)nA + 3 * nF;
   static constexpr size_t bytes = sizeof(T) * elems;
+};
+
+// Threads per CTA and the resident CTAs per SM the register budget must allow.
+// FP32 arithmetic: 256 threads; four CTAs per SM (64 registers) where the tile's
+// shared memory fits four in the SM's 228 KB (1 KB reserved per CTA), else as
+// many as fit (three: 80 registers).  FP64: 256 threads, one CTA.
+template <class T, int BZ, int BR>
+struct Threads {
+  static constexpr int value = 256;
+  static constexpr int fit = (int)(233472 / (PGeo<T, BZ, BR>::bytes + 1024 + 16));
+  static constexpr int min_blocks = fit >= 4 ? 4 : (fit >= 1 ? fit : 1);
+};
+template <int BZ, int BR>
+struct Threads<D1, BZ, BR> {
+  static constexpr int value = 256, min_blocks = 1;
 };
 
 // Flat walk over the pair tasks of a ROWS x PAIRS region.
@@ -78,7 +88,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
                                           int tile, int parity, uint32_t step) {
   using C = typename Store<S>::C;
   using G = PGeo<T, BZ, BR>;
-  constexpr int NTH = Threads<T>::value;
+  constexpr int NTH = Threads<T, BZ, BR>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sPsi = reinterpret_cast<T*>(smem_raw);  // region A, stages 0-2a
   T* sDr = sPsi + G::nP;
@@ -87,9 +97,9 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   T* sRho = sPsi + G::nA;  // region B
   T* sUz = sRho + G::nF;
   T* sUr = sUz + G::nF;
-  T* sFz = sUr + G::nF;
-  T* sFr = sFz + G::nF;
-  T* sPs = sFr + G::nF;
+  T* sFz = sUz;  // stage 2a writes, stage 2b reads and overwrites (same task, same thread)
+  T* sFr = sUr;
+  T* sPs = sRho;
 
   const int inst = tile_inst[tile];
   const InstDesc& D = descs[inst];
@@ -376,7 +386,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
 // is left (ctr as for the fused schedule: this step's tile counter and step
 // number at [parity] and [2 + parity], the next step's reset here).
 template <class S, class T, int BZ, int BR>
-__global__ void __launch_bounds__(Threads<T>::value, Threads<T>::min_blocks) pair_persistent(
+__global__ void __launch_bounds__(Threads<T, BZ, BR>::value, Threads<T, BZ, BR>::min_blocks) pair_persistent(
     const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int ntiles, int parity,
     int* __restrict__ ctr) {
   __shared__ int s_tile;
@@ -418,20 +428,20 @@ cudaError_t launch_pair_t(const InstDesc* d, const int* ti, int ntiles, int pari
     if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (r == cudaSuccess)
       r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_persistent<S, T, BZ, BR>,
-                                                        Threads<T>::value, smem);
+                                                        Threads<T, BZ, BR>::value, smem);
     st.grid_cap[dev] = sms * (per_sm > 0 ? per_sm : 1);
     st.err[dev] = r;
   });
   if (st.err[dev] != cudaSuccess) return st.err[dev];
   if (!ctr) return cudaErrorInvalidValue;
   const int grid = ntiles < st.grid_cap[dev] ? ntiles : st.grid_cap[dev];
-  pair_persistent<S, T, BZ, BR><<<grid, Threads<T>::value, smem, s>>>(d, ti, ntiles, parity, ctr);
+  pair_persistent<S, T, BZ, BR><<<grid, Threads<T, BZ, BR>::value, smem, s>>>(d, ti, ntiles, parity, ctr);
   return cudaGetLastError();
 }
 
 struct PairTile { int storage, tz, tr; };
-#define AMLBM_PAIR_TILES(ST) {ST, 32, 16}, {ST, 40, 16}, {ST, 24, 16}, {ST, 64, 8}, {ST, 40, 8}, {ST, 32, 32}, \
-                             {ST, 64, 16}
+#define AMLBM_PAIR_TILES(ST) {ST, 40, 24}, {ST, 48, 20}, {ST, 32, 16}, {ST, 48, 16}, {ST, 24, 16}, \
+                             {ST, 64, 16}, {ST, 32, 32}, {ST, 48, 22}
 constexpr PairTile kPairTiles[] = {
     {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 28, 8},
     AMLBM_PAIR_TILES(AMLBM_STORE_F32), AMLBM_PAIR_TILES(AMLBM_STORE_F16), AMLBM_PAIR_TILES(AMLBM_STORE_BF16),
@@ -448,13 +458,14 @@ cudaError_t pair_dispatch(int tz, int tr, const InstDesc* d, const int* ti, int 
     AMLBM_PT(32, 8)
     AMLBM_PT(28, 8)
   } else {
+    AMLBM_PT(40, 24)
+    AMLBM_PT(48, 20)
     AMLBM_PT(32, 16)
-    AMLBM_PT(40, 16)
+    AMLBM_PT(48, 16)
     AMLBM_PT(24, 16)
-    AMLBM_PT(64, 8)
-    AMLBM_PT(40, 8)
-    AMLBM_PT(32, 32)
     AMLBM_PT(64, 16)
+    AMLBM_PT(32, 32)
+    AMLBM_PT(48, 22)
   }
 #undef AMLBM_PT
   return cudaErrorInvalidValue;
