@@ -320,8 +320,8 @@ def run_gpu(args):
                          "traffic": (round(traffic) if traffic and tkernel == kname else None),
                          "peak_kind": f"{kind} (HBM copy bandwidth)", "bytes_per_lu": BYTES_PER_LU[STORAGE],
                          "kernel": kname,
-                         "limiter": "latency of the per-tile stage chain (barrier and load stalls, 54 % issue), "
-                                    "not HBM (DRAM 11 % busy)"},
+                         "limiter": "latency of the per-tile stage chain (barrier and load stalls, 51 % issue), "
+                                    "not HBM (DRAM 12 % busy)"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
