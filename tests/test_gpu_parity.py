@@ -88,34 +88,49 @@ def test_fp64_thread_full_size():
     check_fp64(run_pair(200, 128, 1000, I.thread(200, 128, 25.0, 0.1)))
 
 
-# Max relative error in rho after 1000 steps of the static-drop workload, per
-# storage form and shift (measured values are printed; the bounds below are the
-# ones each form meets with margin).  The 16-bit errors are random walks whose
-# maximum over the sites varies with the drop's placement: over four placements
-# BF16 measured 1.0e-2 .. 6.2e-2 rounded to nearest and 4.3e-3 .. 1.8e-2 with
-# stochastic rounding, FP16 7e-4 .. 3.4e-3 either way.
-PRECISION_CASES = [
-    ("f32", "none", "nearest", 1e-4), ("f32", "local", "nearest", 1e-4),
+# Max relative error in rho after 1000 steps of the static-drop workload against
+# the FP64 oracle, per storage form, shift and rounding.
+#
+# Forms held to the stated accuracy target, 1e-4:
+TARGET_FORMS = [("f32", "none", "nearest"), ("f32", "local", "nearest"), ("f32", "equilibrium", "nearest")]
+#
+# Forms that do NOT meet the 1e-4 target.  Their bounds are measured findings with
+# margin, kept as regression bounds on the measured error, not the specification.
+# The 16-bit errors are random walks whose maximum over the sites varies with the
+# drop's placement: over four placements BF16 measured 1.0e-2 .. 6.2e-2 rounded to
+# nearest and 4.3e-3 .. 1.8e-2 with stochastic rounding, FP16 7e-4 .. 3.4e-3 either
+# way; with the equilibrium shift (the 16-bit value holds f_i - f^eq_i) FP16 1.1e-5 ..
+# 1.1e-4 (nearest), BF16 2.2e-4 .. 1.5e-3 (nearest) and 2.0e-4 .. 2.0e-3 (stochastic).
+BELOW_TARGET_FINDINGS = [
     ("f16", "local", "nearest", 5e-3), ("bf16", "local", "nearest", 1.5e-1),
     ("f16", "local", "stochastic", 5e-3), ("bf16", "local", "stochastic", 3e-2),
     ("f16", "global", "nearest", 1.0), ("bf16", "global", "nearest", 1.0),
-    # equilibrium shift (the 16-bit value holds f_i - f^eq_i): over the four placements
-    # FP16 measured 1.1e-5 .. 1.1e-4 (nearest), BF16 2.2e-4 .. 1.5e-3 (nearest) and
-    # 2.0e-4 .. 2.0e-3 (stochastic)
     ("f16", "equilibrium", "nearest", 2.5e-4), ("bf16", "equilibrium", "nearest", 4e-3),
-    ("bf16", "equilibrium", "stochastic", 5e-3), ("f32", "equilibrium", "nearest", 1e-4),
+    ("bf16", "equilibrium", "stochastic", 5e-3),
 ]
 
 
-@pytest.mark.parametrize("storage,shift,rounding,bound", PRECISION_CASES)
-def test_reduced_precision_forms(storage, shift, rounding, bound):
-    """FP32 arithmetic with FP32 or 16-bit storage of f_i - W_i s against the FP64 oracle."""
+def drop_rho_error(storage, shift, rounding):
     _, _, (rho, uz, ur), F = run_pair(64, 32, 1000, I.drop(64, 32, 32.0, 12.0), storage=storage,
                                       tile=(32, 8), shift=shift, rounding=rounding)
     err = np.abs(rho / F["rho"] - 1).max()
     uerr = max(np.abs(uz - F["uz"]).max(), np.abs(ur - F["ur"]).max()) / np.abs(F["uz"]).max()
     print(f"{storage}/{shift}/{rounding}: rho max rel err {err:.3e}, u normwise {uerr:.3e}")
-    assert np.isfinite(rho).all() and err < bound
+    assert np.isfinite(rho).all()
+    return err
+
+
+@pytest.mark.parametrize("storage,shift,rounding", TARGET_FORMS)
+def test_forms_meeting_the_accuracy_target(storage, shift, rounding):
+    """FP32 arithmetic and FP32 storage against the FP64 oracle: within 1e-4."""
+    assert drop_rho_error(storage, shift, rounding) <= 1e-4
+
+
+@pytest.mark.parametrize("storage,shift,rounding,bound", BELOW_TARGET_FINDINGS)
+def test_forms_below_the_target_stay_at_their_measured_error(storage, shift, rounding, bound):
+    """16-bit storage of f_i - W_i s (or of f_i - f^eq_i): these miss the 1e-4 target;
+    the bound only keeps their measured error from growing."""
+    assert drop_rho_error(storage, shift, rounding) < bound
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
