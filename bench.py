@@ -258,25 +258,33 @@ def run_gpu(args):
         # fields from pinned host memory (one copy per field array for the whole
         # batch), runs one timestep, and reads every instance's diagnostics (FP64
         # reductions) back to the host
+        # The FP32 form computes in FP32 and rounds its inputs to FP32 first, so
+        # its fields go up as FP32 (amlbm_batch_init_all_f32, the same state); the
+        # FP64 fields are timed as well (e2e_fp64_inputs).
         e2e_steps = max(3, min(args.steps, 50))
         cols = [np.concatenate([np.ravel(x.make_fields()[q]) for x in inst]) for q in range(3)]
-        pinned = [torch.from_numpy(c).pin_memory() for c in cols]
-        host = [t.numpy() for t in pinned]
         params = np.array([[x.zc, x.R, x.rho_l, x.rho_v] for x in inst], dtype=np.float64)
-        h2d = sum(a.nbytes for a in host)
         d2h = 64 * 16 * 8
-        b.init_all(*host)
-        b.step(1)
-        b.diagnostics_all(params, check=False, as_array=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+
+        def e2e_run(dtype):
+            pinned = [torch.from_numpy(c.astype(dtype)).pin_memory() for c in cols]
+            host = [t.numpy() for t in pinned]
             b.init_all(*host)
             b.step(1)
             b.diagnostics_all(params, check=False, as_array=True)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e2e_val = job_mlups(job_sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                b.init_all(*host)
+                b.step(1)
+                b.diagnostics_all(params, check=False, as_array=True)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            return (job_mlups(job_sites, e2e_steps, max_over_ranks(e2e_s, world, "cuda") * 1e3),
+                    sum(a.nbytes for a in host))
+
+        e2e_val, h2d = e2e_run(np.float32 if STORAGE != "f64" else np.float64)
+        e2e64_val, h2d64 = e2e_run(np.float64)
         b.close()
 
         # the same workload in the other storage forms (plain FP64 is the
@@ -325,8 +333,12 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
-                    "path": "amlbm_batch_init_all (pinned host, all 64 instances) + amlbm_batch_step(1) + "
-                            "amlbm_batch_diagnostics_all"},
+                    "path": "amlbm_batch_init_all_f32 (pinned FP32 host arrays, all 64 instances) + "
+                            "amlbm_batch_step(1) + amlbm_batch_diagnostics_all"},
+            "e2e_fp64_inputs": {"value": round(e2e64_val, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d64),
+                                "d2h_bytes_per_step": int(d2h),
+                                "path": "amlbm_batch_init_all (pinned FP64 host arrays) + amlbm_batch_step(1) + "
+                                        "amlbm_batch_diagnostics_all"},
             "gpu_launches": args.steps * lps,
             "clocks": clk.summary(),
             "graph_back_to_back": graph,

@@ -366,8 +366,9 @@ typedef struct amlbm_tune_result {
  * n instances (all with inst[0].bc.storage) it creates a temporary batch for
  * every compiled (schedule, tile) pair, sets a resting drop on every lattice,
  * runs 3 warm-up and 3 x `steps` timed timesteps on cuda_stream, and writes the
- * fastest pair to *best (graph_chunk 0) and, when results is not NULL, up to cap
- * candidates with their timings.  Every candidate computes the same state.
+ * fastest pair to *best (graph_chunk 0; a candidate within 0.5 % of an earlier
+ * one, in schedule and amlbm_tiles order, does not replace it) and, when results
+ * is not NULL, up to cap candidates with their timings.  Every candidate computes the same state.
  * Allocates and frees device memory for each candidate (it is not capturable)
  * and synchronises the stream.  Returns the number of candidates timed (> 0)
  * or a negative status. */
@@ -402,6 +403,13 @@ int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, 
  * that follow equal those of a newly created batch.  Synchronises the batch
  * stream. */
 int amlbm_batch_init_all(amlbm_batch* b, const double* rho, const double* uz, const double* ur);
+/* amlbm_batch_init_all from FP32 host arrays (same layout, ownership, checks
+ * and errors), half the bytes over the CPU-GPU link.  Each value is widened
+ * exactly to FP64, so the state equals that of amlbm_batch_init_all given the
+ * same values in FP64; the FP32-arithmetic forms (FP32, FP16 and BF16 storage)
+ * round their FP64 inputs to FP32 first, so for them it equals
+ * amlbm_batch_init_all of any FP64 arrays that round to these values. */
+int amlbm_batch_init_all_f32(amlbm_batch* b, const float* rho, const float* uz, const float* ur);
 /* The diagnostics of every instance in one pass (one read-back launch, one
  * partial-sum launch, one final launch, one device-to-host copy): dp holds n
  * parameter sets (NULL: the defaults of amlbm_batch_diagnostics), out receives

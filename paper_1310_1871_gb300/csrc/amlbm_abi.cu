@@ -583,32 +583,34 @@ int read_host(amlbm_batch* b, int k, double* rho, double* uz, double* ur, double
 // the device check finds every rho positive and finite.
 // Device address of a host array the GPU can read in place (page-locked memory,
 // mapped into the unified address space), or nullptr.
-const double* device_view(const double* h) {
+template <class In>
+const In* device_view(const In* h) {
   if (!h) return nullptr;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const double*>(a.devicePointer) : nullptr;
+  return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const In*>(a.devicePointer) : nullptr;
 }
 
-int init_all_host(amlbm_batch* b, const double* rho, const double* uz, const double* ur) {
+template <class In>
+int init_all_host(amlbm_batch* b, const In* rho, const In* uz, const In* ur) {
   if (!b) return fail(AMLBM_EINVAL, "NULL batch");
   if (!rho) return fail(AMLBM_EINVAL, "rho is NULL");
   const long long T = b->sites;
-  double* st = reinterpret_cast<double*>(b->arena + b->L.upload);
+  In* st = reinterpret_cast<In*>(b->arena + b->L.upload);  // room for three FP64 arrays
   const long long* off = reinterpret_cast<const long long*>(b->arena + b->L.site_off);
   int* bad = b->d_ctr + 4;
   // Page-locked host arrays are read by the init kernel in place (over the
   // CPU-GPU link, without a separate copy); others are copied to the device first.
-  const double* src[3] = {rho, uz, ur};
-  const double* dev[3] = {nullptr, nullptr, nullptr};
+  const In* src[3] = {rho, uz, ur};
+  const In* dev[3] = {nullptr, nullptr, nullptr};
   for (int q = 0; q < 3; ++q) {
     if (!src[q]) continue;
     dev[q] = device_view(src[q]);
     if (!dev[q]) {
-      AMLBM_CK(cudaMemcpyAsync(st + q * T, src[q], T * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+      AMLBM_CK(cudaMemcpyAsync(st + q * T, src[q], T * sizeof(In), cudaMemcpyHostToDevice, b->stream));
       dev[q] = st + q * T;
     }
   }
@@ -794,7 +796,11 @@ int amlbm_batch_diagnostics(amlbm_batch* b, int k, const amlbm_diag_params* dp, 
 }
 
 int amlbm_batch_init_all(amlbm_batch* b, const double* rho, const double* uz, const double* ur) {
-  return init_all_host(b, rho, uz, ur);
+  return init_all_host<double>(b, rho, uz, ur);
+}
+
+int amlbm_batch_init_all_f32(amlbm_batch* b, const float* rho, const float* uz, const float* ur) {
+  return init_all_host<float>(b, rho, uz, ur);
 }
 
 int amlbm_batch_diagnostics_all(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) {

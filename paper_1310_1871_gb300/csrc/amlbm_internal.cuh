@@ -117,8 +117,12 @@ double a2_norm(double R);
 // f = f^eq(rho, u) for every instance from device arrays holding all
 // instances back to back (site_off: n + 1 prefix offsets); counts the sites
 // whose rho is not positive and finite into *bad (which must start at zero).
+// FP64 or FP32 inputs.
 cudaError_t launch_init_all(int storage, const InstDesc* d_desc, int n, const long long* d_site_off,
                             long long total, const double* rho, const double* uz, const double* ur,
+                            int parity, int* bad, cudaStream_t s);
+cudaError_t launch_init_all(int storage, const InstDesc* d_desc, int n, const long long* d_site_off,
+                            long long total, const float* rho, const float* uz, const float* ur,
                             int parity, int* bad, cudaStream_t s);
 bool tile_supported(int storage, int schedule, int tz, int tr);
 int tile_list(int storage, int schedule, int* tz, int* tr, int cap);

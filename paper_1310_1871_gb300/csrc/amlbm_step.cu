@@ -735,18 +735,19 @@ __global__ void init_kernel(const InstDesc* __restrict__ descs, int inst, const 
 // g belongs to the instance m with site_off[m] <= g < site_off[m + 1].  Sites
 // whose rho is not positive and finite are counted into *bad and the state is
 // written all the same (the caller writes into the buffers of the other parity
-// and discards them when *bad is non-zero).
-template <class S>
+// and discards them when *bad is non-zero).  The inputs are FP64 or FP32 (In);
+// FP32 inputs are widened exactly, so they give the state of the same values in FP64.
+template <class S, class In>
 __global__ void init_all_kernel(const InstDesc* __restrict__ descs, int n_inst,
                                 const long long* __restrict__ site_off, long long total,
-                                const double* rho_in, const double* uz_in, const double* ur_in,
+                                const In* rho_in, const In* uz_in, const In* ur_in,
                                 int parity, int* bad) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   // the inputs first (they may be host memory read over the CPU-GPU link): their
   // latency overlaps the search for the instance
   const double rho = rho_in[g];
-  const double uz = uz_in ? uz_in[g] : 0.0, ur = ur_in ? ur_in[g] : 0.0;
+  const double uz = uz_in ? (double)uz_in[g] : 0.0, ur = ur_in ? (double)ur_in[g] : 0.0;
   int lo = 0, hi = n_inst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -989,24 +990,37 @@ cudaError_t launch_init(int storage, const InstDesc* d, int inst, int Nz, int Nr
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_all(int storage, const InstDesc* d, int n, const long long* site_off,
-                            long long total, const double* rho, const double* uz, const double* ur,
-                            int parity, int* bad, cudaStream_t s) {
+template <class In>
+static cudaError_t launch_init_all_t(int storage, const InstDesc* d, int n, const long long* site_off,
+                                    long long total, const In* rho, const In* uz, const In* ur, int parity,
+                                    int* bad, cudaStream_t s) {
   if (total < 1) return cudaErrorInvalidValue;
   const unsigned nb = (unsigned)((total + 255) / 256);
   switch (storage) {
     case AMLBM_STORE_F64:
-      init_all_kernel<double><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+      init_all_kernel<double, In><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
     case AMLBM_STORE_F32:
-      init_all_kernel<float><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+      init_all_kernel<float, In><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
     case AMLBM_STORE_F16:
-      init_all_kernel<__half><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
+      init_all_kernel<__half, In><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad); break;
     case AMLBM_STORE_BF16:
-      init_all_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad);
+      init_all_kernel<__nv_bfloat16, In><<<nb, 256, 0, s>>>(d, n, site_off, total, rho, uz, ur, parity, bad);
       break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_init_all(int storage, const InstDesc* d, int n, const long long* site_off,
+                            long long total, const double* rho, const double* uz, const double* ur,
+                            int parity, int* bad, cudaStream_t s) {
+  return launch_init_all_t<double>(storage, d, n, site_off, total, rho, uz, ur, parity, bad, s);
+}
+
+cudaError_t launch_init_all(int storage, const InstDesc* d, int n, const long long* site_off,
+                            long long total, const float* rho, const float* uz, const float* ur,
+                            int parity, int* bad, cudaStream_t s) {
+  return launch_init_all_t<float>(storage, d, n, site_off, total, rho, uz, ur, parity, bad, s);
 }
 
 cudaError_t launch_unpack(int storage, const InstDesc* d, int inst, int Nz, int Nr, int parity,

@@ -27,8 +27,15 @@ def test_autotune_times_every_candidate(storage):
                   len(amlbm.tiles(storage, "pair")))
     assert len(cands) == n_expected
     assert all(c["ms_per_step"] > 0 for c in cands)
+    # the choice: candidates in timed order, a later one replacing the best only
+    # when faster by more than 0.5 %
+    best = cands[0]
+    for c in cands[1:]:
+        if c["ms_per_step"] < best["ms_per_step"] * (1 - 0.005):
+            best = c
+    assert (best["schedule"], tuple(best["tile"])) == (sched, tile)
     fastest = min(cands, key=lambda c: c["ms_per_step"])
-    assert (fastest["schedule"], tuple(fastest["tile"])) == (sched, tile)
+    assert best["ms_per_step"] <= fastest["ms_per_step"] / (1 - 0.005)
 
 
 def test_autotuned_batch_equals_fixed_tile(monkeypatch):

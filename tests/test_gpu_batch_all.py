@@ -86,6 +86,49 @@ def test_init_all_rejects_bad_density_and_keeps_state():
     ref.close()
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+def test_init_all_f32_equals_fp64_inputs(storage):
+    """amlbm_batch_init_all_f32: for the FP32-arithmetic forms the state equals that of
+    amlbm_batch_init_all of the FP64 fields (both round to FP32 first); for FP64
+    storage it equals amlbm_batch_init_all of the FP32 values widened to FP64."""
+    a, fields = make(storage)
+    b, _ = make(storage)
+    cols = [np.concatenate([np.ravel(fl[q]) for fl in fields]) for q in range(3)]
+    cols32 = [c.astype(np.float32) for c in cols]
+    a.init_all(*([c.astype(np.float64) for c in cols32] if storage == "f64" else cols))
+    b.init_all(*cols32)
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    a.step(20)
+    b.step(20)
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    b.init_all(cols32[0])  # zero velocity
+    a.init_all(cols32[0].astype(np.float64))
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    a.close()
+    b.close()
+
+
+def test_init_all_f32_rejects_bad_density_and_keeps_state():
+    b, fields = make("f32")
+    cols = [np.concatenate([np.ravel(fl[q]) for fl in fields]).astype(np.float32) for q in range(3)]
+    b.init_all(*cols)
+    b.step(4)
+    before = [b.read_f(k) for k in range(len(fields))]
+    bad = cols[0].copy()
+    bad[100] = np.nan
+    bad[7] = 0.0
+    bad[9] = -2.0
+    with pytest.raises(amlbm.AmlbmError) as e:
+        b.init_all(bad, cols[1], cols[2])
+    assert e.value.code == amlbm.EINVAL and "3 sites" in str(e.value)
+    for k in range(len(fields)):
+        assert np.array_equal(b.read_f(k), before[k]), k
+    b.close()
+
+
 @pytest.mark.parametrize("storage", ["f64", "bf16"])
 def test_diagnostics_all_equals_per_instance(storage):
     b, fields = make(storage)
