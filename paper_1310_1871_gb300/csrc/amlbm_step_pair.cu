@@ -316,6 +316,7 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
       lds2(sRho + fi, rr[0], rr[1]);
       const T inv_r = inv_r_of(T(), j, r0c);
       T* o = sFs + lr * G::SZ + 2 * cp;
+      T h[2][9];
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const T druz = d1(wz + 4 + s, 2);
@@ -323,10 +324,13 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
         const T drur = d1(wr + 4 + s, 2);
         T S_, Hz, Hr;
         site_sources(q, rr[s], wz[4 + s], wr[4 + s], druz, dzur, drur, inv_r, S_, Hz, Hr);
-        T h[9];
-        sources(S_, Hz, Hr, h);
+        sources(S_, Hz, Hr, h[s]);
+      }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o[i * G::nS + s] = o[i * G::nS + s] + h[i];
+      for (int i = 0; i < 9; ++i) {  // both sites' populations of direction i as one pair
+        T a, b;
+        lds2(o + i * G::nS, a, b);
+        sts2(o + i * G::nS, a + h[0][i], b + h[1][i]);
       }
     });
     __syncthreads();
@@ -346,13 +350,21 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
     const int o = j * P + k;
     S qv[2][9];
     C ps[2], vz[2], vr[2];
+    T fn2[2][9];
+    if (!edge) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      T fn[9];
-      if (!edge) {
+      for (int i = 0; i < 9; ++i) {
+        const T* src = c0 + i * G::nS - cr_(i) * G::SZ - cz_(i);
+        if (cz_(i) == 0) {  // the two sources are an aligned pair
+          lds2(src, fn2[0][i], fn2[1][i]);
+        } else {
+          fn2[0][i] = src[0];
+          fn2[1][i] = src[1];
+        }
+      }
+    } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fn[i] = c0[i * G::nS - cr_(i) * G::SZ - cz_(i) + s];
-      } else {
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           int dl = -cr_(i), dc = -cz_(i), ii = i;
@@ -364,9 +376,12 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
             if (noslip) { dc = 0; ii = opp_(i); }
             else { ii = mirror_(i); }
           }
-          fn[i] = c0[ii * G::nS + dl * G::SZ + dc + s];
+          fn2[s][i] = c0[ii * G::nS + dl * G::SZ + dc + s];
         }
-      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T* fn = fn2[s];
       const T rho = moment0(fn);
       ps[s] = psi_of(q, rho).v;
       encode_values<S>(shift, fn, rho, ps[s], inv_rho0c, rho0c, rrefc, D.rounding, (uint32_t)(j * Nz + k + s),
