@@ -603,7 +603,10 @@ def run_reference(args):
         "metric": METRIC, "value": round(val, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(el / max(args.steps, 1) * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference", "config": config(sum(x.Nz * x.Nr for x in inst), "f64"),
+        "data": "synthetic", "impl": "reference",
+        "config": dict(config(sum(x.Nz * x.Nr for x in inst), "f64"),
+                       l2="host caches (the oracle runs on the host cores)",
+                       launch="FP64 oracle, one instance-timestep of the sweep per step, instances in turn"),
         "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": f"one instance-timestep of the 64-drop sweep per step, instances in "
                                    f"turn ({sites} site updates in {el:.1f} s), FP64 oracle, OpenMP "
