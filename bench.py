@@ -56,17 +56,18 @@ def config(sites, storage=STORAGE, tile=None, schedule=None):
             "launch": "every tile of all 64 instances in one launch per kernel per timestep"}
 
 
-def profiled_traffic(kernel_src):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
-    when the kernel source changed since it was captured."""
+def profiled_traffic(kernel_src, kernel):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary, or None
+    when that kernel was not captured or its source changed since."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
-        return None, None
+        return None
     d = json.load(open(p))
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
     if d.get("source_sha256") != sha:
-        return None, d.get("kernel")
-    return d.get("dram_bytes_per_launch"), d.get("kernel")
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return k.get("dram_bytes_per_launch") if k else None
 
 
 def autotune_summary(tuned):
@@ -312,7 +313,7 @@ def run_gpu(args):
             precision = precision_vs_f64(torch)
 
     kname, ksrc = kernel_name(STORAGE, sched, tile)
-    traffic, tkernel = profiled_traffic(ksrc)
+    traffic = profiled_traffic(ksrc, kname)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(seconds=args.cpu_seconds)
@@ -325,7 +326,7 @@ def run_gpu(args):
                                                 autotune=autotune_summary(tuned)),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4),
-                         "traffic": (round(traffic) if traffic and tkernel == kname else None),
+                         "traffic": (round(traffic) if traffic else None),
                          "peak_kind": f"{kind} (HBM copy bandwidth)", "bytes_per_lu": BYTES_PER_LU[STORAGE],
                          "kernel": kname,
                          "limiter": "latency of the per-tile stage chain (barrier and load stalls, 51 % issue), "

@@ -200,7 +200,18 @@ struct Layout {
   long long sumN = 0, sumNz = 0;
 };
 
-Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz, int tr) {
+// Tile of the read-back kernel: a pair batch reads back with the pair schedule's
+// kernel on its step tile, every other batch with the fused read-back (rb_tile()).
+void rb_tiling(int storage, int sched, int tz, int tr, int* rz, int* rr) {
+  if (sched == amlbm::SCHED_PAIR) {
+    *rz = tz;
+    *rr = tr;
+  } else {
+    amlbm::rb_tile(storage, rz, rr);
+  }
+}
+
+Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz, int tr, int sched) {
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes); return at; };
@@ -208,7 +219,7 @@ Layout make_layout(const std::vector<amlbm_instance>& inst, int storage, int tz,
   for (const auto& I : inst) {
     L.ntiles += ((I.Nz + tz - 1) / tz) * ((I.Nr + tr - 1) / tr);
     int rz, rr;
-    amlbm::rb_tile(storage, &rz, &rr);
+    rb_tiling(storage, sched, tz, tr, &rz, &rr);
     L.rb_ntiles += ((I.Nz + rz - 1) / rz) * ((I.Nr + rr - 1) / rr);
     L.maxN = std::max(L.maxN, I.Nz * I.Nr);
     L.maxNz = std::max(L.maxNz, I.Nz);
@@ -359,7 +370,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   if (b->graph_chunk % 2) b->graph_chunk += 1;  // even: a chunk returns to its parity
   b->stream = static_cast<cudaStream_t>(stream);
   if (!b->stream) b->graph_chunk = 0;  // the legacy stream cannot be captured
-  b->L = make_layout(inst, storage, tz, tr);
+  b->L = make_layout(inst, storage, tz, tr, sched);
   if (workspace) {
     if (ws_bytes < b->L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign)) {
       delete b;
@@ -406,7 +417,7 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
     d.tiles_r = (I.Nr + tr - 1) / tr;
     d.tile_base = (int)tiles.size();
     int rz, rr;
-    amlbm::rb_tile(storage, &rz, &rr);
+    rb_tiling(storage, sched, tz, tr, &rz, &rr);
     d.rb_tiles_z = (I.Nz + rz - 1) / rz;
     d.rb_tiles_r = (I.Nr + rr - 1) / rr;
     d.rb_tile_base = (int)rb_tiles.size();
@@ -474,6 +485,9 @@ int batch_build(const std::vector<amlbm_instance>& inst, const amlbm_tune* tune,
   // the allocation-free diagnostics' scratch: looked up now, in a call that
   // allocates anyway (its failure surfaces at that entry point, not here)
   amlbm::noalloc_prepare(storage);
+  // the pair read-back's code, loaded now for the same reason (its first use
+  // may be an allocation-free diagnostics call)
+  if (sched == amlbm::SCHED_PAIR) amlbm::readback_pair_preload(storage, tz, tr);
   *out = b;
   return AMLBM_OK;
 }
@@ -530,13 +544,20 @@ int set_inlet(amlbm_batch* b, int k, const double* uz, const double* ur) {
   return AMLBM_OK;
 }
 
+// rho and u of nt tiles of the read-back list from toff into the read-back planes
+cudaError_t launch_readback(amlbm_batch* b, int nt, int toff) {
+  if (b->sched == amlbm::SCHED_PAIR)
+    return amlbm::launch_readback_pair(b->storage, b->tz, b->tr, b->d_desc, b->d_rb_tiles, nt, toff, b->parity,
+                                       b->stream);
+  int rz, rr;
+  amlbm::rb_tile(b->storage, &rz, &rr);
+  return amlbm::launch_macro(b->storage, rz, rr, b->d_desc, b->d_rb_tiles, nt, toff, b->parity, b->stream);
+}
+
 int macro_for(amlbm_batch* b, int k) {
   const InstDesc& d = b->desc[k];
   const int nt = d.rb_tiles_z * d.rb_tiles_r;
-  int rz, rr;
-  amlbm::rb_tile(b->storage, &rz, &rr);
-  const cudaError_t e = amlbm::launch_macro(b->storage, rz, rr, b->d_desc, b->d_rb_tiles, nt,
-                                            d.rb_tile_base, b->parity, b->stream);
+  const cudaError_t e = launch_readback(b, nt, d.rb_tile_base);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
   return AMLBM_OK;
 }
@@ -672,10 +693,7 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
     if (!b->pin) AMLBM_CK(cudaStreamSynchronize(b->stream));  // the pageable source goes out of scope
     b->last_jobs = jobs;
   }
-  int rz, rr;
-  amlbm::rb_tile(b->storage, &rz, &rr);
-  cudaError_t e = amlbm::launch_macro(b->storage, rz, rr, b->d_desc, b->d_rb_tiles, b->L.rb_ntiles, 0,
-                                      b->parity, b->stream);
+  cudaError_t e = launch_readback(b, b->L.rb_ntiles, 0);
   if (e != cudaSuccess) return fail(AMLBM_ECUDA, std::string("macro kernel: ") + cudaGetErrorString(e));
   double* part = reinterpret_cast<double*>(b->arena + b->L.diag_part);
   double* cols = reinterpret_cast<double*>(b->arena + b->L.diag_cols);
@@ -749,7 +767,8 @@ size_t amlbm_batch_workspace_bytes(int n, const amlbm_instance* inst) {
   for (int sc = amlbm::SCHED_FUSED; sc <= amlbm::SCHED_PAIR; ++sc) {
     int tz[32], tr[32];
     const int nt = std::min(32, amlbm::tile_list(v[0].bc.storage, sc, tz, tr, 32));
-    for (int c = 0; c < nt; ++c) need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c]).total);
+    for (int c = 0; c < nt; ++c)
+      need = std::max(need, make_layout(v, v[0].bc.storage, tz[c], tr[c], sc).total);
   }
   return need;
 }

@@ -132,6 +132,12 @@ bool pair_tile_supported(int storage, int tz, int tr);
 int pair_tile_list(int storage, int* tz, int* tr, int cap);
 cudaError_t launch_step_pair(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
                              int ntiles, int parity, cudaStream_t s, int* ctr);
+// The read-back (rho, u into the read-back planes) of a pair batch, whose
+// read-back list is tiled like its step: nt tiles from toff.  And the loading of
+// that kernel's code on the current device (launches nothing).
+cudaError_t launch_readback_pair(int storage, int tz, int tr, const InstDesc* d_desc, const int* d_tile_inst,
+                                 int nt, int toff, int parity, cudaStream_t s);
+cudaError_t readback_pair_preload(int storage, int tz, int tr);
 
 // Access to a lattice context for entry points defined outside the ABI file
 // (amlbm_abi.cu implements these).

@@ -83,6 +83,99 @@ __device__ __forceinline__ void for_pairs(F&& body) {
   }
 }
 
+// Stage 0 of a tile: psi on tile + (8, 7); rows mirrored about the axis and the
+// wall.  All of a thread's loads are issued before its first store, so that
+// their latencies overlap.
+template <class C, class T, int BZ, int BR, int NTH>
+__device__ __forceinline__ void stage_psi(T* sPsi, const C* __restrict__ psin, int j0, int k0, int Nz, int Nr,
+                                          int P, bool tiny) {
+  using G = PGeo<T, BZ, BR>;
+  constexpr int PP = G::PZ / 2, TOT = G::PR * PP, NB = (TOT + NTH - 1) / NTH;
+  C va[NB], vb[NB];
+#pragma unroll
+  for (int n = 0; n < NB; ++n) {
+    const int t = threadIdx.x + n * NTH;
+    if (t < TOT) {
+      const int lr = t / PP, cp = t - lr * PP;
+      const int jj = reflect_row(j0 - 7 + lr, Nr);
+      const int kk = wrap_col(k0 - 8 + 2 * cp, Nz, tiny);
+      ld2<C>(psin + jj * P + kk, va[n], vb[n]);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NB; ++n) {
+    const int t = threadIdx.x + n * NTH;
+    if (t < TOT) sts2(sPsi + 2 * t, T{va[n]}, T{vb[n]});  // PZ = 2 PP: row-major pairs
+  }
+}
+
+// Stage 1 of a tile: isotropic d_r psi and 1D d_r psi on tile + (6, 5).
+template <class T, int BZ, int BR, int NTH>
+__device__ __forceinline__ void stage_dr(const T* sPsi, T* sDr, T* sD1) {
+  using G = PGeo<T, BZ, BR>;
+  for_pairs<NTH, G::DR, G::DZ / 2>([&](int lr, int cp) {
+    // psi rows -2..2 around the pair, columns -2..3 (row 0 is not a tap)
+    T w[5 * 6];
+    const T* p = sPsi + (lr + 2) * G::PZ + 2 * cp;  // column -2 of the window at row 0
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+      if (r != 2) load_row<T, 3>(p + (r - 2) * G::PZ, w + 6 * r);
+    T dr[2], d1r[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      dr[s] = iso_r(w + 12 + 2 + s, 6);
+      d1r[s] = d1(w + 12 + 2 + s, 6);
+    }
+    sts2(sDr + lr * G::DZ + 2 * cp, dr[0], dr[1]);
+    sts2(sD1 + lr * G::DZ + 2 * cp, d1r[0], d1r[1]);
+  });
+}
+
+// The force without its body-force term (Shan-Chen sums, d_rr psi, d_zr psi) of
+// the pair at (lr, cp) of the force region (tile + (4, 3)), row j of the
+// lattice; psi of the two sites in ps.
+template <class T, int BZ, int BR>
+__device__ __forceinline__ void force_pair(const T* sPsi, const T* sDr, const T* sD1, const Par<T>& q, bool ax,
+                                           T inv_r, int lr, int cp, T* Fz2, T* Fr2, T* ps) {
+  using G = PGeo<T, BZ, BR>;
+  // psi rows -1..1, columns -2..3 around the pair
+  T wp[3 * 6];
+  const T* p = sPsi + (lr + 4) * G::PZ + 2 * cp + 2;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) load_row<T, 3>(p + (r - 1) * G::PZ, wp + 6 * r);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T psi = wp[6 + 2 + s];
+    T sz, sr;
+    sc_sums(wp + 6 + 2 + s, 6, sz, sr);
+    T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
+    if (ax) {
+      // d_r psi rows -2..2 (columns -1..2 on rows -1, 1; -2..3 on rows -2, 2; 0..1
+      // on row 0) and 1D d_r psi row 0 (columns -2..3)
+      const T* pd = sDr + (lr + 2) * G::DZ + 2 * cp + 2 + s;
+      T w[5 * 5];
+#pragma unroll
+      for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          const bool tap = (r == 2 && c == 2) || ((r == 1 || r == 3) && c >= 1 && c <= 3) ||
+                           ((r == 0 || r == 4) && (c == 0 || c == 2 || c == 4));
+          if (tap) w[5 * r + c] = pd[(r - 2) * G::DZ + (c - 2)];
+        }
+      dr0 = w[12];
+      Drr = iso_r(w + 12, 5);
+      const T* pe = sD1 + (lr + 2) * G::DZ + 2 * cp + 2 + s;
+      T e[5];
+#pragma unroll
+      for (int m = -2; m <= 2; ++m) e[m + 2] = m ? pe[m] : lit<T>(0.0);
+      Dzr = d1(e + 2, 1);
+    }
+    forces_partial(q, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz2[s], Fr2[s]);
+  }
+  ps[0] = wp[8];
+  ps[1] = wp[9];
+}
+
 template <class S, class T, int BZ, int BR>
 __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst,
                                           int tile, int parity, uint32_t step) {
@@ -117,48 +210,13 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   const bool guo = D.forcing == AMLBM_FORCE_GUO;
   const bool tiny = Nz < BZ + 16;  // region columns may wrap more than once
 
-  // Stage 0: psi on tile + (8, 7); rows mirrored about the axis and the wall.
-  // All of a thread's loads are issued before its first store, so that their
-  // latencies overlap.
-  {
-    constexpr int PP = G::PZ / 2, TOT = G::PR * PP, NB = (TOT + NTH - 1) / NTH;
-    C va[NB], vb[NB];
-#pragma unroll
-    for (int n = 0; n < NB; ++n) {
-      const int t = threadIdx.x + n * NTH;
-      if (t < TOT) {
-        const int lr = t / PP, cp = t - lr * PP;
-        const int jj = reflect_row(j0 - 7 + lr, Nr);
-        const int kk = wrap_col(k0 - 8 + 2 * cp, Nz, tiny);
-        ld2<C>(psin + jj * P + kk, va[n], vb[n]);
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < NB; ++n) {
-      const int t = threadIdx.x + n * NTH;
-      if (t < TOT) sts2(sPsi + 2 * t, T{va[n]}, T{vb[n]});  // PZ = 2 PP: row-major pairs
-    }
-  }
+  // Stage 0: psi on tile + (8, 7)
+  stage_psi<C, T, BZ, BR, NTH>(sPsi, psin, j0, k0, Nz, Nr, P, tiny);
   __syncthreads();
 
-  // Stage 1: isotropic d_r psi and 1D d_r psi on tile + (6, 5).
+  // Stage 1: isotropic d_r psi and 1D d_r psi on tile + (6, 5)
   if (ax) {
-    for_pairs<NTH, G::DR, G::DZ / 2>([&](int lr, int cp) {
-      // psi rows -2..2 around the pair, columns -2..3 (row 0 is not a tap)
-      T w[5 * 6];
-      const T* p = sPsi + (lr + 2) * G::PZ + 2 * cp;  // column -2 of the window at row 0
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-        if (r != 2) load_row<T, 3>(p + (r - 2) * G::PZ, w + 6 * r);
-      T dr[2], d1r[2];
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        dr[s] = iso_r(w + 12 + 2 + s, 6);
-        d1r[s] = d1(w + 12 + 2 + s, 6);
-      }
-      sts2(sDr + lr * G::DZ + 2 * cp, dr[0], dr[1]);
-      sts2(sD1 + lr * G::DZ + 2 * cp, d1r[0], d1r[1]);
-    });
+    stage_dr<T, BZ, BR, NTH>(sPsi, sDr, sD1);
     __syncthreads();
   }
 
@@ -167,46 +225,12 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   for_pairs<NTH, G::FR, G::FZ / 2>([&](int lr, int cp) {
     const int j = j0 - 3 + lr;
     if (j < 0 || j >= Nr) return;
-    // psi rows -1..1, columns -2..3 around the pair
-    T wp[3 * 6];
-    const T* p = sPsi + (lr + 4) * G::PZ + 2 * cp + 2;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) load_row<T, 3>(p + (r - 1) * G::PZ, wp + 6 * r);
-    const T inv_r = inv_r_of(T(), j, r0c);
-    T Fz2[2], Fr2[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const T psi = wp[6 + 2 + s];
-      T sz, sr;
-      sc_sums(wp + 6 + 2 + s, 6, sz, sr);
-      T dr0 = lit<T>(0.0), Drr = lit<T>(0.0), Dzr = lit<T>(0.0);
-      if (ax) {
-        // d_r psi rows -2..2 (columns -1..2 on rows -1, 1; -2..3 on rows -2, 2; 0..1
-        // on row 0) and 1D d_r psi row 0 (columns -2..3)
-        const T* pd = sDr + (lr + 2) * G::DZ + 2 * cp + 2 + s;
-        T w[5 * 5];
-#pragma unroll
-        for (int r = 0; r < 5; ++r)
-#pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            const bool tap = (r == 2 && c == 2) || ((r == 1 || r == 3) && c >= 1 && c <= 3) ||
-                             ((r == 0 || r == 4) && (c == 0 || c == 2 || c == 4));
-            if (tap) w[5 * r + c] = pd[(r - 2) * G::DZ + (c - 2)];
-          }
-        dr0 = w[12];
-        Drr = iso_r(w + 12, 5);
-        const T* pe = sD1 + (lr + 2) * G::DZ + 2 * cp + 2 + s;
-        T e[5];
-#pragma unroll
-        for (int m = -2; m <= 2; ++m) e[m + 2] = m ? pe[m] : lit<T>(0.0);
-        Dzr = d1(e + 2, 1);
-      }
-      forces_partial(q, psi, sz, sr, ax, dr0, Drr, Dzr, inv_r, Fz2[s], Fr2[s]);
-    }
+    T Fz2[2], Fr2[2], ps[2];
+    force_pair<T, BZ, BR>(sPsi, sDr, sD1, q, ax, inv_r_of(T(), j, r0c), lr, cp, Fz2, Fr2, ps);
     const int fi = lr * G::FZ + 2 * cp;
     sts2(sFz + fi, Fz2[0], Fz2[1]);
     sts2(sFr + fi, Fr2[0], Fr2[1]);
-    sts2(sPs + fi, wp[8], wp[9]);
+    sts2(sPs + fi, ps[0], ps[1]);
   });
   __syncthreads();
 
@@ -397,6 +421,87 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
   });
 }
 
+// The read-back of the pair schedule: rho, u_z and u_r of the current state on
+// every site of a tile, in the compute type, into the instance's [Nr][Nz]
+// read-back planes.  Stages 0 and 1 of the step, then the force, moments and
+// velocity of stage 2 at the tile's own sites only (nothing downstream needs
+// them on the halo): the step's operations on the step's values, so the
+// results equal those of the fused schedule's read-back bit for bit.  One CTA
+// per tile of the read-back list (which, for a pair batch, is tiled like the step).
+template <class T, int BZ, int BR>
+struct RGeo {
+  using G = PGeo<T, BZ, BR>;
+  static constexpr size_t bytes = sizeof(T) * ((size_t)G::nP + 2 * (size_t)G::nD);
+};
+
+template <class S, class T, int BZ, int BR>
+__global__ void __launch_bounds__(Threads<T, BZ, BR>::value, Threads<T, BZ, BR>::min_blocks) pair_readback(
+    const InstDesc* __restrict__ descs, const int* __restrict__ tile_inst, int toff, int parity) {
+  using C = typename Store<S>::C;
+  using G = PGeo<T, BZ, BR>;
+  constexpr int NTH = Threads<T, BZ, BR>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sPsi = reinterpret_cast<T*>(smem_raw);
+  T* sDr = sPsi + G::nP;
+  T* sD1 = sDr + G::nD;
+
+  const int tile = blockIdx.x + toff;
+  const InstDesc& D = descs[tile_inst[tile]];
+  const int Nz = D.Nz, Nr = D.Nr, P = D.P;
+  const int l = tile - D.rb_tile_base;
+  const int k0 = (l % D.rb_tiles_z) * BZ, j0 = (l / D.rb_tiles_z) * BR;
+  const int plane = P * Nr;
+  const S* __restrict__ fin = static_cast<const S*>(D.f[parity]);
+  const C* __restrict__ psin = static_cast<const C*>(D.psi[parity]);
+  const bool ax = D.axisym != 0;
+  const int shift = D.shift;
+  const Par<T> q = par_of<T>(D);
+  const C rho0c = kc(D, K_RHO0, C()), rrefc = kc(D, K_RREF, C()), inv_rho0c = kc(D, K_INVRHO0, C());
+  const C r0c = kc(D, K_R0, C());
+  const bool tiny = Nz < BZ + 16;
+
+  stage_psi<C, T, BZ, BR, NTH>(sPsi, psin, j0, k0, Nz, Nr, P, tiny);
+  __syncthreads();
+  if (ax) {
+    stage_dr<T, BZ, BR, NTH>(sPsi, sDr, sD1);
+    __syncthreads();
+  }
+  C* rho_out = static_cast<C*>(D.rho_out);
+  C* uz_out = static_cast<C*>(D.uz_out);
+  C* ur_out = static_cast<C*>(D.ur_out);
+  for_pairs<NTH, BR, BZ / 2>([&](int lr, int cp) {
+    const int j = j0 + lr, k = k0 + 2 * cp;
+    if (j >= Nr || k >= Nz) return;
+    const int so = j * P + k;
+    S qa[9], qb[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) ld2<S>(fin + i * plane + so, qa[i], qb[i]);
+    C va = C(0), vb = C(0), wa = C(0), wb = C(0);
+    if (shift == 3) {
+      ld2<C>(psin + plane + so, va, vb);
+      ld2<C>(psin + 2 * plane + so, wa, wb);
+    }
+    T fz[2], fr[2], ps[2];
+    force_pair<T, BZ, BR>(sPsi, sDr, sD1, q, ax, inv_r_of(T(), j, r0c), lr + 3, cp + 2, fz, fr, ps);
+    C rho2[2], uz2[2], ur2[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      T f[9];
+      decode_values<S>(shift, s ? qb : qa, ps[s].v, s ? vb : va, s ? wb : wa, inv_rho0c, rho0c, rrefc, f);
+      const T rho = moment0(f), jz = moment_z(f), jr = moment_r(f);
+      const T Fz = fma(rho, q.gz, fz[s]), Fr = fr[s];
+      const T inv_rho = rcp(rho);
+      rho2[s] = rho.v;
+      uz2[s] = (fma(Fz, lit<T>(0.5), jz) * inv_rho).v;
+      ur2[s] = (fma(Fr, lit<T>(0.5), jr) * inv_rho).v;
+    }
+    const int o = j * Nz + k;  // Nz and k are even: an aligned pair
+    st2<C>(rho_out + o, rho2[0], rho2[1]);
+    st2<C>(uz_out + o, uz2[0], uz2[1]);
+    st2<C>(ur_out + o, ur2[0], ur2[1]);
+  });
+}
+
 // The timestep as a persistent grid: CTAs take tiles from a counter until none
 // is left (ctr as for the fused schedule: this step's tile counter and step
 // number at [parity] and [2 + parity], the next step's reset here).
@@ -454,6 +559,15 @@ cudaError_t launch_pair_t(const InstDesc* d, const int* ti, int ntiles, int pari
   return cudaGetLastError();
 }
 
+template <class S, int BZ, int BR>
+cudaError_t launch_readback_t(const InstDesc* d, const int* ti, int nt, int toff, int parity, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  constexpr size_t smem = RGeo<T, BZ, BR>::bytes;
+  static_assert(smem <= 48 * 1024, "read-back tiles fit the default shared-memory limit");
+  pair_readback<S, T, BZ, BR><<<nt, Threads<T, BZ, BR>::value, smem, s>>>(d, ti, toff, parity);
+  return cudaGetLastError();
+}
+
 struct PairTile { int storage, tz, tr; };
 #define AMLBM_PAIR_TILES(ST) {ST, 40, 24}, {ST, 48, 20}, {ST, 32, 16}, {ST, 48, 16}, {ST, 24, 16}, \
                              {ST, 64, 16}, {ST, 32, 32}, {ST, 48, 22}
@@ -463,12 +577,20 @@ constexpr PairTile kPairTiles[] = {
 };
 #undef AMLBM_PAIR_TILES
 
+// kind 0: the timestep (ctr: its counters); 1: the read-back of nt tiles from
+// toff; 2: load the read-back kernel's code (nothing is launched)
 template <class S>
-cudaError_t pair_dispatch(int tz, int tr, const InstDesc* d, const int* ti, int nt, int par, cudaStream_t s,
-                          int* ctr) {
-  if (nt <= 0) return cudaSuccess;
-#define AMLBM_PT(TZ, TR) \
-  if (tz == TZ && tr == TR) return launch_pair_t<S, TZ, TR>(d, ti, nt, par, s, ctr);
+cudaError_t pair_dispatch(int kind, int tz, int tr, const InstDesc* d, const int* ti, int nt, int toff, int par,
+                          cudaStream_t s, int* ctr) {
+  using T = typename Store<S>::T;
+  if (kind != 2 && nt <= 0) return cudaSuccess;
+#define AMLBM_PT(TZ, TR)                                                             \
+  if (tz == TZ && tr == TR) {                                                        \
+    if (kind == 0) return launch_pair_t<S, TZ, TR>(d, ti, nt, par, s, ctr);          \
+    if (kind == 1) return launch_readback_t<S, TZ, TR>(d, ti, nt, toff, par, s);     \
+    cudaFuncAttributes a;                                                            \
+    return cudaFuncGetAttributes(&a, pair_readback<S, T, TZ, TR>);                   \
+  }
   if constexpr (std::is_same<S, double>::value) {
     AMLBM_PT(32, 8)
     AMLBM_PT(28, 8)
@@ -504,15 +626,29 @@ int pair_tile_list(int storage, int* tz, int* tr, int cap) {
   return n;
 }
 
-cudaError_t launch_step_pair(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt, int parity,
-                             cudaStream_t s, int* ctr) {
+static cudaError_t pair_kind(int kind, int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt,
+                             int toff, int parity, cudaStream_t s, int* ctr) {
   switch (storage) {
-    case AMLBM_STORE_F64: return pair_dispatch<double>(tz, tr, d, ti, nt, parity, s, ctr);
-    case AMLBM_STORE_F32: return pair_dispatch<float>(tz, tr, d, ti, nt, parity, s, ctr);
-    case AMLBM_STORE_F16: return pair_dispatch<__half>(tz, tr, d, ti, nt, parity, s, ctr);
-    case AMLBM_STORE_BF16: return pair_dispatch<__nv_bfloat16>(tz, tr, d, ti, nt, parity, s, ctr);
+    case AMLBM_STORE_F64: return pair_dispatch<double>(kind, tz, tr, d, ti, nt, toff, parity, s, ctr);
+    case AMLBM_STORE_F32: return pair_dispatch<float>(kind, tz, tr, d, ti, nt, toff, parity, s, ctr);
+    case AMLBM_STORE_F16: return pair_dispatch<__half>(kind, tz, tr, d, ti, nt, toff, parity, s, ctr);
+    case AMLBM_STORE_BF16: return pair_dispatch<__nv_bfloat16>(kind, tz, tr, d, ti, nt, toff, parity, s, ctr);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_step_pair(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt, int parity,
+                             cudaStream_t s, int* ctr) {
+  return pair_kind(0, storage, tz, tr, d, ti, nt, 0, parity, s, ctr);
+}
+
+cudaError_t launch_readback_pair(int storage, int tz, int tr, const InstDesc* d, const int* ti, int nt, int toff,
+                                 int parity, cudaStream_t s) {
+  return pair_kind(1, storage, tz, tr, d, ti, nt, toff, parity, s, nullptr);
+}
+
+cudaError_t readback_pair_preload(int storage, int tz, int tr) {
+  return pair_kind(2, storage, tz, tr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr);
 }
 
 }  // namespace amlbm
