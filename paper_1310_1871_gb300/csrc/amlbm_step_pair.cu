@@ -22,6 +22,10 @@
 // an outer wall that reflects (free-slip) or bounces back (no-slip), the source
 // at the departure site, either forcing.  Pairs never straddle the periodic
 // seam because Nz and every tile origin are even.
+//
+// The file also holds the schedule's read-back (rho and u of the current state,
+// the input of the diagnostics): stages 0 and 1 as above, then the force,
+// moments and u at the tile's own sites.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
