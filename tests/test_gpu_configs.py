@@ -30,7 +30,7 @@ if not torch.cuda.is_available():
 
 from paper_1310_1871_gb300 import amlbm  # noqa: E402
 
-# The benchmark spec tolerance on the period and the pinch-off time of the FP32 form.
+# The accuracy target on the oscillation period and the pinch-off time of the FP32 form (0.5 %).
 PHYS_TOL = 5e-3
 
 
