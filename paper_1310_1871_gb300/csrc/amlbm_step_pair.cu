@@ -292,36 +292,29 @@ __device__ __forceinline__ void pair_tile(const InstDesc* __restrict__ descs, co
     sts2(sRho + fi, rho2[0], rho2[1]);
     sts2(sUz + fi, uz2[0], uz2[1]);
     sts2(sUr + fi, ur2[0], ur2[1]);
+    // Ghost rows of u (depth 2) for the sources' gradients, written by the thread
+    // that computed the row they mirror: rows -1, -2 mirror rows 0, 1 about the
+    // axis (u_z even, u_r odd); rows Nr, Nr + 1 mirror rows Nr - 1, Nr - 2 about
+    // the outer wall (u_r odd, u_z even for free-slip and odd for no-slip).
+    if (ax) {
+      if (j <= 1) {
+        const int lg = (-1 - j) - (j0 - 3);
+        if (lg >= 0) {
+          sts2(sUz + lg * G::FZ + 2 * cp, uz2[0], uz2[1]);
+          sts2(sUr + lg * G::FZ + 2 * cp, -ur2[0], -ur2[1]);
+        }
+      }
+      if (j >= Nr - 2) {
+        const int lg = (2 * Nr - 1 - j) - (j0 - 3);
+        if (lg < G::FR) {
+          const bool flip_z = D.wall == AMLBM_WALL_NOSLIP;
+          sts2(sUz + lg * G::FZ + 2 * cp, flip_z ? -uz2[0] : uz2[0], flip_z ? -uz2[1] : uz2[1]);
+          sts2(sUr + lg * G::FZ + 2 * cp, -ur2[0], -ur2[1]);
+        }
+      }
+    }
   });
   __syncthreads();
-
-  // Ghost rows of u (depth 2) on tiles that touch row 0 or row Nr - 1: u_z even
-  // and u_r odd about the axis; about the outer wall u_r odd and u_z even
-  // (free-slip) or odd (no-slip).
-  if (ax && (j0 < 3 || j0 + BR + 3 > Nr)) {
-    const bool noslip = D.wall == AMLBM_WALL_NOSLIP;
-    for_pairs<NTH, G::FR, G::FZ / 2>([&](int lr, int cp) {
-      const int j = j0 - 3 + lr;
-      int m;
-      bool flip_z;
-      if (j == -1 || j == -2) {
-        m = -1 - j;
-        flip_z = false;
-      } else if (j == Nr || j == Nr + 1) {
-        m = 2 * Nr - 1 - j;
-        flip_z = noslip;
-      } else {
-        return;
-      }
-      const int src = (m - (j0 - 3)) * G::FZ + 2 * cp, dst = lr * G::FZ + 2 * cp;
-      T a, b;
-      lds2(sUz + src, a, b);
-      sts2(sUz + dst, flip_z ? -a : a, flip_z ? -b : b);
-      lds2(sUr + src, a, b);
-      sts2(sUr + dst, -a, -b);
-    });
-    __syncthreads();
-  }
 
   // Stage 3 (tile + (2, 1)): velocity gradients and the sources of App. A,
   // added to the collided populations.
