@@ -668,7 +668,7 @@ int diag_all_host(amlbm_batch* b, const amlbm_diag_params* dp, amlbm_diag* out) 
       return fail(AMLBM_EINVAL, "diag params of instance " + std::to_string(k) + ": need R > 0, rho_l != rho_v");
     amlbm::DiagJob& J = jobs[k];
     J.zc = p.zc; J.R = p.R; J.rho_l = p.rho_l; J.rho_v = p.rho_v;
-    J.a2norm = amlbm::a2_norm(p.R);
+    amlbm::diag_job_constants(J);
     J.inst = k;
     J.blk0 = blk;
     J.nblk = amlbm::diag_blocks(d.Nz, d.Nr);

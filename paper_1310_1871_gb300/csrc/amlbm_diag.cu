@@ -101,7 +101,7 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
                               double* cols) {
   const int Nz = D.Nz, Nr = D.Nr, N = Nz * Nr;
   const C two_pi = C(2.0 * 3.14159265358979323846);
-  const C inv_dl = C(1.0 / (J.rho_l - J.rho_v)), rho_v = C(J.rho_v), zc = C(J.zc);
+  const C inv_dl = C(J.inv_dl), rho_v = C(J.rho_v), zc = C(J.zc);
   const C r0 = sizeof(C) == 8 ? C(D.k64[K_R0]) : C(D.k32[K_R0]);
   const C* __restrict__ rho_o = static_cast<const C*>(D.rho_out);
   const C* __restrict__ uz_o = static_cast<const C*>(D.uz_out);
@@ -110,8 +110,12 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   // and the final pass reduce those per-thread sums in FP64: the FP32 forms then
   // need one FP64 conversion and addition per sum and thread, not per site.
   C tacc[NSUM] = {C(0), C(0), C(0), C(0), C(0), C(0), C(0), C(0)};
-  for (int n = blk * DIAG_NT + threadIdx.x; n < N; n += J.nblk * DIAG_NT) {
-    const int j = n / Nz, k = n - j * Nz;
+  // sites n = blk * NT + tid + m * S, S = nblk * NT; (j, k) advanced without a
+  // division per site
+  const int S = J.nblk * DIAG_NT, sj = S / Nz, sk = S - sj * Nz;
+  const int n0 = blk * DIAG_NT + threadIdx.x;
+  int j = n0 / Nz, k = n0 - (n0 / Nz) * Nz;
+  for (int n = n0; n < N; n += S) {
     const C r = C(j) + r0, rho = rho_o[n], uz = uz_o[n], ur = ur_o[n];
     const C u2 = uz * uz + ur * ur, w = two_pi * r * rho;
     tacc[0] += rho;
@@ -124,6 +128,12 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
     const bool bad = !(rho > C(0)) || !isfinite(rho) || !isfinite(u2);
     tacc[6] += bad ? C(1) : C(0);
     tacc[7] = fmax(tacc[7], bad ? C(0) : u2);
+    k += sk;
+    j += sj;
+    if (k >= Nz) {
+      k -= Nz;
+      ++j;
+    }
   }
   // The warp's sums (128 sites) pairwise in C too, then FP64 across warps and
   // blocks: the FP32 forms convert 8 values per warp instead of per thread.
@@ -153,44 +163,35 @@ __device__ void partial_block(const InstDesc& D, const DiagJob& J, int blk, doub
   }
 }
 
-// One block: the job's partial sums and column radii reduced into out[16].
+// One warp: the job's partial sums and column radii reduced into out[16].  Lane
+// q + 8 s (q < 8, s < 4) folds quantity q of the blocks b = s (mod 4) in FP64,
+// two shuffles join the four, and every lane takes the minimum over a share of
+// the columns: short FP64 chains and no block barrier (GB300's FP64 operations
+// are slow, so the pass is bound by their latency).
+constexpr int FINAL_NT = 32;
+
 template <class C>
-__device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, const double* partials,
-                            const double* cols, double* out) {
+__device__ void final_warp(const InstDesc& D, const DiagJob& J, int parity, const double* partials,
+                           const double* cols, double* out) {
   const int Nz = D.Nz, Nr = D.Nr;
-  double acc[NSUM + 1] = {0, 0, 0, 0, 0, 0, 0, 0, 1e300};
-  for (int b = threadIdx.x; b < J.nblk; b += DIAG_NT) {
-    const double* p = partials + (size_t)(J.blk0 + b) * NSUM;
-#pragma unroll
-    for (int q = 0; q < NSUM - 1; ++q) acc[q] += p[q];
-    acc[NSUM - 1] = fmax(acc[NSUM - 1], p[NSUM - 1]);
+  const int lane = threadIdx.x & 31, q = lane & (NSUM - 1), sub = lane >> 3;
+  double acc = 0.0;
+  for (int b = sub; b < J.nblk; b += 4) {
+    const double v = partials[(size_t)(J.blk0 + b) * NSUM + q];
+    acc = q == NSUM - 1 ? fmax(acc, v) : acc + v;
   }
-  for (int k = threadIdx.x; k < Nz; k += DIAG_NT) acc[NSUM] = fmin(acc[NSUM], cols[J.col0 + k]);
-  __shared__ double red[DIAG_WARPS][NSUM + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < NSUM - 1; ++q) acc[q] = warp_sum(acc[q]);
-  acc[NSUM - 1] = warp_max(acc[NSUM - 1]);
-  acc[NSUM] = warp_min(acc[NSUM]);
+  for (int o = 8; o < 32; o <<= 1) {
+    const double v = __shfl_xor_sync(0xffffffffu, acc, o);
+    acc = q == NSUM - 1 ? fmax(acc, v) : acc + v;
+  }
+  double cmin = 1e300;
+  for (int k = lane; k < Nz; k += 32) cmin = fmin(cmin, cols[J.col0 + k]);
+  cmin = warp_min(cmin);
+  double t[NSUM];
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) t[i] = __shfl_sync(0xffffffffu, acc, i);
   if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q <= NSUM; ++q) red[warp][q] = acc[q];
-  }
-  __syncthreads();
-  // one thread per quantity across the warps (short FP64 chains), then thread 0
-  __shared__ double tot[NSUM + 1];
-  if (threadIdx.x <= NSUM) {
-    const int q = threadIdx.x;
-    double v = red[0][q];
-    for (int w = 1; w < DIAG_WARPS; ++w)
-      v = q < NSUM - 1 ? v + red[w][q] : (q == NSUM - 1 ? fmax(v, red[w][q]) : fmin(v, red[w][q]));
-    tot[q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[NSUM + 1];
-#pragma unroll
-    for (int q = 0; q <= NSUM; ++q) t[q] = tot[q];
     out[0] = t[0];
     out[1] = t[1];
     out[2] = t[2];
@@ -201,7 +202,7 @@ __device__ void final_block(const InstDesc& D, const DiagJob& J, int parity, con
     kc %= Nz;
     if (kc < 0) kc += Nz;
     out[6] = cols[J.col0 + kc];
-    out[7] = t[NSUM];
+    out[7] = cmin;
     const C* psi = static_cast<const C*>(D.psi[parity]);
     const double G = D.G;
     auto pres = [&](int k, int j) {
@@ -226,10 +227,10 @@ __global__ void __launch_bounds__(DIAG_NT) diag_partial_one(const InstDesc* __re
 }
 
 template <class C>
-__global__ void __launch_bounds__(DIAG_NT) diag_final_one(const InstDesc* __restrict__ descs, DiagJob J,
-                                                          int parity, const double* partials,
-                                                          const double* cols, double* out) {
-  final_block<C>(descs[J.inst], J, parity, partials, cols, out);
+__global__ void __launch_bounds__(FINAL_NT) diag_final_one(const InstDesc* __restrict__ descs, DiagJob J,
+                                                           int parity, const double* partials,
+                                                           const double* cols, double* out) {
+  final_warp<C>(descs[J.inst], J, parity, partials, cols, out);
 }
 
 // Every job of a batch: block b belongs to job blkjob[b] (the host's table of
@@ -244,17 +245,22 @@ __global__ void __launch_bounds__(DIAG_NT) diag_partial_all(const InstDesc* __re
 }
 
 template <class C>
-__global__ void __launch_bounds__(DIAG_NT) diag_final_all(const InstDesc* __restrict__ descs,
-                                                          const DiagJob* __restrict__ jobs, int parity,
-                                                          const double* partials, const double* cols,
-                                                          double* out) {
+__global__ void __launch_bounds__(FINAL_NT) diag_final_all(const InstDesc* __restrict__ descs,
+                                                           const DiagJob* __restrict__ jobs, int parity,
+                                                           const double* partials, const double* cols,
+                                                           double* out) {
   const DiagJob J = jobs[blockIdx.x];
-  final_block<C>(descs[J.inst], J, parity, partials, cols, out + (size_t)16 * blockIdx.x);
+  final_warp<C>(descs[J.inst], J, parity, partials, cols, out + (size_t)16 * blockIdx.x);
 }
 
 }  // namespace
 
 double a2_norm(double R) { return 5.0 / (4.0 * 3.14159265358979323846 * std::pow(R, 5.0)); }
+
+void diag_job_constants(DiagJob& J) {
+  J.a2norm = a2_norm(J.R);
+  J.inv_dl = 1.0 / (J.rho_l - J.rho_v);
+}
 
 int diag_blocks(int Nz, int Nr) {
   const int N = Nz * Nr;
@@ -275,17 +281,17 @@ cudaError_t launch_diag(int storage, const InstDesc* d, int inst, int Nz, int Nr
   J.R = R;
   J.rho_l = rho_l;
   J.rho_v = rho_v;
-  J.a2norm = a2_norm(R);
+  diag_job_constants(J);
   J.inst = inst;
   J.blk0 = 0;
   J.nblk = nblk;
   J.col0 = 0;
   if (storage == AMLBM_STORE_F64) {
     diag_partial_one<double><<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
-    diag_final_one<double><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
+    diag_final_one<double><<<1, FINAL_NT, 0, s>>>(d, J, parity, partials, cols, out);
   } else {
     diag_partial_one<float><<<nblk, DIAG_NT, 0, s>>>(d, J, partials, cols);
-    diag_final_one<float><<<1, DIAG_NT, 0, s>>>(d, J, parity, partials, cols, out);
+    diag_final_one<float><<<1, FINAL_NT, 0, s>>>(d, J, parity, partials, cols, out);
   }
   return cudaGetLastError();
 }
@@ -305,10 +311,10 @@ cudaError_t launch_diag_all(int storage, const InstDesc* d, const DiagJob* d_job
   if (njobs < 1 || total_blocks < 1) return cudaErrorInvalidValue;
   if (storage == AMLBM_STORE_F64) {
     diag_partial_all<double><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, d_blkjob, partials, cols);
-    diag_final_all<double><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
+    diag_final_all<double><<<njobs, FINAL_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
   } else {
     diag_partial_all<float><<<total_blocks, DIAG_NT, 0, s>>>(d, d_jobs, d_blkjob, partials, cols);
-    diag_final_all<float><<<njobs, DIAG_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
+    diag_final_all<float><<<njobs, FINAL_NT, 0, s>>>(d, d_jobs, parity, partials, cols, out);
   }
   return cudaGetLastError();
 }

@@ -105,8 +105,12 @@ cudaError_t diag_preload();
 struct DiagJob {
   double zc, R, rho_l, rho_v;
   double a2norm;  // 5 / (4 pi R^5), the normalisation of a2 (computed on the host)
+  double inv_dl;  // 1 / (rho_l - rho_v) (computed on the host)
   int inst, blk0, nblk, col0;
 };
+// The job's constants that need a division or a power (a2norm, inv_dl), from R,
+// rho_l and rho_v, on the host: GB300's FP64 division is slow.
+void diag_job_constants(DiagJob& J);
 // Every job in one partial launch (total_blocks = sum of nblk; d_blkjob[b] is
 // the job of partial block b) and one final launch (one block per job,
 // out[16 * job]).
