@@ -213,3 +213,19 @@ def test_init_all_reads_pinned_host_arrays_in_place():
         assert np.array_equal(b.read_f(k), before[k]), k
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_init_all_reads_pinned_host_arrays_in_place(dtype):
+    """Page-locked host arrays are read by the init kernel over the CPU-GPU link (no
+    staging copy): the state equals that of the same values from pageable arrays."""
+    a, fields = make("f32")
+    b, _ = make("f32")
+    cols = [np.concatenate([np.ravel(fl[q]) for fl in fields]).astype(dtype) for q in range(3)]
+    pinned = [torch.from_numpy(c.copy()).pin_memory() for c in cols]
+    a.init_all(*cols)
+    b.init_all(*[t.numpy() for t in pinned])
+    for k in range(len(fields)):
+        assert np.array_equal(a.read_f(k), b.read_f(k)), k
+    a.close()
+    b.close()
