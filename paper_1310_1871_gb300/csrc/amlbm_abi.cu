@@ -116,7 +116,7 @@ void pick_tile(int storage, const std::vector<amlbm_instance>& inst, int* sched,
   static const int pref64[][2] = {{32, 16}, {32, 8}, {32, 8}};
   static const int pref64f[][2] = {{32, 8}, {32, 8}, {32, 8}};  // fused, for bounded lattices
   static const int pref32[][2] = {{26, 16}, {64, 8}, {32, 8}};
-  static const int prefpair[][2] = {{40, 24}, {32, 16}, {24, 16}};
+  static const int prefpair[][2] = {{64, 24}, {40, 24}, {24, 16}};
   bool any_bounded = false;
   for (const auto& I : inst) any_bounded = any_bounded || bounded(I.bc);
   const bool f64 = storage == AMLBM_STORE_F64;

@@ -64,14 +64,15 @@ struct PGeo {
 };
 
 // Threads per CTA and the resident CTAs per SM the register budget must allow.
-// FP32 arithmetic: 256 threads; four CTAs per SM (64 registers) where the tile's
-// shared memory fits four in the SM's 228 KB (1 KB reserved per CTA), else as
-// many as fit (three: 80 registers).  FP64: 256 threads, one CTA.
+// FP32 arithmetic: as many CTAs per SM as the tile's shared memory fits in the
+// SM's 228 KB (1 KB reserved per CTA), at most four: four of 256 threads at 64
+// registers, three of 256 at 80, and two of 384 at 80 (a tile that fits only
+// two keeps 24 warps per SM that way).  FP64: 256 threads, one CTA.
 template <class T, int BZ, int BR>
 struct Threads {
-  static constexpr int value = 256;
   static constexpr int fit = (int)(233472 / (PGeo<T, BZ, BR>::bytes + 1024 + 16));
   static constexpr int min_blocks = fit >= 4 ? 4 : (fit >= 1 ? fit : 1);
+  static constexpr int value = min_blocks == 2 ? 384 : 256;
 };
 template <int BZ, int BR>
 struct Threads<D1, BZ, BR> {
@@ -566,8 +567,8 @@ cudaError_t launch_readback_t(const InstDesc* d, const int* ti, int nt, int toff
 }
 
 struct PairTile { int storage, tz, tr; };
-#define AMLBM_PAIR_TILES(ST) {ST, 40, 24}, {ST, 48, 20}, {ST, 32, 16}, {ST, 48, 16}, {ST, 24, 16}, \
-                             {ST, 64, 16}, {ST, 32, 32}, {ST, 48, 22}
+#define AMLBM_PAIR_TILES(ST) {ST, 40, 24}, {ST, 48, 20}, {ST, 64, 24}, {ST, 32, 16}, {ST, 48, 16}, \
+                             {ST, 24, 16}, {ST, 64, 16}, {ST, 32, 32}
 constexpr PairTile kPairTiles[] = {
     {AMLBM_STORE_F64, 32, 8}, {AMLBM_STORE_F64, 28, 8},
     AMLBM_PAIR_TILES(AMLBM_STORE_F32), AMLBM_PAIR_TILES(AMLBM_STORE_F16), AMLBM_PAIR_TILES(AMLBM_STORE_BF16),
@@ -594,12 +595,12 @@ cudaError_t pair_dispatch(int kind, int tz, int tr, const InstDesc* d, const int
   } else {
     AMLBM_PT(40, 24)
     AMLBM_PT(48, 20)
+    AMLBM_PT(64, 24)
     AMLBM_PT(32, 16)
     AMLBM_PT(48, 16)
     AMLBM_PT(24, 16)
     AMLBM_PT(64, 16)
     AMLBM_PT(32, 32)
-    AMLBM_PT(48, 22)
   }
 #undef AMLBM_PT
   return cudaErrorInvalidValue;
