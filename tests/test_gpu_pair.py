@@ -78,14 +78,16 @@ def test_pair_fp64_matches_oracle_1000_steps():
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 def test_pair_sweep_equals_fused_bitwise(storage):
-    """The 64-drop sweep (uneven lattices, one persistent launch per step), 60 steps."""
+    """The 64-drop sweep (uneven lattices, one persistent launch per step), 60 steps, on
+    the default pair tile and two others."""
     inst = I.batch_sweep(64)
     specs = [amlbm.InstanceSpec(x.Nz, x.Nr, x.tau, x.G) for x in inst]
     fields = [x.make_fields() for x in inst]
     a = run(specs, fields, storage, "fused", (26, 16), 60)
-    b = run(specs, fields, storage, "pair", (32, 16), 60)
-    for k in range(len(specs)):
-        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    for tile in ((64, 24), (40, 24), (32, 16)):
+        b = run(specs, fields, storage, "pair", tile, 60)
+        for k in range(len(specs)):
+            assert np.array_equal(a[k], b[k], equal_nan=True), (tile, k)
 
 
 @pytest.mark.parametrize("kw,Nz", [(dict(src="link"), 32), (dict(), 33), (dict(z_bc="noslip"), 32),
